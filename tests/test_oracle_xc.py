@@ -1,0 +1,144 @@
+"""Pins for the oracle's B3LYP(VWN5) energy density and its potentials. CPU only.
+
+Independent references:
+* Slater exchange == the uniform-gas exchange -(3/4pi) k_F per electron, k_F = (3 pi^2 rho)^(1/3).
+* Hydrogen-atom exchange energies (LSDA, B88) printed by Becke 1988
+  (tests/golden/h_atom_exchange_becke1988.json), via spin scaling
+  E_x[rho_a, 0] = E_x^closed[2 rho_a] / 2.
+* B88 correction vanishes for a uniform gas (sigma -> 0).
+* VWN5: high-density limit slope d eps_c / d ln r_s -> (1 - ln 2)/pi^2 (Gell-Mann-Brueckner),
+  and agreement with the independent Perdew-Wang 1992 fit to the same QMC data.
+* LYP: the Laplacian-free Miehlich form integrates to the same energy as the
+  original Lee-Yang-Parr form (with t_W and the Laplacian) for spherical densities.
+* Potentials: complex-step derivatives vs central finite differences; and
+  V_xc = dE_xc/dD by finite differences in D (whole chain: AO gradients, rho,
+  sigma, assembly).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import xc
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_slater_is_uniform_gas_exchange():
+    rho = np.logspace(-8, 3, 23)
+    kf = (3.0 * math.pi ** 2 * rho) ** (1.0 / 3.0)
+    ref = -(3.0 / (4.0 * math.pi)) * kf * rho
+    assert np.allclose(xc.slater(rho), ref, rtol=1e-14)
+
+
+def _radial(f, rmax):
+    return integrate.quad(lambda r: 4 * math.pi * r * r * f(r), 0, rmax, limit=400,
+                          epsabs=1e-14, epsrel=1e-13)[0]
+
+
+def test_hydrogen_atom_exchange_becke1988():
+    g = json.load(open(os.path.join(GOLD, "h_atom_exchange_becke1988.json")))
+    rho = lambda r: math.exp(-2 * r) / math.pi  # noqa: E731
+    drho = lambda r: -2 * math.exp(-2 * r) / math.pi  # noqa: E731
+    lda = 0.5 * _radial(lambda r: xc.slater(2 * rho(r)), 40)
+    b88 = 0.5 * _radial(lambda r: xc.slater(2 * rho(r))
+                        + xc.b88_correction(2 * rho(r), (2 * drho(r)) ** 2), 40)
+    assert abs(lda - g["E_x_lsda"]) < g["tol"]
+    assert abs(b88 - g["E_x_b88"]) < g["tol"]
+    assert abs(b88 - g["E_x_exact"]) < 5e-3
+
+
+def test_b88_uniform_gas_limit():
+    rho = np.logspace(-6, 2, 9)
+    ratio = xc.b88_correction(rho, 1e-20 * rho ** (8 / 3)) / xc.slater(rho)
+    assert np.all(np.abs(ratio) < 1e-18)
+
+
+def test_vwn5_high_density_slope():
+    h = 1e-3
+    for rs in (1e-6, 1e-8):
+        slope = (xc.vwn5_eps(rs * math.exp(h)) - xc.vwn5_eps(rs * math.exp(-h))) / (2 * h)
+        assert slope == pytest.approx((1 - math.log(2)) / math.pi ** 2, rel=2e-4)
+
+
+def test_vwn5_matches_pw92_fit():
+    A, a1, b1, b2, b3, b4 = 0.031091, 0.21370, 7.5957, 3.5876, 1.6382, 0.49294
+    rs = np.linspace(0.2, 20, 60)
+    pw = -2 * A * (1 + a1 * rs) * np.log(1 + 1 / (2 * A * (b1 * rs ** 0.5 + b2 * rs
+                                                         + b3 * rs ** 1.5 + b4 * rs ** 2)))
+    assert np.max(np.abs(xc.vwn5_eps(rs) / pw - 1)) < 1e-2
+
+
+def _lyp_original(rho, grad2, lap):
+    a, b, c, d = xc.LYP_A, xc.LYP_B, xc.LYP_C, xc.LYP_D
+    tw = grad2 / (8 * rho) - lap / 8
+    return -a / (1 + d * rho ** (-1 / 3)) * (
+        rho + b * rho ** (-2 / 3) * (xc.C_F * rho ** (5 / 3) - 2 * tw + (tw / 9 + lap / 18))
+        * math.exp(-c * rho ** (-1 / 3)))
+
+
+@pytest.mark.parametrize("kind", ["slater", "gauss"])
+def test_lyp_forms_integrate_equal(kind):
+    if kind == "slater":
+        z = 1.6875
+        N = 2 * z ** 3 / math.pi
+        r0 = lambda r: N * math.exp(-2 * z * r)  # noqa: E731
+        r1 = lambda r: -2 * z * r0(r)  # noqa: E731
+        r2 = lambda r: 4 * z * z * r0(r)  # noqa: E731
+        rmax = 30
+    else:
+        al = 1.3
+        N = 2 * (al / math.pi) ** 1.5
+        r0 = lambda r: N * math.exp(-al * r * r)  # noqa: E731
+        r1 = lambda r: -2 * al * r * r0(r)  # noqa: E731
+        r2 = lambda r: (4 * al * al * r * r - 2 * al) * r0(r)  # noqa: E731
+        rmax = 12
+    i1 = _radial(lambda r: float(xc.lyp(r0(r), r1(r) ** 2)), rmax)
+    i2 = _radial(lambda r: _lyp_original(r0(r), r1(r) ** 2, r2(r) + 2 * r1(r) / r), rmax)
+    assert i1 == pytest.approx(i2, rel=1e-9)
+
+
+def test_complex_step_potentials_vs_finite_differences():
+    rng = np.random.default_rng(0)
+    rho = 10.0 ** rng.uniform(-6, 2, 200)
+    sigma = rho ** (8 / 3) * 10.0 ** rng.uniform(-3, 2, 200)
+    e, vr, vs = xc.b3lyp(rho, sigma)
+
+    def cd(f, x, h):
+        return (f(x * (1 + h)) - f(x * (1 - h))) / (2 * h * x)
+
+    def rich(f, x, h=2e-3):  # Richardson-extrapolated central difference
+        return (4 * cd(f, x, h / 2) - cd(f, x, h)) / 3
+
+    fr = rich(lambda r: xc.b3lyp_e(r, sigma), rho)
+    fs = rich(lambda s_: xc.b3lyp_e(rho, s_), sigma)
+    assert np.allclose(vr, fr, rtol=1e-8, atol=0)
+    assert np.allclose(vs, fs, rtol=1e-7, atol=0)
+
+
+def test_cutoff():
+    e, vr, vs = xc.b3lyp(np.array([1e-11, 1e-10]), np.array([1e-25, 1e-25]))
+    assert e[0] == 0 and vr[0] == 0 and vs[0] == 0
+    assert e[1] != 0
+
+
+def test_vxc_is_derivative_of_exc():
+    """V_xc(D) . dD == d/dh E_xc(D + h dD) for a symmetric perturbation."""
+    from molgen import h2o
+    from oracle import scf
+    Z, xyz = h2o()
+    s = scf.System(Z, xyz)
+    D = s.core_guess()
+    phi, dphi = s.ao()
+    rng = np.random.default_rng(2)
+    dD = rng.normal(size=D.shape)
+    dD = 0.005 * (dD + dD.T)  # small: keeps every point on one side of the cut-off
+    exc, V, _ = scf.vxc_matrix(phi, dphi, s.w, D)
+    h = 1e-4
+    ep, _, _ = scf.vxc_matrix(phi, dphi, s.w, D + h * dD)
+    em, _, _ = scf.vxc_matrix(phi, dphi, s.w, D - h * dD)
+    fd = (ep - em) / (2 * h)
+    assert np.sum(V * dD) == pytest.approx(fd, rel=1e-7)
