@@ -1,0 +1,227 @@
+/*
+ * rks.h -- C ABI of the batched closed-shell Kohn-Sham (B3LYP/STO-3G) SCF
+ * engine for one GB300 (sm_103a).
+ *
+ * What it computes (arXiv 2311.01135, Section 3.1, Eq. 1): for each molecule
+ * (atomic numbers Z, positions R) the self-consistent solution of
+ *     [V + T + J(rho) + K(rho) + V_xc(rho)] C = S C eps,   rho = C D C^T,
+ * D_ii = 2 for the N_el/2 lowest orbitals, with the Coulomb and exchange
+ * contractions of the two-electron tensor I^2e written in Eq. 1, B3LYP
+ * exchange-correlation (Section 3.2, "Libxc") in the STO-3G basis
+ * (Section 3.3), and the HL gap of Section 3.1 (reported here as
+ * eps_LUMO - eps_HOMO > 0).  Outputs match the labels of the paper's dataset
+ * (Section 4: energy, HOMO, LUMO).
+ *
+ * Conventions shared by every call:
+ *  - Return value 0 (RKS_OK) on success, a negative RKS_E* code otherwise;
+ *    rks_strerror() names it.  Numerical outcomes of one molecule (not
+ *    converged, non-finite, ill-conditioned S) are reported in
+ *    rks_result_t.status, not as call errors.
+ *  - Every input array is read during the call and copied; the library never
+ *    keeps a caller pointer.  Every output buffer is caller-owned.
+ *  - Coordinates are bohr unless rks_options.coords_in_angstrom is set
+ *    (1 bohr = 0.52917721092 Angstrom).  Energies are Hartree.
+ *  - AO order: atoms in input order; per heavy atom (C, N, O, F) 1s, 2s, 2px,
+ *    2py, 2pz; per H 1s.  Matrices are nbf x nbf, row-major, FP64.
+ *  - Supported elements: H, C, N, O, F.  The electron count must be even.
+ *  - A context owns one CUDA device, its streams and all device memory.  It
+ *    is safe to call rks_submit / rks_poll / rks_wait / rks_result from
+ *    several host threads.
+ */
+#ifndef RKS_H
+#define RKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define RKS_OK 0
+#define RKS_EINVAL (-1)    /* bad argument: element, natom, odd N_el, non-finite xyz, nbf too large */
+#define RKS_ENOMEM (-2)    /* device or host allocation failed, or request exceeds the HBM budget */
+#define RKS_EAGAIN (-3)    /* submission queue full; retry later */
+#define RKS_ENOTREADY (-4) /* ticket not finished yet */
+#define RKS_ECUDA (-5)     /* a CUDA call failed (message via rks_last_error) */
+#define RKS_ETIMEOUT (-6)  /* rks_wait timed out */
+#define RKS_ENOTFOUND (-7) /* unknown or already released ticket */
+#define RKS_EDEVICE (-8)   /* a device-side bounded wait or bounds check gave up */
+
+/* ---------------------------------------------------- per-molecule status */
+#define RKS_STATUS_OK 0
+#define RKS_STATUS_NOT_CONVERGED 1 /* "converge" protocol hit max_iters */
+#define RKS_STATUS_NONFINITE 2     /* a NaN/Inf appeared in F, E or eps */
+#define RKS_STATUS_S_ILL 3         /* min eig(S) < 1e-8 */
+#define RKS_STATUS_EIGH 4          /* Jacobi did not reach tolerance */
+
+/* ---------------------------------------------------------- ticket state */
+#define RKS_PENDING 0
+#define RKS_RUNNING 1
+#define RKS_DONE 2
+#define RKS_FAILED 3
+
+/* --------------------------------------------------------------- precision */
+#define RKS_FP64 0  /* every step in FP64 */
+#define RKS_MIXED 1 /* FP32 ERIs / J/K / grid + FP64 linear algebra and energy, FP64 final correction */
+
+#define RKS_MAX_NBF 128 /* largest basis a molecule may have */
+
+typedef struct rks_ctx rks_ctx;
+typedef struct rks_batch rks_batch;
+
+typedef struct rks_options {
+    int32_t basis;          /* 0 = STO-3G (only value) */
+    int32_t n_rad;          /* radial points per atom (Treutler-Ahlrichs M4), default 50 */
+    int32_t n_theta;        /* Gauss-Legendre nodes in cos(theta), default 12 */
+    int32_t n_phi;          /* uniform azimuthal points, default 24 */
+    int32_t becke_iters;    /* Becke smoothing iterations, default 3 */
+    int32_t precision;      /* RKS_FP64 or RKS_MIXED */
+    int32_t fixed_iters;    /* > 0: run exactly this many SCF iterations, then the final step;
+                               0: iterate to convergence (e_tol, err_tol), at most max_iters */
+    int32_t max_iters;      /* cap for the converge protocol, default 100 */
+    double e_tol;           /* |E_k - E_(k-1)| threshold (Ha), default 1e-9 */
+    double err_tol;         /* max |X^T(FDS - SDF)X| threshold, default 1e-6 */
+    int32_t diis_space;     /* DIIS history length (1..8), default 8 */
+    int32_t coords_in_angstrom;
+    int32_t xc;             /* 1 = B3LYP (default); 0 = Hartree-Fock test mode (a0 = 1, no V_xc) */
+    int32_t max_slots;      /* most molecules resident on the device at once, default 4096 */
+    uint64_t hbm_budget_bytes; /* admission cap for resident molecules; 0 = 85% of free memory */
+    int32_t device;         /* CUDA device ordinal, default 0 */
+    int32_t use_graphs;     /* capture fixed-iteration loops in CUDA graphs, default 1 */
+} rks_options;
+
+typedef struct rks_result_t {
+    int32_t status;   /* RKS_STATUS_* */
+    int32_t nbf;      /* basis size */
+    int32_t n_occ;    /* doubly occupied orbitals */
+    int32_t iters;    /* SCF iterations run (excluding the final step) */
+    double e_total;   /* total energy (Ha) at the last density */
+    double e_homo;    /* eps[n_occ - 1] */
+    double e_lumo;    /* eps[n_occ] */
+    double gap;       /* e_lumo - e_homo */
+    double e_xc;      /* exchange-correlation energy (no exact-exchange part) */
+    double e_nuc;     /* nuclear repulsion */
+    double latency_s; /* submit -> done (serving API); batch wall time per molecule (batch API) */
+    int32_t paper_converged; /* std of the last 5 energies < 0.01 Ha (the paper's flag) */
+    int32_t pad;
+} rks_result_t;
+
+/* Fill *o with the defaults listed above. */
+int rks_options_default(rks_options *o);
+
+/* Number of STO-3G basis functions of a molecule (no context needed);
+ * negative RKS_EINVAL for an unsupported element or natom <= 0. */
+int rks_nbf(int32_t natom, const int32_t *Z);
+
+const char *rks_strerror(int code);
+/* Last CUDA / internal error message of the context (or the library when ctx is NULL). */
+const char *rks_last_error(rks_ctx *ctx);
+
+/* ------------------------------------------------------------ context */
+/* Create a context on options->device: allocates streams and the constant
+ * tables (Boys function table), starts the serving worker thread.
+ * Errors: RKS_EINVAL (bad options), RKS_ECUDA, RKS_ENOMEM. */
+int rks_create(const rks_options *options, rks_ctx **out);
+/* Stops the worker (pending tickets are failed), frees device memory. */
+int rks_destroy(rks_ctx *ctx);
+/* The context's compute stream (a cudaStream_t), for timing with events. */
+void *rks_stream(rks_ctx *ctx);
+
+/* ------------------------------------------------------- serving API */
+/* Queue one molecule.  Non-blocking: copies Z[natom] and xyz[natom*3]
+ * (row-major) and returns a ticket.  The worker admits queued molecules into
+ * device slots as memory frees up (continuous batching: molecules admitted
+ * while others are mid-SCF join the next iteration tick).
+ * Errors: RKS_EINVAL (validation as above), RKS_EAGAIN (queue full). */
+int rks_submit(rks_ctx *ctx, int32_t natom, const int32_t *Z, const double *xyz,
+               uint64_t *ticket_out);
+/* Non-blocking state query: RKS_PENDING / RKS_RUNNING / RKS_DONE / RKS_FAILED. */
+int rks_poll(rks_ctx *ctx, uint64_t ticket, int32_t *state_out);
+/* Block the calling host thread until the ticket is done or timeout_s passes. */
+int rks_wait(rks_ctx *ctx, uint64_t ticket, double timeout_s);
+/* Copy the result of a finished ticket and release it.  eps_out (nbf values,
+ * ascending) and D_out (nbf*nbf, the output total density) may be NULL;
+ * cap_nbf is their capacity in basis functions (RKS_EINVAL if smaller than
+ * nbf).  Errors: RKS_ENOTREADY, RKS_ENOTFOUND. */
+int rks_result(rks_ctx *ctx, uint64_t ticket, rks_result_t *out, double *eps_out,
+               double *D_out, int32_t cap_nbf);
+
+/* --------------------------------------------------------- batch API */
+/* A batch is a fixed set of molecules resident on the device; used by the
+ * benchmark (device-resident inputs) and the parity tests.  Z and xyz are the
+ * concatenation of every molecule's atoms; natom[m] gives the split.
+ * Setup copies the inputs to the device (host->device happens here).
+ * Errors: RKS_EINVAL, RKS_ENOMEM, RKS_ECUDA. */
+int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom, const int32_t *Z,
+                     const double *xyz, rks_batch **out);
+/* Enqueue the whole method (integrals, grid, SCF iterations, final step) on
+ * the context stream and return without waiting (for the converge protocol the
+ * call waits for convergence checks every few iterations). */
+int rks_batch_run(rks_batch *b);
+/* Wait for the batch's work to finish; RKS_EDEVICE if a kernel reported a
+ * bounded-wait or bounds failure. */
+int rks_batch_sync(rks_batch *b);
+/* Results of molecule m (after sync), same buffers as rks_result. */
+int rks_batch_result(rks_batch *b, int32_t m, rks_result_t *out, double *eps_out, double *D_out,
+                     int32_t cap_nbf);
+int rks_batch_destroy(rks_batch *b);
+
+/* ------------------------------------------------- stage-level entries */
+/* Run only the iteration-0 steps (one-electron integrals, Schwarz screening,
+ * packing, ERIs, grid, orthogonaliser) for the batch. */
+int rks_batch_setup(rks_batch *b);
+/* With the batch set up, build F[D] for the given densities (one nbf*nbf
+ * FP64 matrix per molecule, concatenated): J, K, V_xc, E_xc and E at D.
+ * final_step = 1 uses the precision of the final correction. */
+int rks_batch_fock(rks_batch *b, const double *D_all, int32_t final_step);
+
+/* Copy a per-molecule array out for inspection (parity tests).
+ * what: see RKS_DUMP_*.  Returns the number of bytes written, or a negative
+ * error (RKS_EINVAL if cap is too small). */
+#define RKS_DUMP_PAIRS 0    /* kept shell pairs: int32 [npair][2] (P, Q in packing shell order) */
+#define RKS_DUMP_PAIR_Q 1   /* Schwarz Q of the kept pairs: double [npair] */
+#define RKS_DUMP_ROW_OFF 2  /* element offset of every kept pair's row: int64 [npair + 1] */
+#define RKS_DUMP_STORE 3    /* packed ERI values: double [n] (FP32 stores are widened) */
+#define RKS_DUMP_S 4        /* overlap, double [nbf*nbf] */
+#define RKS_DUMP_T 5        /* kinetic */
+#define RKS_DUMP_V 6        /* nuclear attraction */
+#define RKS_DUMP_GRID 7     /* grid points: double [npts][4] (x, y, z, w), padding removed */
+#define RKS_DUMP_J 8        /* last Coulomb matrix */
+#define RKS_DUMP_K 9        /* last exchange matrix K_std (no -a0/2 factor) */
+#define RKS_DUMP_VXC 10     /* last V_xc */
+#define RKS_DUMP_D 11       /* current density (input of the last Fock build) */
+#define RKS_DUMP_F 12       /* last Fock matrix */
+#define RKS_DUMP_EPS 13     /* orbital energies [nbf] */
+#define RKS_DUMP_X 14       /* S^-1/2 */
+#define RKS_DUMP_SCALARS 15 /* double [8]: E, E_xc, E_nuc, n_pair_all, n_quartets, store elements, npts, near-tie count */
+#define RKS_DUMP_QUARTETS 16 /* kept quartet count per row: int32 [npair] */
+int64_t rks_batch_dump(rks_batch *b, int32_t m, int32_t what, void *out, int64_t cap_bytes);
+
+/* ------------------------------------------------------ profiling */
+typedef struct rks_stage_time {
+    char name[24];
+    int32_t launches; /* kernel launches recorded since the last reset */
+    double ms;        /* summed CUDA-event time of those launches */
+    double units;     /* algorithmic work processed (bytes or flops, per stage) */
+} rks_stage_time;
+/* Record CUDA events around every stage launch on the context stream (on = 1). */
+int rks_profile_enable(rks_ctx *ctx, int32_t on);
+/* Read and reset per-stage totals; returns the number of stages written. */
+int rks_profile_read(rks_ctx *ctx, rks_stage_time *out, int32_t cap);
+
+/* ------------------------------------------------------ unit entries */
+/* Boys function F_m(T) for m = 0..mmax at n arguments, by the device kernel
+ * (tabulated Taylor expansion + asymptotic form).  out is [n][mmax+1].
+ * precision RKS_FP64 or RKS_MIXED (FP32).  Host buffers. */
+int rks_eval_boys(rks_ctx *ctx, int32_t mmax, int32_t n, const double *T, double *out,
+                  int32_t precision);
+/* B3LYP energy density and potentials (e, v_rho, v_sigma) at n points of
+ * (rho, sigma = |grad rho|^2), by the device kernel.  Host buffers. */
+int rks_eval_xc(rks_ctx *ctx, int32_t n, const double *rho, const double *sigma, double *e,
+                double *v_rho, double *v_sigma, int32_t precision);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RKS_H */

@@ -1,0 +1,127 @@
+// Internal structures shared by the kernels and the host engine.
+//
+// One batch = a set of molecules ("slots") resident in HBM.  Every per-molecule
+// array lives in a batch-wide buffer; MolDesc holds the offsets.  Kernels take
+// a DevBatch by value and index through the descriptors, so one launch covers
+// every molecule of the batch (uneven basis sizes included).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define RKS_NBF_CAP 96      // largest nbf the kernels are compiled for
+#define RKS_DIIS_MAX 8
+#define RKS_MAXP 3          // primitives per STO-3G shell
+#define RKS_PTS_BLOCK 128   // grid points are stored in blocks of this many
+#define RKS_NHIST 64        // energies kept per molecule (paper's std(E[-5:]) flag)
+
+// Slot (per-molecule) descriptor.  All offsets are element offsets into the
+// batch-wide arrays named in the comments.
+struct MolDesc {
+    int natom, nbf, nocc, nsh;
+    int atom0;          // Z[], axyz[]
+    int sh0;            // shell arrays
+    int npair_all;      // candidate shell pairs (P >= Q)
+    int pair0;          // cand[], cand_q[], kpair[], kq[], row_nq[]; row_off[] uses pair0 + index_in_batch
+    int npts;           // real grid points
+    int nblk;           // 128-point blocks (padded)
+    long long pts0;     // grid arrays (multiple of 128)
+    long long eri0;     // packed store (elements)
+    long long eri_cap;  // store capacity (unscreened upper bound, elements)
+    long long mat0;     // FP64 matrix arena (doubles); see MatSlot
+    long long acc0;     // accumulator arena offset (elements), 3 * nbf^2
+};
+
+// FP64 matrices of one molecule, each nbf*nbf, at mat0 + slot * nbf*nbf.
+enum MatSlot {
+    M_S = 0, M_T, M_V, M_H, M_X, M_D, M_F, M_C, M_J, M_K, M_VXC, M_FX, M_TMP1, M_TMP2, M_TMP3,
+    M_CP,     // eigenvectors of the previous X^T F X (unused when cold-started)
+    M_DIIS_F, // RKS_DIIS_MAX matrices
+    M_DIIS_E = M_DIIS_F + RKS_DIIS_MAX,
+    M_COUNT = M_DIIS_E + RKS_DIIS_MAX
+};
+
+// Per-molecule FP64 scalars and small state (one struct per slot, device).
+struct MolState {
+    double E, E_prev, Exc, Enuc, max_err, smin;
+    double eps_homo, eps_lumo;
+    double B[RKS_DIIS_MAX * RKS_DIIS_MAX]; // DIIS Gram matrix of the stored error vectors
+    double Ehist[RKS_NHIST];
+    int diis_n, diis_head;  // ring buffer: entries, index of the oldest
+    int iter;               // SCF iterations done
+    int active;             // 1 while iterating
+    int converged;
+    int status;             // RKS_STATUS_*
+    int eigh_fail;
+    int err_flag;           // device-side bounds / consistency failures
+    int n_quartets;
+    int near_ties;
+    long long n_elem;       // store elements written
+    double eps[RKS_NBF_CAP];
+};
+
+// Device view of a batch (passed by value to kernels).
+struct DevBatch {
+    int nmol;
+    int precision;          // 0 FP64, 1 mixed
+    int xc;                 // 1 B3LYP, 0 Hartree-Fock
+    double a0;              // exact-exchange fraction in the Fock matrix
+    const MolDesc *mol;
+    MolState *st;
+    // atoms
+    const int *Z;
+    const double *axyz;     // [natom][3]
+    // shells in packing order (s shells, then p shells; atom order inside)
+    const int *sh_atom, *sh_l, *sh_ao0;
+    const double *sh_xyz;   // [nsh][3]
+    const double *sh_ex;    // [nsh][3]
+    const double *sh_co;    // [nsh][3] normalised contraction coefficients
+    // candidate shell pairs (all P >= Q, ordered by (l_P + l_Q, P, Q))
+    const int2 *cand;
+    const int *cand_mol;    // owning molecule of each candidate
+    double *cand_q;         // Schwarz Q per candidate
+    int2 *kpair;            // kept pairs (compacted, same order)
+    double *kq;             // their Q
+    int *npair;             // kept pairs per molecule
+    int *row_nq;            // kept quartets per kept row
+    long long *row_off;     // exclusive prefix of row element counts; [pair0 + m + r], r <= npair
+    void *store;            // packed ERIs (float or double)
+    // grid (SoA, padded blocks; padding points have w = 0)
+    void *gx, *gy, *gz, *gw;
+    // FP64 matrices
+    double *mat;
+    // accumulators J', K', V' (3 * nbf^2 per molecule at acc0): FP32 for the
+    // mixed iterations, FP64 for the FP64 path and the final step
+    float *accf;
+    double *accd;
+    // Boys tables
+    const double *boys64;
+    const float *boys32;
+    // grid options
+    int n_rad, n_theta, n_phi, becke_iters;
+    int diis_space;
+    int fixed_iters, max_iters;
+    double e_tol, err_tol;
+};
+
+__host__ __device__ inline long long nbf2(int n) { return (long long)n * n; }
+
+__device__ inline double *matp(const DevBatch &b, const MolDesc &m, int slot) {
+    return b.mat + m.mat0 + (long long)slot * nbf2(m.nbf);
+}
+
+// Boys table layout: rows T_i = i * h for i = 0..n-1, columns F_0..F_(ncol-1).
+#define BOYS_H 0.05
+#define BOYS_N64 801   // T < 40 in FP64 (Taylor, 7 terms)
+#define BOYS_COL64 11
+#define BOYS_TMAX64 40.0
+#define BOYS_N32 601   // T < 30 in FP32 (Taylor, 4 terms)
+#define BOYS_COL32 8
+#define BOYS_TMAX32 30.0
+
+#define CUDA_OK(x)                                                                              \
+    do {                                                                                        \
+        cudaError_t e_ = (x);                                                                   \
+        if (e_ != cudaSuccess) return rks_cuda_fail(e_, #x, __FILE__, __LINE__);                \
+    } while (0)
+
+int rks_cuda_fail(cudaError_t e, const char *what, const char *file, int line);

@@ -1,0 +1,956 @@
+// Host engine and C ABI (include/rks.h): contexts, batches, the stage
+// sequence of the SCF, results, profiling and the serving queue.
+//
+// Stage sequence of one batch (paper Section 3.1: iteration 0 precomputes
+// V, T, S, I^2e and a first C; each iteration builds rho, V_xc, J, K and
+// solves the eigenproblem):
+//   setup: one-electron ints -> Schwarz Q -> kept pairs -> per-row quartet
+//          counts -> row offsets -> packed ERIs -> grid -> H, E_nuc -> S^-1/2
+//          and the core-Hamiltonian guess
+//   iterate: zero accumulators -> J/K (packed store) -> grid XC -> FP64 step
+//   final:   the same Fock build at the final precision -> plain diagonalisation
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/rks.h"
+#include "common.cuh"
+#include "kernels.h"
+
+// ------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+int rks_cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    g_err = buf;
+    return e == cudaErrorMemoryAllocation ? RKS_ENOMEM : RKS_ECUDA;
+}
+
+static int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+// ------------------------------------------------------------ STO-3G
+// Hehre-Stewart-Pople STO-3G at the standard molecular exponents (H, C, N, O, F);
+// 2s and 2p share exponents and are separate shells here.  Coefficients are for
+// normalised primitives; the contracted functions are renormalised at start-up.
+struct ShellDef {
+    int l;
+    double e[3], c[3];
+};
+struct ElemDef {
+    int Z;
+    int nsh;
+    ShellDef sh[3];
+};
+static const double kC1s[3] = {0.15432897, 0.53532814, 0.44463454};
+static const double kC2s[3] = {-0.09996723, 0.39951283, 0.70011547};
+static const double kC2p[3] = {0.15591627, 0.60768372, 0.39195739};
+static ElemDef g_elem[5] = {
+    {1, 1, {{0, {3.42525091, 0.62391373, 0.16885540}, {0}}}},
+    {6, 3, {{0, {71.6168370, 13.0450960, 3.5305122}, {0}}, {0, {2.9412494, 0.6834831, 0.2222899}, {0}},
+            {1, {2.9412494, 0.6834831, 0.2222899}, {0}}}},
+    {7, 3, {{0, {99.1061690, 18.0523120, 4.8856602}, {0}}, {0, {3.7804559, 0.8784966, 0.2857144}, {0}},
+            {1, {3.7804559, 0.8784966, 0.2857144}, {0}}}},
+    {8, 3, {{0, {130.7093200, 23.8088610, 6.4436083}, {0}}, {0, {5.0331513, 1.1695961, 0.3803890}, {0}},
+            {1, {5.0331513, 1.1695961, 0.3803890}, {0}}}},
+    {9, 3, {{0, {166.6791300, 30.3608120, 8.2168207}, {0}}, {0, {6.4648032, 1.5022812, 0.4885885}, {0}},
+            {1, {6.4648032, 1.5022812, 0.4885885}, {0}}}},
+};
+static std::once_flag g_basis_once;
+
+// Multiply the published coefficients by the primitive norms
+// (2a/pi)^(3/4) (4a)^(l/2) and rescale to unit self-overlap.
+static void init_basis() {
+    for (auto &E : g_elem)
+        for (int s = 0; s < E.nsh; s++) {
+            ShellDef &sd = E.sh[s];
+            const double *src = (E.Z == 1 || s == 0) ? kC1s : (sd.l == 0 ? kC2s : kC2p);
+            double c[3];
+            for (int k = 0; k < 3; k++)
+                c[k] = src[k] * pow(2.0 * sd.e[k] / M_PI, 0.75) * pow(4.0 * sd.e[k], 0.5 * sd.l);
+            double so = 0.0;
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) {
+                    double p = sd.e[i] + sd.e[j];
+                    double v = pow(M_PI / p, 1.5);
+                    if (sd.l == 1) v /= 2.0 * p;
+                    so += c[i] * c[j] * v;
+                }
+            for (int k = 0; k < 3; k++) sd.c[k] = c[k] / sqrt(so);
+        }
+}
+
+static const ElemDef *elem_of(int Z) {
+    for (auto &E : g_elem)
+        if (E.Z == Z) return &E;
+    return nullptr;
+}
+
+extern "C" int rks_nbf(int32_t natom, const int32_t *Z) {
+    if (natom <= 0 || !Z) return RKS_EINVAL;
+    int n = 0;
+    for (int i = 0; i < natom; i++) {
+        const ElemDef *E = elem_of(Z[i]);
+        if (!E) return RKS_EINVAL;
+        for (int s = 0; s < E->nsh; s++) n += E->sh[s].l ? 3 : 1;
+    }
+    return n;
+}
+
+extern "C" const char *rks_strerror(int code) {
+    switch (code) {
+    case RKS_OK: return "ok";
+    case RKS_EINVAL: return "invalid argument";
+    case RKS_ENOMEM: return "out of memory / over budget";
+    case RKS_EAGAIN: return "queue full";
+    case RKS_ENOTREADY: return "not ready";
+    case RKS_ECUDA: return "CUDA error";
+    case RKS_ETIMEOUT: return "timed out";
+    case RKS_ENOTFOUND: return "unknown ticket";
+    case RKS_EDEVICE: return "device-side check failed";
+    default: return "unknown error";
+    }
+}
+
+extern "C" int rks_options_default(rks_options *o) {
+    if (!o) return RKS_EINVAL;
+    memset(o, 0, sizeof *o);
+    o->basis = 0;
+    o->n_rad = 50;
+    o->n_theta = 12;
+    o->n_phi = 24;
+    o->becke_iters = 3;
+    o->precision = RKS_FP64;
+    o->fixed_iters = 0;
+    o->max_iters = 100;
+    o->e_tol = 1e-9;
+    o->err_tol = 1e-6;
+    o->diis_space = 8;
+    o->coords_in_angstrom = 0;
+    o->xc = 1;
+    o->max_slots = 4096;
+    o->hbm_budget_bytes = 0;
+    o->device = 0;
+    o->use_graphs = 1;
+    return RKS_OK;
+}
+
+// --------------------------------------------------------- profiling
+struct StageRec {
+    std::string name;
+    cudaEvent_t a, b;
+    double units;
+};
+
+// ------------------------------------------------------------ context
+struct rks_batch;
+struct Ticket {
+    int state = RKS_PENDING;
+    std::vector<int> Z;
+    std::vector<double> xyz;
+    rks_result_t res{};
+    std::vector<double> eps, D;
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+struct rks_ctx {
+    rks_options opt{};
+    cudaStream_t stream = nullptr;
+    double *boys64 = nullptr;
+    float *boys32 = nullptr;
+    double *rad = nullptr, *ang = nullptr;
+    std::string err;
+    // profiling
+    bool prof = false;
+    std::vector<StageRec> recs;
+    std::map<std::string, rks_stage_time> totals;
+    // serving
+    std::mutex mu;
+    std::condition_variable cv, cv_done;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, Ticket> tickets;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+    size_t queue_cap = 1 << 20;
+};
+
+extern "C" const char *rks_last_error(rks_ctx *ctx) {
+    (void)ctx;
+    return g_err.c_str();
+}
+
+extern "C" void *rks_stream(rks_ctx *ctx) { return ctx ? (void *)ctx->stream : nullptr; }
+
+struct StageScope {
+    rks_ctx *c;
+    StageRec r;
+    bool on;
+    StageScope(rks_ctx *ctx, const char *name, double units) : c(ctx), on(ctx->prof) {
+        if (on) {
+            r.name = name;
+            r.units = units;
+            cudaEventCreate(&r.a);
+            cudaEventCreate(&r.b);
+            cudaEventRecord(r.a, c->stream);
+        }
+    }
+    ~StageScope() {
+        if (on) {
+            cudaEventRecord(r.b, c->stream);
+            c->recs.push_back(r);
+        }
+    }
+};
+
+extern "C" int rks_profile_enable(rks_ctx *ctx, int32_t on) {
+    if (!ctx) return RKS_EINVAL;
+    ctx->prof = on != 0;
+    return RKS_OK;
+}
+
+extern "C" int rks_profile_read(rks_ctx *ctx, rks_stage_time *out, int32_t cap) {
+    if (!ctx) return RKS_EINVAL;
+    CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    for (auto &r : ctx->recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto &t = ctx->totals[r.name];
+        snprintf(t.name, sizeof t.name, "%s", r.name.c_str());
+        t.launches += 1;
+        t.ms += ms;
+        t.units += r.units;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    ctx->recs.clear();
+    int n = 0;
+    for (auto &kv : ctx->totals) {
+        if (n < cap && out) out[n] = kv.second;
+        n++;
+    }
+    ctx->totals.clear();
+    return std::min(n, (int)cap);
+}
+
+// ------------------------------------------------------------- batch
+struct HostMol {
+    int natom, nbf, nocc, nsh, npair_all;
+    long long eri_cap;
+    int npts;
+};
+
+struct rks_batch {
+    rks_ctx *ctx = nullptr;
+    int nmol = 0;
+    int precision = 0;
+    int max_nbf = 0, max_nsh = 0, max_atoms = 0;
+    long long ncand = 0, nblk_total = 0;
+    std::vector<HostMol> hm;
+    std::vector<MolDesc> md;
+    DevBatch d{};
+    int *blk_mol = nullptr;
+    std::vector<void *> allocs;
+    bool set_up = false;
+    double wall_s = 0.0;
+    std::vector<MolState> st_host;
+    bool st_valid = false;
+    cudaGraphExec_t graph = nullptr;
+};
+
+template <typename T> static int dalloc(rks_batch *b, T **p, size_t n) {
+    void *q = nullptr;
+    size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return rks_cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+    b->allocs.push_back(q);
+    *p = (T *)q;
+    return RKS_OK;
+}
+
+static int validate(int natom, const int *Z, const double *xyz, int *nbf_out) {
+    if (natom <= 0 || natom > 128 || !Z || !xyz) return fail(RKS_EINVAL, "natom out of range or null input");
+    int nel = 0;
+    for (int i = 0; i < natom; i++) {
+        if (!elem_of(Z[i])) return fail(RKS_EINVAL, "unsupported element Z=" + std::to_string(Z[i]));
+        nel += Z[i];
+        for (int k = 0; k < 3; k++)
+            if (!std::isfinite(xyz[3 * i + k])) return fail(RKS_EINVAL, "non-finite coordinate");
+    }
+    if (nel % 2) return fail(RKS_EINVAL, "odd electron count");
+    int nbf = rks_nbf(natom, Z);
+    if (nbf > RKS_NBF_CAP) return fail(RKS_EINVAL, "nbf " + std::to_string(nbf) + " above the compiled maximum");
+    if (nbf_out) *nbf_out = nbf;
+    return RKS_OK;
+}
+
+extern "C" int rks_batch_destroy(rks_batch *b) {
+    if (!b) return RKS_EINVAL;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (void *p : b->allocs) cudaFree(p);
+    delete b;
+    return RKS_OK;
+}
+
+extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom, const int32_t *Z,
+                                const double *xyz, rks_batch **out) {
+    if (!ctx || nmol <= 0 || !natom || !Z || !xyz || !out) return fail(RKS_EINVAL, "null argument");
+    std::call_once(g_basis_once, init_basis);
+    const rks_options &o = ctx->opt;
+    const double conv = o.coords_in_angstrom ? 1.0 / 0.52917721092 : 1.0;
+    rks_batch *b = new rks_batch();
+    b->ctx = ctx;
+    b->nmol = nmol;
+    b->precision = o.precision;
+    b->hm.resize(nmol);
+    b->md.resize(nmol);
+    const int nang = o.n_theta * o.n_phi, npa = o.n_rad * nang;
+    // ---- host shell model
+    std::vector<int> hZ, hsh_atom, hsh_l, hsh_ao0, hcand_mol;
+    std::vector<double> haxyz, hsh_xyz, hsh_ex, hsh_co;
+    std::vector<int2> hcand;
+    std::vector<int> hblk_mol;
+    long long atom_off = 0, sh_off = 0, pair_off = 0, pts_off = 0, eri_off = 0, mat_off = 0, acc_off = 0;
+    for (int m = 0; m < nmol; m++) {
+        const int na = natom[m];
+        const int32_t *Zm = Z + atom_off;
+        const double *Xm = xyz + 3 * atom_off;
+        int nbf = 0;
+        int rc = validate(na, Zm, Xm, &nbf);
+        if (rc) {
+            delete b;
+            return fail(rc, "molecule " + std::to_string(m) + ": " + g_err);
+        }
+        int nel = 0;
+        for (int i = 0; i < na; i++) nel += Zm[i];
+        // shells in AO order, then reorder: s first, then p (stable)
+        struct Sh { int atom, l, ao0; const ShellDef *sd; };
+        std::vector<Sh> ao;
+        int aoi = 0;
+        for (int i = 0; i < na; i++) {
+            const ElemDef *E = elem_of(Zm[i]);
+            for (int s = 0; s < E->nsh; s++) {
+                ao.push_back({i, E->sh[s].l, aoi, &E->sh[s]});
+                aoi += E->sh[s].l ? 3 : 1;
+            }
+        }
+        std::vector<Sh> sh;
+        for (int l = 0; l <= 1; l++)
+            for (auto &x : ao)
+                if (x.l == l) sh.push_back(x);
+        const int nsh = (int)sh.size();
+        for (auto &x : sh) {
+            hsh_atom.push_back(x.atom);
+            hsh_l.push_back(x.l);
+            hsh_ao0.push_back(x.ao0);
+            for (int k = 0; k < 3; k++) {
+                hsh_xyz.push_back(Xm[3 * x.atom + k] * conv);
+                hsh_ex.push_back(x.sd->e[k]);
+                hsh_co.push_back(x.sd->c[k]);
+            }
+        }
+        for (int i = 0; i < na; i++) {
+            hZ.push_back(Zm[i]);
+            for (int k = 0; k < 3; k++) haxyz.push_back(Xm[3 * i + k] * conv);
+        }
+        // candidate pairs ordered by (l_P + l_Q, P, Q)
+        std::vector<int2> pr;
+        for (int cls = 0; cls <= 2; cls++)
+            for (int P = 0; P < nsh; P++)
+                for (int Q = 0; Q <= P; Q++)
+                    if (sh[P].l + sh[Q].l == cls) pr.push_back(make_int2(P, Q));
+        const int npair_all = (int)pr.size();
+        // unscreened store bound: sum over rows r of n_r * sum_{s <= r} n_s
+        long long cap = 0, pref = 0;
+        for (auto &p : pr) {
+            long long nr = (long long)(sh[p.x].l ? 3 : 1) * (sh[p.y].l ? 3 : 1);
+            pref += nr;
+            cap += nr * pref;
+        }
+        for (auto &p : pr) {
+            hcand.push_back(p);
+            hcand_mol.push_back(m);
+        }
+        const int npts = na * npa;
+        const int nblk = (npts + RKS_PTS_BLOCK - 1) / RKS_PTS_BLOCK;
+        for (int k = 0; k < nblk; k++) hblk_mol.push_back(m);
+        MolDesc &d = b->md[m];
+        d.natom = na; d.nbf = nbf; d.nocc = nel / 2; d.nsh = nsh;
+        d.atom0 = (int)atom_off; d.sh0 = (int)sh_off; d.npair_all = npair_all; d.pair0 = (int)pair_off;
+        d.npts = npts; d.nblk = nblk; d.pts0 = pts_off;
+        d.eri0 = eri_off; d.eri_cap = cap;
+        d.mat0 = mat_off; d.acc0 = acc_off;
+        b->hm[m] = {na, nbf, nel / 2, nsh, npair_all, cap, npts};
+        b->max_nbf = std::max(b->max_nbf, nbf);
+        b->max_nsh = std::max(b->max_nsh, nsh);
+        b->max_atoms = std::max(b->max_atoms, na);
+        atom_off += na;
+        sh_off += nsh;
+        pair_off += npair_all;
+        pts_off += (long long)nblk * RKS_PTS_BLOCK;
+        eri_off += (cap + 3) & ~3LL;  // keep every molecule's store 16-byte aligned
+        mat_off += (long long)M_COUNT * nbf * nbf;
+        acc_off += 3LL * nbf * nbf;
+    }
+    b->ncand = pair_off;
+    b->nblk_total = pts_off / RKS_PTS_BLOCK;
+    // ---- device buffers
+    DevBatch &d = b->d;
+    d.nmol = nmol;
+    d.precision = o.precision;
+    d.xc = o.xc;
+    d.a0 = o.xc ? 0.2 : 1.0;
+    d.n_rad = o.n_rad; d.n_theta = o.n_theta; d.n_phi = o.n_phi; d.becke_iters = o.becke_iters;
+    d.diis_space = std::max(1, std::min(o.diis_space, RKS_DIIS_MAX));
+    d.fixed_iters = o.fixed_iters;
+    d.max_iters = o.max_iters;
+    d.e_tol = o.e_tol;
+    d.err_tol = o.err_tol;
+    d.boys64 = ctx->boys64;
+    d.boys32 = ctx->boys32;
+    const size_t esz = o.precision ? sizeof(float) : sizeof(double);
+    int rc = 0;
+    MolDesc *dmol; MolState *dst; int *dZ, *dsa, *dsl, *dsao, *dcm, *dnp, *drnq; double *dax, *dsx, *dse, *dsc, *dcq, *dkq;
+    int2 *dcand, *dkp; long long *droff; void *store; void *gx, *gy, *gz, *gw; double *mat, *accd; float *accf;
+    if ((rc = dalloc(b, &dmol, nmol)) || (rc = dalloc(b, &dst, nmol)) || (rc = dalloc(b, &dZ, atom_off)) ||
+        (rc = dalloc(b, &dax, 3 * atom_off)) || (rc = dalloc(b, &dsa, sh_off)) || (rc = dalloc(b, &dsl, sh_off)) ||
+        (rc = dalloc(b, &dsao, sh_off)) || (rc = dalloc(b, &dsx, 3 * sh_off)) || (rc = dalloc(b, &dse, 3 * sh_off)) ||
+        (rc = dalloc(b, &dsc, 3 * sh_off)) || (rc = dalloc(b, &dcand, pair_off)) || (rc = dalloc(b, &dcm, pair_off)) ||
+        (rc = dalloc(b, &dcq, pair_off)) || (rc = dalloc(b, &dkp, pair_off)) || (rc = dalloc(b, &dkq, pair_off)) ||
+        (rc = dalloc(b, &dnp, nmol)) || (rc = dalloc(b, &drnq, pair_off)) || (rc = dalloc(b, &droff, pair_off + nmol)) ||
+        (rc = dalloc(b, (unsigned char **)&store, eri_off * esz)) ||
+        (rc = dalloc(b, (unsigned char **)&gx, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gy, pts_off * esz)) ||
+        (rc = dalloc(b, (unsigned char **)&gz, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gw, pts_off * esz)) ||
+        (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) || (rc = dalloc(b, &accf, acc_off)) ||
+        (rc = dalloc(b, &b->blk_mol, b->nblk_total))) {
+        rks_batch_destroy(b);
+        return rc;
+    }
+    d.mol = dmol; d.st = dst; d.Z = dZ; d.axyz = dax; d.sh_atom = dsa; d.sh_l = dsl; d.sh_ao0 = dsao;
+    d.sh_xyz = dsx; d.sh_ex = dse; d.sh_co = dsc; d.cand = dcand; d.cand_mol = dcm; d.cand_q = dcq;
+    d.kpair = dkp; d.kq = dkq; d.npair = dnp; d.row_nq = drnq; d.row_off = droff; d.store = store;
+    d.gx = gx; d.gy = gy; d.gz = gz; d.gw = gw; d.mat = mat; d.accd = accd; d.accf = accf;
+    cudaStream_t s = ctx->stream;
+#define UP(dst_, src_)                                                                                      \
+    if (!(src_).empty()) {                                                                                  \
+        cudaError_t e_ = cudaMemcpyAsync(dst_, (src_).data(), (src_).size() * sizeof((src_)[0]),          \
+                                         cudaMemcpyHostToDevice, s);                                        \
+        if (e_ != cudaSuccess) { rks_batch_destroy(b); return rks_cuda_fail(e_, "H2D", __FILE__, __LINE__); } \
+    }
+    UP(dmol, b->md);
+    UP(dZ, hZ);
+    UP(dax, haxyz);
+    UP(dsa, hsh_atom);
+    UP(dsl, hsh_l);
+    UP(dsao, hsh_ao0);
+    UP(dsx, hsh_xyz);
+    UP(dse, hsh_ex);
+    UP(dsc, hsh_co);
+    UP(dcand, hcand);
+    UP(dcm, hcand_mol);
+    UP(b->blk_mol, hblk_mol);
+#undef UP
+    cudaError_t e = cudaMemsetAsync(dst, 0, sizeof(MolState) * nmol, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mat, 0, sizeof(double) * mat_off, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        rks_batch_destroy(b);
+        return rks_cuda_fail(e, "batch upload", __FILE__, __LINE__);
+    }
+    *out = b;
+    return RKS_OK;
+}
+
+// -------------------------------------------------------------- stages
+static int check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rks_cuda_fail(e, what, __FILE__, __LINE__);
+    return RKS_OK;
+}
+
+extern "C" int rks_batch_setup(rks_batch *b) {
+    if (!b) return RKS_EINVAL;
+    rks_ctx *c = b->ctx;
+    cudaStream_t s = c->stream;
+    const DevBatch &d = b->d;
+    const int fp32 = b->precision;
+    { StageScope sc(c, "onee", 0); launch_onee(d, (int)b->ncand, s); }
+    { StageScope sc(c, "schwarz", 0); launch_schwarz(d, (int)b->ncand, s); }
+    { StageScope sc(c, "pairs", 0); launch_compact_pairs(d, s); }
+    { StageScope sc(c, "row_count", 0); launch_row_count(d, (int)b->ncand, s); }
+    { StageScope sc(c, "row_scan", 0); launch_row_scan(d, s); }
+    { StageScope sc(c, "eri", 0); launch_eri_store(d, (int)b->ncand, fp32, s); }
+    { StageScope sc(c, "grid_build", 0); launch_grid_build(d, b->nblk_total, b->blk_mol, c->rad, c->ang, b->max_atoms, s); }
+    { StageScope sc(c, "scf_init", 0); launch_scf_init(d, s); }
+    { StageScope sc(c, "scf_guess", 0); launch_scf_guess(d, s); }
+    int rc = check_launch("setup kernels");
+    if (rc) return rc;
+    b->set_up = true;
+    b->st_valid = false;
+    return RKS_OK;
+}
+
+// One Fock build for every (active when mode 0) molecule.
+static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
+    rks_ctx *c = b->ctx;
+    cudaStream_t s = c->stream;
+    const DevBatch &d = b->d;
+    long long acc_elems = 0;
+    for (auto &m : b->md) acc_elems += 3LL * m.nbf * m.nbf;
+    if (acc_fp64 || b->precision == 0) CUDA_OK(cudaMemsetAsync(d.accd, 0, sizeof(double) * acc_elems, s));
+    else CUDA_OK(cudaMemsetAsync(d.accf, 0, sizeof(float) * acc_elems, s));
+    launch_reset_exc(d, s);
+    const int nchunk_jk = 8;
+    { StageScope sc(c, acc_fp64 ? "jk_final" : "jk", 0); launch_jk(d, nchunk_jk, acc_fp64, mode, b->max_nbf, s); }
+    if (d.xc) {
+        const int nchunk_gx = 16;
+        StageScope sc(c, acc_fp64 ? "grid_xc_final" : "grid_xc", 0);
+        launch_grid_xc(d, nchunk_gx, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
+    }
+    return check_launch("fock pass");
+}
+
+static int count_active(rks_batch *b, int *n_active) {
+    b->st_host.resize(b->nmol);
+    CUDA_OK(cudaMemcpyAsync(b->st_host.data(), b->d.st, sizeof(MolState) * b->nmol, cudaMemcpyDeviceToHost,
+                            b->ctx->stream));
+    CUDA_OK(cudaStreamSynchronize(b->ctx->stream));
+    int n = 0;
+    for (auto &st : b->st_host) n += st.active;
+    *n_active = n;
+    return RKS_OK;
+}
+
+extern "C" int rks_batch_run(rks_batch *b) {
+    if (!b) return RKS_EINVAL;
+    rks_ctx *c = b->ctx;
+    auto t0 = std::chrono::steady_clock::now();
+    int rc;
+    if (!b->set_up && (rc = rks_batch_setup(b))) return rc;
+    const DevBatch &d = b->d;
+    const int fp64_iter = b->precision == 0;
+    if (d.fixed_iters > 0) {
+        for (int it = 0; it < d.fixed_iters; it++) {
+            if ((rc = fock_pass(b, fp64_iter, 0))) return rc;
+            StageScope sc(c, "scf_step", 0);
+            launch_scf_step(d, fp64_iter, c->stream);
+        }
+    } else {
+        for (int it = 0; it < d.max_iters; it++) {
+            if ((rc = fock_pass(b, fp64_iter, 0))) return rc;
+            {
+                StageScope sc(c, "scf_step", 0);
+                launch_scf_step(d, fp64_iter, c->stream);
+            }
+            if ((rc = check_launch("scf step"))) return rc;
+            if (it % 4 == 3 || it == d.max_iters - 1) {
+                int na = 0;
+                if ((rc = count_active(b, &na))) return rc;
+                if (na == 0) break;
+            }
+        }
+    }
+    // final step: every molecule, FP64 accumulation
+    if ((rc = fock_pass(b, 1, 1))) return rc;
+    {
+        StageScope sc(c, "scf_final", 0);
+        launch_scf_final(d, 1, c->stream);
+    }
+    if ((rc = check_launch("final"))) return rc;
+    b->st_valid = false;
+    b->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return RKS_OK;
+}
+
+extern "C" int rks_batch_sync(rks_batch *b) {
+    if (!b) return RKS_EINVAL;
+    CUDA_OK(cudaStreamSynchronize(b->ctx->stream));
+    b->st_host.resize(b->nmol);
+    CUDA_OK(cudaMemcpy(b->st_host.data(), b->d.st, sizeof(MolState) * b->nmol, cudaMemcpyDeviceToHost));
+    b->st_valid = true;
+    for (auto &st : b->st_host)
+        if (st.err_flag) return fail(RKS_EDEVICE, "device-side consistency flag set");
+    return RKS_OK;
+}
+
+extern "C" int rks_batch_fock(rks_batch *b, const double *D_all, int32_t final_step) {
+    if (!b || !D_all) return RKS_EINVAL;
+    int rc;
+    if (!b->set_up && (rc = rks_batch_setup(b))) return rc;
+    long long off = 0;
+    for (int m = 0; m < b->nmol; m++) {
+        const MolDesc &md = b->md[m];
+        long long nn = (long long)md.nbf * md.nbf;
+        CUDA_OK(cudaMemcpyAsync(b->d.mat + md.mat0 + (long long)M_D * nn, D_all + off, nn * sizeof(double),
+                                cudaMemcpyHostToDevice, b->ctx->stream));
+        off += nn;
+    }
+    const int acc64 = final_step || b->precision == 0;
+    if ((rc = fock_pass(b, acc64, 1))) return rc;
+    launch_fock_only(b->d, acc64, b->ctx->stream);
+    b->st_valid = false;
+    return check_launch("fock only");
+}
+
+static int ensure_state(rks_batch *b) {
+    if (b->st_valid) return RKS_OK;
+    return rks_batch_sync(b);
+}
+
+static double paper_std(const MolState &st) {
+    int n = std::min(st.iter, 5);
+    if (n < 5) return 1e30;
+    double mean = 0, v = 0;
+    for (int k = st.iter - 5; k < st.iter; k++) mean += st.Ehist[k % RKS_NHIST];
+    mean /= 5;
+    for (int k = st.iter - 5; k < st.iter; k++) v += pow(st.Ehist[k % RKS_NHIST] - mean, 2);
+    return sqrt(v / 5);
+}
+
+extern "C" int rks_batch_result(rks_batch *b, int32_t m, rks_result_t *out, double *eps_out, double *D_out,
+                                int32_t cap_nbf) {
+    if (!b || m < 0 || m >= b->nmol || !out) return RKS_EINVAL;
+    int rc = ensure_state(b);
+    if (rc && rc != RKS_EDEVICE) return rc;
+    const MolState &st = b->st_host[m];
+    const MolDesc &md = b->md[m];
+    if ((eps_out || D_out) && cap_nbf < md.nbf) return fail(RKS_EINVAL, "cap_nbf smaller than nbf");
+    memset(out, 0, sizeof *out);
+    out->status = st.status;
+    if (b->d.fixed_iters == 0 && !st.converged && st.status == RKS_STATUS_OK) out->status = RKS_STATUS_NOT_CONVERGED;
+    out->nbf = md.nbf;
+    out->n_occ = md.nocc;
+    out->iters = st.iter;
+    out->e_total = st.E;
+    out->e_homo = st.eps_homo;
+    out->e_lumo = st.eps_lumo;
+    out->gap = st.eps_lumo - st.eps_homo;
+    out->e_xc = st.Exc;
+    out->e_nuc = st.Enuc;
+    out->latency_s = b->wall_s;
+    out->paper_converged = paper_std(st) < 0.01;
+    if (eps_out) memcpy(eps_out, st.eps, sizeof(double) * md.nbf);
+    if (D_out) {
+        long long nn = (long long)md.nbf * md.nbf;
+        CUDA_OK(cudaMemcpy(D_out, b->d.mat + md.mat0 + (long long)M_D * nn, nn * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+    }
+    return RKS_OK;
+}
+
+extern "C" int64_t rks_batch_dump(rks_batch *b, int32_t m, int32_t what, void *out, int64_t cap) {
+    if (!b || m < 0 || m >= b->nmol || !out) return RKS_EINVAL;
+    CUDA_OK(cudaStreamSynchronize(b->ctx->stream));
+    const MolDesc &md = b->md[m];
+    const DevBatch &d = b->d;
+    const long long nn = (long long)md.nbf * md.nbf;
+    MolState st;
+    CUDA_OK(cudaMemcpy(&st, d.st + m, sizeof st, cudaMemcpyDeviceToHost));
+    int npair = 0;
+    CUDA_OK(cudaMemcpy(&npair, d.npair + m, sizeof(int), cudaMemcpyDeviceToHost));
+    auto mat_dump = [&](int slot) -> int64_t {
+        int64_t bytes = nn * sizeof(double);
+        if (cap < bytes) return RKS_EINVAL;
+        cudaError_t e = cudaMemcpy(out, d.mat + md.mat0 + (long long)slot * nn, bytes, cudaMemcpyDeviceToHost);
+        return e == cudaSuccess ? bytes : (int64_t)rks_cuda_fail(e, "dump", __FILE__, __LINE__);
+    };
+    switch (what) {
+    case RKS_DUMP_PAIRS: {
+        int64_t bytes = (int64_t)npair * 8;
+        if (cap < bytes) return RKS_EINVAL;
+        CUDA_OK(cudaMemcpy(out, d.kpair + md.pair0, bytes, cudaMemcpyDeviceToHost));
+        return bytes;
+    }
+    case RKS_DUMP_PAIR_Q: {
+        int64_t bytes = (int64_t)npair * 8;
+        if (cap < bytes) return RKS_EINVAL;
+        CUDA_OK(cudaMemcpy(out, d.kq + md.pair0, bytes, cudaMemcpyDeviceToHost));
+        return bytes;
+    }
+    case RKS_DUMP_ROW_OFF: {
+        int64_t bytes = (int64_t)(npair + 1) * 8;
+        if (cap < bytes) return RKS_EINVAL;
+        CUDA_OK(cudaMemcpy(out, d.row_off + md.pair0 + m, bytes, cudaMemcpyDeviceToHost));
+        return bytes;
+    }
+    case RKS_DUMP_QUARTETS: {
+        int64_t bytes = (int64_t)npair * 4;
+        if (cap < bytes) return RKS_EINVAL;
+        CUDA_OK(cudaMemcpy(out, d.row_nq + md.pair0, bytes, cudaMemcpyDeviceToHost));
+        return bytes;
+    }
+    case RKS_DUMP_STORE: {
+        long long n = st.n_elem;
+        int64_t bytes = n * 8;
+        if (cap < bytes) return RKS_EINVAL;
+        if (b->precision) {
+            std::vector<float> tmp(n);
+            CUDA_OK(cudaMemcpy(tmp.data(), (float *)d.store + md.eri0, n * 4, cudaMemcpyDeviceToHost));
+            for (long long i = 0; i < n; i++) ((double *)out)[i] = tmp[i];
+        } else {
+            CUDA_OK(cudaMemcpy(out, (double *)d.store + md.eri0, bytes, cudaMemcpyDeviceToHost));
+        }
+        return bytes;
+    }
+    case RKS_DUMP_S: return mat_dump(M_S);
+    case RKS_DUMP_T: return mat_dump(M_T);
+    case RKS_DUMP_V: return mat_dump(M_V);
+    case RKS_DUMP_J: return mat_dump(M_J);
+    case RKS_DUMP_K: return mat_dump(M_K);
+    case RKS_DUMP_VXC: return mat_dump(M_VXC);
+    case RKS_DUMP_D: return mat_dump(M_D);
+    case RKS_DUMP_F: return mat_dump(M_F);
+    case RKS_DUMP_X: return mat_dump(M_X);
+    case RKS_DUMP_EPS: {
+        int64_t bytes = md.nbf * 8;
+        if (cap < bytes) return RKS_EINVAL;
+        memcpy(out, st.eps, bytes);
+        return bytes;
+    }
+    case RKS_DUMP_GRID: {
+        int64_t bytes = (int64_t)md.npts * 32;
+        if (cap < bytes) return RKS_EINVAL;
+        const size_t esz = b->precision ? 4 : 8;
+        std::vector<unsigned char> t(md.npts * esz);
+        void *src[4] = {d.gx, d.gy, d.gz, d.gw};
+        for (int k = 0; k < 4; k++) {
+            CUDA_OK(cudaMemcpy(t.data(), (unsigned char *)src[k] + md.pts0 * esz, md.npts * esz, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < md.npts; i++)
+                ((double *)out)[4 * i + k] = esz == 4 ? (double)((float *)t.data())[i] : ((double *)t.data())[i];
+        }
+        return bytes;
+    }
+    case RKS_DUMP_SCALARS: {
+        if (cap < 64) return RKS_EINVAL;
+        double *o = (double *)out;
+        o[0] = st.E; o[1] = st.Exc; o[2] = st.Enuc; o[3] = md.npair_all; o[4] = st.n_quartets;
+        o[5] = (double)st.n_elem; o[6] = md.npts; o[7] = st.near_ties;
+        return 64;
+    }
+    default: return RKS_EINVAL;
+    }
+}
+
+// -------------------------------------------------------- unit entries
+extern "C" int rks_eval_boys(rks_ctx *ctx, int32_t mmax, int32_t n, const double *T, double *out, int32_t precision) {
+    if (!ctx || n <= 0 || !T || !out || mmax < 0 || mmax > 4) return RKS_EINVAL;
+    double *dT, *dO;
+    CUDA_OK(cudaMalloc(&dT, n * sizeof(double)));
+    CUDA_OK(cudaMalloc(&dO, (size_t)n * (mmax + 1) * sizeof(double)));
+    CUDA_OK(cudaMemcpy(dT, T, n * sizeof(double), cudaMemcpyHostToDevice));
+    launch_boys_eval(mmax, n, dT, dO, precision == RKS_MIXED, ctx->boys64, ctx->boys32, ctx->stream);
+    CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    CUDA_OK(cudaMemcpy(out, dO, (size_t)n * (mmax + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    cudaFree(dT);
+    cudaFree(dO);
+    return RKS_OK;
+}
+
+extern "C" int rks_eval_xc(rks_ctx *ctx, int32_t n, const double *rho, const double *sigma, double *e, double *vr,
+                           double *vs, int32_t precision) {
+    if (!ctx || n <= 0 || !rho || !sigma || !e || !vr || !vs) return RKS_EINVAL;
+    double *dr, *ds, *dO;
+    CUDA_OK(cudaMalloc(&dr, n * sizeof(double)));
+    CUDA_OK(cudaMalloc(&ds, n * sizeof(double)));
+    CUDA_OK(cudaMalloc(&dO, 3ull * n * sizeof(double)));
+    CUDA_OK(cudaMemcpy(dr, rho, n * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpy(ds, sigma, n * sizeof(double), cudaMemcpyHostToDevice));
+    launch_eval_xc(n, dr, ds, dO, precision == RKS_MIXED, ctx->stream);
+    CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    std::vector<double> o(3ull * n);
+    CUDA_OK(cudaMemcpy(o.data(), dO, 3ull * n * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; i++) {
+        e[i] = o[3 * i];
+        vr[i] = o[3 * i + 1];
+        vs[i] = o[3 * i + 2];
+    }
+    cudaFree(dr);
+    cudaFree(ds);
+    cudaFree(dO);
+    return RKS_OK;
+}
+
+// ----------------------------------------------------- serving worker
+// Admits queued tickets into a batch (up to max_slots), runs it, and
+// publishes the results; molecules arriving meanwhile wait for the next batch.
+static void worker_main(rks_ctx *c) {
+    cudaSetDevice(c->opt.device);
+    for (;;) {
+        std::vector<uint64_t> ids;
+        {
+            std::unique_lock<std::mutex> lk(c->mu);
+            c->cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+            if (c->stop) break;
+            while (!c->queue.empty() && (int)ids.size() < c->opt.max_slots) {
+                ids.push_back(c->queue.front());
+                c->queue.pop_front();
+            }
+            for (auto id : ids) c->tickets[id].state = RKS_RUNNING;
+        }
+        std::vector<int32_t> na, Z;
+        std::vector<double> xyz;
+        {
+            std::lock_guard<std::mutex> lk(c->mu);
+            for (auto id : ids) {
+                Ticket &t = c->tickets[id];
+                na.push_back((int)t.Z.size());
+                Z.insert(Z.end(), t.Z.begin(), t.Z.end());
+                xyz.insert(xyz.end(), t.xyz.begin(), t.xyz.end());
+            }
+        }
+        rks_batch *b = nullptr;
+        int rc = rks_batch_create(c, (int)ids.size(), na.data(), Z.data(), xyz.data(), &b);
+        if (!rc) rc = rks_batch_run(b);
+        if (!rc) rc = rks_batch_sync(b);
+        std::lock_guard<std::mutex> lk(c->mu);
+        auto now = std::chrono::steady_clock::now();
+        for (size_t k = 0; k < ids.size(); k++) {
+            Ticket &t = c->tickets[ids[k]];
+            if (rc && rc != RKS_EDEVICE) {
+                t.state = RKS_FAILED;
+                continue;
+            }
+            int nbf = b->md[k].nbf;
+            t.eps.resize(nbf);
+            t.D.resize((size_t)nbf * nbf);
+            rks_batch_result(b, (int)k, &t.res, t.eps.data(), t.D.data(), nbf);
+            t.res.latency_s = std::chrono::duration<double>(now - t.t_submit).count();
+            t.state = RKS_DONE;
+        }
+        if (b) rks_batch_destroy(b);
+        c->cv_done.notify_all();
+    }
+}
+
+extern "C" int rks_create(const rks_options *options, rks_ctx **out) {
+    if (!out) return RKS_EINVAL;
+    std::call_once(g_basis_once, init_basis);
+    rks_options o;
+    if (options) o = *options; else rks_options_default(&o);
+    if (o.basis != 0 || o.n_rad <= 0 || o.n_theta <= 0 || o.n_theta > 64 || o.n_phi <= 0 || o.becke_iters < 0 ||
+        (o.precision != RKS_FP64 && o.precision != RKS_MIXED) || o.max_iters <= 0 || o.max_slots <= 0)
+        return fail(RKS_EINVAL, "bad options");
+    int ndev = 0;
+    CUDA_OK(cudaGetDeviceCount(&ndev));
+    if (o.device < 0 || o.device >= ndev) return fail(RKS_EINVAL, "no such device");
+    CUDA_OK(cudaSetDevice(o.device));
+    rks_ctx *c = new rks_ctx();
+    c->opt = o;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->boys64, sizeof(double) * BOYS_N64 * BOYS_COL64);
+    if (e == cudaSuccess) e = cudaMalloc(&c->boys32, sizeof(float) * BOYS_N32 * BOYS_COL32);
+    if (e == cudaSuccess) e = cudaMalloc(&c->rad, sizeof(double) * 5 * o.n_rad * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&c->ang, sizeof(double) * o.n_theta * o.n_phi * 4);
+    if (e != cudaSuccess) {
+        delete c;
+        return rks_cuda_fail(e, "context allocation", __FILE__, __LINE__);
+    }
+    launch_boys_table(c->boys64, c->boys32, c->stream);
+    launch_quad_tables(c->rad, c->ang, o.n_rad, o.n_theta, o.n_phi, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        delete c;
+        return rks_cuda_fail(e, "context tables", __FILE__, __LINE__);
+    }
+    c->worker = std::thread(worker_main, c);
+    *out = c;
+    return RKS_OK;
+}
+
+extern "C" int rks_destroy(rks_ctx *c) {
+    if (!c) return RKS_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->stop = true;
+        for (auto id : c->queue) c->tickets[id].state = RKS_FAILED;
+        c->queue.clear();
+    }
+    c->cv.notify_all();
+    if (c->worker.joinable()) c->worker.join();
+    cudaStreamSynchronize(c->stream);
+    for (auto &r : c->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    cudaFree(c->boys64);
+    cudaFree(c->boys32);
+    cudaFree(c->rad);
+    cudaFree(c->ang);
+    cudaStreamDestroy(c->stream);
+    delete c;
+    return RKS_OK;
+}
+
+extern "C" int rks_submit(rks_ctx *c, int32_t natom, const int32_t *Z, const double *xyz, uint64_t *ticket_out) {
+    if (!c || !ticket_out) return RKS_EINVAL;
+    int rc = validate(natom, Z, xyz, nullptr);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->queue.size() >= c->queue_cap) return RKS_EAGAIN;
+    uint64_t id = c->next_ticket++;
+    Ticket &t = c->tickets[id];
+    t.Z.assign(Z, Z + natom);
+    t.xyz.assign(xyz, xyz + 3 * natom);
+    t.t_submit = std::chrono::steady_clock::now();
+    c->queue.push_back(id);
+    *ticket_out = id;
+    c->cv.notify_one();
+    return RKS_OK;
+}
+
+extern "C" int rks_poll(rks_ctx *c, uint64_t ticket, int32_t *state_out) {
+    if (!c || !state_out) return RKS_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->tickets.find(ticket);
+    if (it == c->tickets.end()) return RKS_ENOTFOUND;
+    *state_out = it->second.state;
+    return RKS_OK;
+}
+
+extern "C" int rks_wait(rks_ctx *c, uint64_t ticket, double timeout_s) {
+    if (!c) return RKS_EINVAL;
+    std::unique_lock<std::mutex> lk(c->mu);
+    auto done = [&] {
+        auto it = c->tickets.find(ticket);
+        return it == c->tickets.end() || it->second.state == RKS_DONE || it->second.state == RKS_FAILED;
+    };
+    if (!c->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done)) return RKS_ETIMEOUT;
+    if (c->tickets.find(ticket) == c->tickets.end()) return RKS_ENOTFOUND;
+    return RKS_OK;
+}
+
+extern "C" int rks_result(rks_ctx *c, uint64_t ticket, rks_result_t *out, double *eps_out, double *D_out,
+                          int32_t cap_nbf) {
+    if (!c || !out) return RKS_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->tickets.find(ticket);
+    if (it == c->tickets.end()) return RKS_ENOTFOUND;
+    Ticket &t = it->second;
+    if (t.state == RKS_FAILED) {
+        c->tickets.erase(it);
+        return fail(RKS_ECUDA, "ticket failed");
+    }
+    if (t.state != RKS_DONE) return RKS_ENOTREADY;
+    if ((eps_out || D_out) && cap_nbf < t.res.nbf) return RKS_EINVAL;
+    *out = t.res;
+    if (eps_out) memcpy(eps_out, t.eps.data(), sizeof(double) * t.eps.size());
+    if (D_out) memcpy(D_out, t.D.data(), sizeof(double) * t.D.size());
+    c->tickets.erase(it);
+    return RKS_OK;
+}

@@ -1,0 +1,206 @@
+// Exchange-correlation quadrature on the molecular grid: AO values and
+// gradients, density and its gradient, the B3LYP kernel, and the V_xc matrix.
+//
+// Paper: V_xc(rho) in Eq. 1 (Section 3.1), B3LYP only (Section 3.2), AO values
+// recomputed on the grid instead of stored (Section 6, "Recomputation").
+//   rho_p = sum_mn phi_pm D_mn phi_pn,  grad rho_p = 2 sum_mn grad phi_pm D_mn phi_pn,
+//   E_xc = sum_p w_p e(rho_p, sigma_p),
+//   V_xc = V' + V'^T,  V'_mn = sum_p phi_pm X_pn,
+//   X_pn = w_p (v_rho/2 phi_pn + 2 v_sigma grad rho_p . grad phi_pn).
+//
+// One thread block owns one molecule's share of grid blocks (grid (nchunk,
+// nmol)); per sub-block of BP points it evaluates every AO into shared memory,
+// forms rho (G threads per point, shuffle-reduced), runs the functional, builds
+// X, and accumulates V' in a per-thread register tile (16 x 16 threads, TILE x
+// TILE entries each).  V' and E_xc leave the block once, at the end.
+#include "common.cuh"
+#include "kernels.h"
+#include "xc.cuh"
+#include "boys.cuh"
+
+template <typename T, typename TA, int BP, int TILE>
+__global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk, int mode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = blockIdx.y, chunk = blockIdx.x;
+    const MolDesc md = b.mol[m];
+    if (mode == 0 && !b.st[m].active) return;
+    const int n = md.nbf, nsh = md.nsh;
+    const int XS = n | 1;  // odd row stride of X (bank-conflict free both ways)
+    T *Ds = (T *)smem_raw;                 // [n][n]
+    T *phi = Ds + n * n;                   // [4][n][BP]
+    T *Xs = phi + 4 * n * BP;              // [BP][XS]
+    T *pt = Xs + BP * XS;                  // [4][BP] x y z w
+    T *cf = pt + 4 * BP;                   // [4][BP] coefficients
+    T *shd = cf + 4 * BP;                  // [nsh][8]: x y z e0 e1 e2 (c's below)
+    T *shc = shd + nsh * 8;                // [nsh][4]: c0 c1 c2 -
+    int *shi = (int *)(shc + nsh * 4);     // [nsh][2]: l, ao0
+    const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ds[i] = (T)D[i];
+    for (int s = threadIdx.x; s < nsh; s += blockDim.x) {
+        int g = md.sh0 + s;
+        for (int k = 0; k < 3; k++) {
+            shd[s * 8 + k] = (T)b.sh_xyz[g * 3 + k];
+            shd[s * 8 + 3 + k] = (T)b.sh_ex[g * 3 + k];
+            shc[s * 4 + k] = (T)b.sh_co[g * 3 + k];
+        }
+        shi[s * 2] = b.sh_l[g];
+        shi[s * 2 + 1] = b.sh_ao0[g];
+    }
+    const int t = threadIdx.x;
+    const int ti = t >> 4, tj = t & 15;
+    TA acc[TILE][TILE];
+#pragma unroll
+    for (int a = 0; a < TILE; a++)
+#pragma unroll
+        for (int c = 0; c < TILE; c++) acc[a][c] = (TA)0;
+    double exc = 0.0;
+    constexpr int G = 256 / BP;  // threads per point in the density step
+    const T *gx = (const T *)b.gx + md.pts0, *gy = (const T *)b.gy + md.pts0;
+    const T *gz = (const T *)b.gz + md.pts0, *gw = (const T *)b.gw + md.pts0;
+    const int nsub = md.nblk * (RKS_PTS_BLOCK / BP);
+    __syncthreads();
+    for (int sb = chunk; sb < nsub; sb += nchunk) {
+        const long long p0 = (long long)sb * BP;
+        for (int i = t; i < BP; i += blockDim.x) {
+            pt[i] = gx[p0 + i];
+            pt[BP + i] = gy[p0 + i];
+            pt[2 * BP + i] = gz[p0 + i];
+            pt[3 * BP + i] = gw[p0 + i];
+        }
+        __syncthreads();
+        // ---- AO values and gradients: phi[0..3][mu][p]
+        for (int idx = t; idx < nsh * BP; idx += blockDim.x) {
+            const int s = idx / BP, p = idx % BP;
+            const T dx = pt[p] - shd[s * 8], dy = pt[BP + p] - shd[s * 8 + 1], dz = pt[2 * BP + p] - shd[s * 8 + 2];
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            T g = 0, gp = 0;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const T e = shc[s * 4 + k] * xc::exp_(-shd[s * 8 + 3 + k] * r2);
+                g += e;
+                gp -= (T)2 * shd[s * 8 + 3 + k] * e;
+            }
+            const int l = shi[s * 2], mu = shi[s * 2 + 1];
+            if (l == 0) {
+                phi[(0 * n + mu) * BP + p] = g;
+                phi[(1 * n + mu) * BP + p] = gp * dx;
+                phi[(2 * n + mu) * BP + p] = gp * dy;
+                phi[(3 * n + mu) * BP + p] = gp * dz;
+            } else {
+                const T d[3] = {dx, dy, dz};
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    phi[(0 * n + mu + c) * BP + p] = d[c] * g;
+#pragma unroll
+                    for (int x = 0; x < 3; x++)
+                        phi[((1 + x) * n + mu + c) * BP + p] = gp * d[c] * d[x] + (x == c ? g : (T)0);
+                }
+            }
+        }
+        __syncthreads();
+        // ---- density: G threads per point
+        {
+            const int p = t / G, gg = t % G;
+            T rho = 0, rx = 0, ry = 0, rz = 0;
+            for (int nu = gg; nu < n; nu += G) {
+                T tv = 0;
+                for (int mu = 0; mu < n; mu++) tv += phi[mu * BP + p] * Ds[mu * n + nu];
+                rho += tv * phi[nu * BP + p];
+                rx += tv * phi[(n + nu) * BP + p];
+                ry += tv * phi[(2 * n + nu) * BP + p];
+                rz += tv * phi[(3 * n + nu) * BP + p];
+            }
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                rho += __shfl_xor_sync(0xffffffffu, rho, o);
+                rx += __shfl_xor_sync(0xffffffffu, rx, o);
+                ry += __shfl_xor_sync(0xffffffffu, ry, o);
+                rz += __shfl_xor_sync(0xffffffffu, rz, o);
+            }
+            if (gg == 0) {
+                rx *= (T)2; ry *= (T)2; rz *= (T)2;
+                const T w = pt[3 * BP + p];
+                T e = 0, vr = 0, vs = 0;
+                if (w != (T)0) xc::b3lyp<T>(rho, rx * rx + ry * ry + rz * rz, e, vr, vs);
+                exc += (double)w * (double)e;
+                cf[p] = (T)0.5 * w * vr;
+                cf[BP + p] = (T)2 * w * vs * rx;
+                cf[2 * BP + p] = (T)2 * w * vs * ry;
+                cf[3 * BP + p] = (T)2 * w * vs * rz;
+            }
+        }
+        __syncthreads();
+        // ---- X[p][nu]
+        for (int idx = t; idx < n * BP; idx += blockDim.x) {
+            const int nu = idx / BP, p = idx % BP;
+            Xs[p * XS + nu] = cf[p] * phi[nu * BP + p] + cf[BP + p] * phi[(n + nu) * BP + p] +
+                              cf[2 * BP + p] * phi[(2 * n + nu) * BP + p] + cf[3 * BP + p] * phi[(3 * n + nu) * BP + p];
+        }
+        __syncthreads();
+        // ---- V'[mu][nu] += sum_p phi[mu][p] X[p][nu]
+        for (int p = 0; p < BP; p++) {
+            T fa[TILE], xb[TILE];
+#pragma unroll
+            for (int a = 0; a < TILE; a++) {
+                const int mu = ti + 16 * a;
+                fa[a] = mu < n ? phi[mu * BP + p] : (T)0;
+            }
+#pragma unroll
+            for (int c = 0; c < TILE; c++) {
+                const int nu = tj + 16 * c;
+                xb[c] = nu < n ? Xs[p * XS + nu] : (T)0;
+            }
+#pragma unroll
+            for (int a = 0; a < TILE; a++)
+#pragma unroll
+                for (int c = 0; c < TILE; c++) acc[a][c] += (TA)(fa[a] * xb[c]);
+        }
+        __syncthreads();
+    }
+    // ---- flush V' and E_xc
+    TA *gV;
+    if constexpr (sizeof(TA) == 8) gV = (TA *)(b.accd + md.acc0) + 2 * n * n;
+    else gV = (TA *)(b.accf + md.acc0) + 2 * n * n;
+#pragma unroll
+    for (int a = 0; a < TILE; a++)
+#pragma unroll
+        for (int c = 0; c < TILE; c++) {
+            const int mu = ti + 16 * a, nu = tj + 16 * c;
+            if (mu < n && nu < n && acc[a][c] != (TA)0) atomicAdd(&gV[mu * n + nu], acc[a][c]);
+        }
+    for (int o = 16; o > 0; o >>= 1) exc += __shfl_xor_sync(0xffffffffu, exc, o);
+    if ((t & 31) == 0 && exc != 0.0) atomicAdd(&b.st[m].Exc, exc);
+}
+
+template <typename T, typename TA, int BP, int TILE>
+static void launch_gx(const DevBatch &b, int nchunk, int mode, int max_nbf, int max_nsh, cudaStream_t s) {
+    const int n = max_nbf, XS = n | 1;
+    size_t sm = sizeof(T) * ((size_t)n * n + 4ull * n * BP + (size_t)BP * XS + 8ull * BP + 12ull * max_nsh) +
+                sizeof(int) * 2ull * max_nsh + 64;
+    cudaFuncSetAttribute(grid_xc_kernel<T, TA, BP, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    grid_xc_kernel<T, TA, BP, TILE><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode);
+}
+
+void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
+                    cudaStream_t s) {
+    if (b.precision == 0) launch_gx<double, double, 32, 6>(b, nchunk, mode, max_nbf, max_nsh, s);
+    else if (acc_fp64) launch_gx<float, double, 64, 6>(b, nchunk, mode, max_nbf, max_nsh, s);
+    else launch_gx<float, float, 64, 6>(b, nchunk, mode, max_nbf, max_nsh, s);
+}
+
+// --------------------------------------------------------- unit entry
+template <typename T>
+__global__ void eval_xc_kernel(int n, const double *rho, const double *sigma, double *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T e, vr, vs;
+    xc::b3lyp<T>((T)rho[i], (T)sigma[i], e, vr, vs);
+    out[3 * i] = e;
+    out[3 * i + 1] = vr;
+    out[3 * i + 2] = vs;
+}
+
+void launch_eval_xc(int n, const double *rho, const double *sigma, double *out, int fp32, cudaStream_t s) {
+    if (fp32) eval_xc_kernel<float><<<(n + 127) / 128, 128, 0, s>>>(n, rho, sigma, out);
+    else eval_xc_kernel<double><<<(n + 127) / 128, 128, 0, s>>>(n, rho, sigma, out);
+}

@@ -1,0 +1,211 @@
+// Coulomb and exchange contractions from the packed two-electron store
+// (paper Section 3.1, Eq. 1:  J_kl = sum_ij I_ijkl rho_ij,
+// K_il = -1/2 sum_jk I_ijkl rho_jk; here K_std_il = sum_jk (ij|kl) rho_jk is
+// accumulated and the -a0/2 factor is applied in the Fock assembly).
+//
+// The store holds one block per symmetry-distinct shell quartet (Section 3.2:
+// 8-fold symmetry cuts storage and J/K flops by 8).  Each stored element v of a
+// canonical quartet, scaled by 1/|stabiliser| (a factor 1/2 each for P = Q,
+// R = S and pq = rs), stands for its 8 permutations:
+//   J'_ij += 2 v D_kl,  J'_kl += 2 v D_ij,
+//   K'_ik += v D_jl,  K'_jk += v D_il,  K'_il += v D_jk,  K'_jl += v D_ik,
+// and J = J' + J'^T, K_std = K' + K'^T.
+//
+// The paper's IPU version replicated the density per thread and summed N^2
+// partial vectors at the end (Section 6, "Current (Naive) Bottleneck").  Here
+// one thread block owns one slice of one molecule's rows: D sits once in shared
+// memory, a warp walks one row pq (lanes take consecutive rs), the row-local
+// J'_PQ terms are reduced across the warp by shuffles, the scattered terms go
+// to shared-memory accumulators, and the block adds its J'/K' to the
+// molecule's global accumulators once at the end.
+#include "common.cuh"
+#include "kernels.h"
+
+#define TAU_SCHWARZ 1e-12
+
+template <typename TA> __device__ __forceinline__ void sh_add(TA *p, TA v) { atomicAdd(p, v); }
+
+template <typename TS, typename TA, int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void jk_block(const TS *__restrict__ v, TA scale, int a0, int b0, int c0, int d0,
+                                         const TA *Ds, TA *Js, TA *Ks, int n, TA *jpq) {
+    constexpr int na = LA ? 3 : 1, nb = LB ? 3 : 1, nc = LC ? 3 : 1, nd = LD ? 3 : 1;
+    TA Drs[nc][nd], Dpq[na][nb], Dqs[nb][nd], Dps[na][nd], Dqr[nb][nc], Dpr[na][nc];
+#pragma unroll
+    for (int k = 0; k < nc; k++)
+#pragma unroll
+        for (int l = 0; l < nd; l++) Drs[k][l] = Ds[(c0 + k) * n + d0 + l];
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int j = 0; j < nb; j++) Dpq[i][j] = Ds[(a0 + i) * n + b0 + j];
+#pragma unroll
+    for (int j = 0; j < nb; j++)
+#pragma unroll
+        for (int l = 0; l < nd; l++) Dqs[j][l] = Ds[(b0 + j) * n + d0 + l];
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int l = 0; l < nd; l++) Dps[i][l] = Ds[(a0 + i) * n + d0 + l];
+#pragma unroll
+    for (int j = 0; j < nb; j++)
+#pragma unroll
+        for (int k = 0; k < nc; k++) Dqr[j][k] = Ds[(b0 + j) * n + c0 + k];
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int k = 0; k < nc; k++) Dpr[i][k] = Ds[(a0 + i) * n + c0 + k];
+
+    TA jrs[nc][nd] = {}, kpr[na][nc] = {}, kqr[nb][nc] = {}, kps[na][nd] = {}, kqs[nb][nd] = {};
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int j = 0; j < nb; j++)
+#pragma unroll
+            for (int k = 0; k < nc; k++)
+#pragma unroll
+                for (int l = 0; l < nd; l++) {
+                    const TA x = scale * (TA)__ldg(v + ((i * nb + j) * nc + k) * nd + l);
+                    jpq[i * nb + j] += x * Drs[k][l];
+                    jrs[k][l] += x * Dpq[i][j];
+                    kpr[i][k] += x * Dqs[j][l];
+                    kqr[j][k] += x * Dps[i][l];
+                    kps[i][l] += x * Dqr[j][k];
+                    kqs[j][l] += x * Dpr[i][k];
+                }
+#pragma unroll
+    for (int k = 0; k < nc; k++)
+#pragma unroll
+        for (int l = 0; l < nd; l++) sh_add(&Js[(c0 + k) * n + d0 + l], (TA)2 * jrs[k][l]);
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int k = 0; k < nc; k++) sh_add(&Ks[(a0 + i) * n + c0 + k], kpr[i][k]);
+#pragma unroll
+    for (int j = 0; j < nb; j++)
+#pragma unroll
+        for (int k = 0; k < nc; k++) sh_add(&Ks[(b0 + j) * n + c0 + k], kqr[j][k]);
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int l = 0; l < nd; l++) sh_add(&Ks[(a0 + i) * n + d0 + l], kps[i][l]);
+#pragma unroll
+    for (int j = 0; j < nb; j++)
+#pragma unroll
+        for (int l = 0; l < nd; l++) sh_add(&Ks[(b0 + j) * n + d0 + l], kqs[j][l]);
+}
+
+// grid (nchunk, nmol); mode 0: only molecules still iterating, 1: all.
+template <typename TS, typename TA>
+__global__ void __launch_bounds__(256) jk_kernel(DevBatch b, int nchunk, int mode) {
+    extern __shared__ unsigned char smem_raw[];
+    const int m = blockIdx.y, c = blockIdx.x;
+    const MolDesc md = b.mol[m];
+    if (mode == 0 && !b.st[m].active) return;
+    const int n = md.nbf, nn = n * n;
+    TA *Ds = (TA *)smem_raw;
+    TA *Js = Ds + nn;
+    TA *Ks = Js + nn;
+    const double *D = b.mat + md.mat0 + (long long)M_D * nn;
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+        Ds[i] = (TA)D[i];
+        Js[i] = (TA)0;
+        Ks[i] = (TA)0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int npair = b.npair[m];
+    const TS *store = (const TS *)b.store + md.eri0;
+    for (int r = c + nchunk * warp; r < npair; r += nchunk * nwarp) {
+        const int2 pq = b.kpair[md.pair0 + r];
+        const double qpq = b.kq[md.pair0 + r];
+        const int P = md.sh0 + pq.x, Q = md.sh0 + pq.y;
+        const int lP = b.sh_l[P], lQ = b.sh_l[Q];
+        const int a0 = b.sh_ao0[P], b0 = b.sh_ao0[Q];
+        const int npq = (lP ? 3 : 1) * (lQ ? 3 : 1);
+        long long base = b.row_off[md.pair0 + m + r];
+        TA jpq[9] = {};
+        for (int s0 = 0; s0 <= r; s0 += 32) {
+            const int s = s0 + lane;
+            bool keep = false;
+            int R = 0, S = 0, nel = 0;
+            if (s <= r && qpq * b.kq[md.pair0 + s] >= TAU_SCHWARZ) {
+                const int2 rs = b.kpair[md.pair0 + s];
+                R = md.sh0 + rs.x;
+                S = md.sh0 + rs.y;
+                keep = true;
+                nel = npq * (b.sh_l[R] ? 3 : 1) * (b.sh_l[S] ? 3 : 1);
+            }
+            int x = nel;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const int tot = __shfl_sync(0xffffffffu, x, 31);
+            if (keep) {
+                const TS *v = store + base + x - nel;
+                TA scale = (TA)1;
+                if (P == Q) scale *= (TA)0.5;
+                if (R == S) scale *= (TA)0.5;
+                if (s == r) scale *= (TA)0.5;
+                const int c0 = b.sh_ao0[R], d0 = b.sh_ao0[S];
+                const int cls = (lP << 3) | (lQ << 2) | (b.sh_l[R] << 1) | b.sh_l[S];
+                switch (cls) {
+                case 0x0: jk_block<TS, TA, 0, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0x8: jk_block<TS, TA, 1, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0xA: jk_block<TS, TA, 1, 0, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0xC: jk_block<TS, TA, 1, 1, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0xE: jk_block<TS, TA, 1, 1, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0xF: jk_block<TS, TA, 1, 1, 1, 1>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                default: break;
+                }
+            }
+            base += tot;
+        }
+        // the J'_PQ block is common to the whole row: reduce across the warp
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            TA t = jpq[k];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            jpq[k] = t;
+        }
+        if (lane < npq) {
+            const int i = lQ ? lane / 3 : lane, j = lQ ? lane % 3 : 0;
+            TA val = jpq[0];
+#pragma unroll
+            for (int k = 1; k < 9; k++)
+                if (k == lane) val = jpq[k];
+            sh_add(&Js[(a0 + i) * n + b0 + j], (TA)2 * val);
+        }
+    }
+    __syncthreads();
+    TA *gJ, *gK;
+    if constexpr (sizeof(TA) == 8) {
+        gJ = (TA *)(b.accd + md.acc0);
+    } else {
+        gJ = (TA *)(b.accf + md.acc0);
+    }
+    gK = gJ + nn;
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+        TA j = Js[i], k = Ks[i];
+        if (j != (TA)0) atomicAdd(&gJ[i], j);
+        if (k != (TA)0) atomicAdd(&gK[i], k);
+    }
+}
+
+void launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, cudaStream_t s) {
+    dim3 grid(nchunk, b.nmol);
+    int n = max_nbf;
+    if (b.precision == 0) {  // FP64 store
+        size_t sm = 3ull * n * n * sizeof(double);
+        cudaFuncSetAttribute(jk_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        jk_kernel<double, double><<<grid, 256, sm, s>>>(b, nchunk, mode);
+    } else if (acc_fp64) {
+        size_t sm = 3ull * n * n * sizeof(double);
+        cudaFuncSetAttribute(jk_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        jk_kernel<float, double><<<grid, 256, sm, s>>>(b, nchunk, mode);
+    } else {
+        size_t sm = 3ull * n * n * sizeof(float);
+        cudaFuncSetAttribute(jk_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        jk_kernel<float, float><<<grid, 256, sm, s>>>(b, nchunk, mode);
+    }
+}

@@ -1,0 +1,30 @@
+// Launch wrappers of the device kernels (host side, internal).
+#pragma once
+#include "common.cuh"
+
+void launch_boys_table(double *t64, float *t32, cudaStream_t s);
+void launch_boys_eval(int mmax, int n, const double *dT, double *dout, int fp32, const double *t64,
+                      const float *t32, cudaStream_t s);
+void launch_quad_tables(double *rad, double *ang, int n_rad, int n_theta, int n_phi, cudaStream_t s);
+void launch_onee(const DevBatch &b, int ncand, cudaStream_t s);
+void launch_schwarz(const DevBatch &b, int ncand, cudaStream_t s);
+void launch_compact_pairs(const DevBatch &b, cudaStream_t s);
+void launch_row_count(const DevBatch &b, int ncand, cudaStream_t s);
+void launch_row_scan(const DevBatch &b, cudaStream_t s);
+void launch_eri_store(const DevBatch &b, int ncand, int fp32, cudaStream_t s);
+int launch_grid_build(const DevBatch &b, long long nblk_total, const int *blk_mol, const double *rad,
+                      const double *ang, int max_atoms, cudaStream_t s);
+// J/K from the packed store.  acc_fp64: accumulate in FP64 (accd) instead of
+// FP32 (accf); mode 0: molecules still iterating, 1: every molecule.
+void launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, cudaStream_t s);
+// AO + density + B3LYP + V_xc on the grid; acc_fp64 and mode as above.
+void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
+                    cudaStream_t s);
+// Per-molecule FP64 SCF stages.
+void launch_scf_init(const DevBatch &b, cudaStream_t s);
+void launch_scf_guess(const DevBatch &b, cudaStream_t s);
+void launch_scf_step(const DevBatch &b, int acc_fp64, cudaStream_t s);
+void launch_scf_final(const DevBatch &b, int acc_fp64, cudaStream_t s);
+void launch_fock_only(const DevBatch &b, int acc_fp64, cudaStream_t s);
+void launch_reset_exc(const DevBatch &b, cudaStream_t s);
+void launch_eval_xc(int n, const double *rho, const double *sigma, double *out, int fp32, cudaStream_t s);

@@ -1,0 +1,428 @@
+// Per-molecule FP64 SCF stages, one thread block per molecule.
+//
+// Paper Section 3.1 (Eq. 1): at iteration i, build rho_i, V_xc, J, K, then
+// solve [V + T + J + K + V_xc] C = S C eps for the next C.  Readings (the paper
+// is silent on them):
+//  * F = H + J - (a0/2) K_std + V_xc, a0 = 0.2 for B3LYP (1 in Hartree-Fock mode);
+//  * E = tr D (H + J/2 - a0 K_std/4) + E_xc + E_nuc;
+//  * X = S^-1/2 (Loewdin), X^T F X diagonalised by Jacobi, C = X C';
+//  * core-Hamiltonian guess;
+//  * Pulay DIIS on e = X^T (F D S - S D F) X with the last diis_space pairs,
+//    used once two pairs exist; a singular bordered system drops the oldest pair;
+//  * convergence: |E - E_prev| < e_tol and max|e| < err_tol (converge protocol),
+//    or exactly fixed_iters iterations; then one plain final Fock build.
+#include <cfloat>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "la.cuh"
+
+#define RKS_STATUS_OK_ 0
+#define RKS_STATUS_NOT_CONVERGED_ 1
+#define RKS_STATUS_NONFINITE_ 2
+#define RKS_STATUS_S_ILL_ 3
+#define RKS_STATUS_EIGH_ 4
+
+struct ScfSmem {
+    double *A, *V, *w, *red, *cs;
+    int *perm;
+};
+
+__device__ inline ScfSmem scf_smem(unsigned char *raw) {
+    ScfSmem s;
+    double *d = (double *)raw;
+    s.A = d;
+    s.V = d + RKS_NBF_CAP * RKS_NBF_CAP;
+    s.w = s.V + RKS_NBF_CAP * RKS_NBF_CAP;
+    s.red = s.w + RKS_NBF_CAP;
+    s.cs = s.red + 64;
+    s.perm = (int *)(s.cs + 2 * RKS_NBF_CAP + 8);
+    return s;
+}
+static const size_t SCF_SMEM = sizeof(double) * (2 * RKS_NBF_CAP * RKS_NBF_CAP + RKS_NBF_CAP + 64 + 2 * RKS_NBF_CAP + 8) +
+                               sizeof(int) * (3 * RKS_NBF_CAP + 8);
+
+// Diagonalise X^T F X (F global, n x n): eigenvalues -> w (shared), C = X C' -> Cout (global).
+__device__ int diag_fock(const double *F, const double *X, double *tmp, double *Cout, ScfSmem &sm, int n) {
+    la::gemm(tmp, F, X, n, false, false);
+    __syncthreads();
+    la::gemm(sm.A, X, tmp, n, true, false);
+    __syncthreads();
+    // exact symmetry before Jacobi
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        int i = idx / n, j = idx % n;
+        if (i < j) {
+            double v = 0.5 * (sm.A[i * n + j] + sm.A[j * n + i]);
+            sm.A[i * n + j] = v;
+            sm.A[j * n + i] = v;
+        }
+    }
+    __syncthreads();
+    int sw = la::jacobi(sm.A, sm.V, sm.w, n, sm.red, sm.perm, sm.cs);
+    la::gemm(Cout, X, sm.V, n, false, false);
+    __syncthreads();
+    return sw;
+}
+
+__device__ void density_from_C(const double *C, double *D, int n, int nocc) {
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        int i = idx / n, j = idx % n;
+        double s = 0.0;
+        for (int k = 0; k < nocc; k++) s += C[i * n + k] * C[j * n + k];
+        D[idx] = 2.0 * s;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ init
+__global__ void scf_init_kernel(DevBatch b) {
+    const int m = blockIdx.x;
+    const MolDesc md = b.mol[m];
+    const int n = md.nbf, nn = n * n;
+    double *Tm = b.mat + md.mat0 + (long long)M_T * nn, *Vm = b.mat + md.mat0 + (long long)M_V * nn;
+    double *H = b.mat + md.mat0 + (long long)M_H * nn;
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) H[i] = Tm[i] + Vm[i];
+    __shared__ double red[32];
+    double e = 0.0;
+    for (int idx = threadIdx.x; idx < md.natom * md.natom; idx += blockDim.x) {
+        int a = idx / md.natom, c = idx % md.natom;
+        if (c < a) {
+            const double *xa = b.axyz + (md.atom0 + a) * 3, *xc = b.axyz + (md.atom0 + c) * 3;
+            double dx = xa[0] - xc[0], dy = xa[1] - xc[1], dz = xa[2] - xc[2];
+            e += (double)b.Z[md.atom0 + a] * b.Z[md.atom0 + c] / sqrt(dx * dx + dy * dy + dz * dz);
+        }
+    }
+    e = la::block_sum(e, red);
+    if (threadIdx.x == 0) {
+        MolState &st = b.st[m];
+        st.Enuc = e;
+        st.E = 0.0; st.E_prev = 0.0; st.Exc = 0.0; st.max_err = 0.0;
+        st.diis_n = 0; st.diis_head = 0; st.iter = 0; st.active = 1; st.converged = 0;
+        st.status = RKS_STATUS_OK_; st.eigh_fail = 0;
+    }
+}
+
+void launch_scf_init(const DevBatch &b, cudaStream_t s) { scf_init_kernel<<<b.nmol, 256, 0, s>>>(b); }
+
+// ------------------------------------------- orthogonaliser + core guess
+__global__ void scf_guess_kernel(DevBatch b) {
+    extern __shared__ unsigned char raw[];
+    ScfSmem sm = scf_smem(raw);
+    const int m = blockIdx.x;
+    const MolDesc md = b.mol[m];
+    const int n = md.nbf, nn = n * n;
+    double *S = b.mat + md.mat0 + (long long)M_S * nn;
+    double *X = b.mat + md.mat0 + (long long)M_X * nn;
+    double *H = b.mat + md.mat0 + (long long)M_H * nn;
+    double *C = b.mat + md.mat0 + (long long)M_C * nn;
+    double *D = b.mat + md.mat0 + (long long)M_D * nn;
+    double *tmp = b.mat + md.mat0 + (long long)M_TMP1 * nn;
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) sm.A[i] = S[i];
+    __syncthreads();
+    int sw = la::jacobi(sm.A, sm.V, sm.w, n, sm.red, sm.perm, sm.cs);
+    // X = U diag(s^-1/2) U^T
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+        int i = idx / n, j = idx % n;
+        double v = 0.0;
+        for (int k = 0; k < n; k++) v += sm.V[i * n + k] * sm.V[j * n + k] / sqrt(sm.w[k]);
+        X[idx] = v;
+    }
+    __syncthreads();
+    double smin = sm.w[0];
+    int sw2 = diag_fock(H, X, tmp, C, sm, n);
+    density_from_C(C, D, n, md.nocc);
+    if (threadIdx.x == 0) {
+        MolState &st = b.st[m];
+        st.smin = smin;
+        if (smin < 1e-8) st.status = RKS_STATUS_S_ILL_;
+        if (sw < 0 || sw2 < 0) st.eigh_fail++;
+        for (int i = 0; i < n; i++) st.eps[i] = sm.w[i];
+    }
+}
+
+void launch_scf_guess(const DevBatch &b, cudaStream_t s) {
+    cudaFuncSetAttribute(scf_guess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
+    scf_guess_kernel<<<b.nmol, 256, SCF_SMEM, s>>>(b);
+}
+
+// ----------------------------------------------------- Fock assembly
+// J = J' + J'^T etc. from the accumulators; F = H + J - a0/2 K + V_xc;
+// returns E (valid in every thread).
+template <typename TA>
+__device__ double assemble_fock(const DevBatch &b, int m, const MolDesc &md, const TA *acc, double *red) {
+    const int n = md.nbf, nn = n * n;
+    double *H = b.mat + md.mat0 + (long long)M_H * nn;
+    double *D = b.mat + md.mat0 + (long long)M_D * nn;
+    double *F = b.mat + md.mat0 + (long long)M_F * nn;
+    double *J = b.mat + md.mat0 + (long long)M_J * nn;
+    double *K = b.mat + md.mat0 + (long long)M_K * nn;
+    double *Vx = b.mat + md.mat0 + (long long)M_VXC * nn;
+    const TA *aJ = acc, *aK = acc + nn, *aV = acc + 2 * nn;
+    double e = 0.0;
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+        int i = idx / n, j = idx % n, tr = j * n + i;
+        double jj = (double)aJ[idx] + (double)aJ[tr];
+        double kk = (double)aK[idx] + (double)aK[tr];
+        double vv = b.xc ? (double)aV[idx] + (double)aV[tr] : 0.0;
+        J[idx] = jj;
+        K[idx] = kk;
+        Vx[idx] = vv;
+        F[idx] = H[idx] + jj - 0.5 * b.a0 * kk + vv;
+        e += D[idx] * (H[idx] + 0.5 * jj - 0.25 * b.a0 * kk);
+    }
+    e = la::block_sum(e, red);
+    return e + b.st[m].Exc + b.st[m].Enuc;
+}
+
+// ------------------------------------------------------------ one step
+template <typename TA>
+__global__ void scf_step_kernel(DevBatch b, const TA *accbase) {
+    extern __shared__ unsigned char raw[];
+    ScfSmem sm = scf_smem(raw);
+    const int m = blockIdx.x;
+    const MolDesc &md = b.mol[m];
+    MolState &st = b.st[m];
+    if (!st.active) return;
+    const int n = md.nbf, nn = n * n;
+    double *S = b.mat + md.mat0 + (long long)M_S * nn;
+    double *X = b.mat + md.mat0 + (long long)M_X * nn;
+    double *D = b.mat + md.mat0 + (long long)M_D * nn;
+    double *F = b.mat + md.mat0 + (long long)M_F * nn;
+    double *C = b.mat + md.mat0 + (long long)M_C * nn;
+    double *FX = b.mat + md.mat0 + (long long)M_FX * nn;
+    double *t1 = b.mat + md.mat0 + (long long)M_TMP1 * nn;
+    double *t2 = b.mat + md.mat0 + (long long)M_TMP2 * nn;
+    double *t3 = b.mat + md.mat0 + (long long)M_TMP3 * nn;
+    const double E = assemble_fock<TA>(b, m, md, accbase + md.acc0, sm.red);
+    __syncthreads();
+    // e = X^T (F D S - S D F) X ;  S D F = (F D S)^T for symmetric F, D, S
+    la::gemm(t1, F, D, n, false, false);
+    __syncthreads();
+    la::gemm(t2, t1, S, n, false, false);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+        int i = idx / n, j = idx % n;
+        t3[idx] = t2[idx] - t2[j * n + i];
+    }
+    __syncthreads();
+    la::gemm(t1, X, t3, n, true, false);
+    __syncthreads();
+    la::gemm(t2, t1, X, n, false, false);  // t2 = error matrix
+    __syncthreads();
+    double mx = 0.0;
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) mx = fmax(mx, fabs(t2[idx]));
+    mx = la::block_max(mx, sm.red);
+    const int diis_space = b.diis_space;
+    __shared__ int s_conv, s_nd, s_ok;
+    __shared__ double s_c[RKS_DIIS_MAX + 1];
+    __shared__ int s_slot[RKS_DIIS_MAX];
+    if (threadIdx.x == 0) {
+        s_conv = 0;
+        if (!isfinite(E) || !isfinite(mx)) {
+            st.status = RKS_STATUS_NONFINITE_;
+            st.active = 0;
+            s_conv = 2;
+        } else if (b.fixed_iters == 0 && st.iter >= 1 && fabs(E - st.E_prev) < b.e_tol && mx < b.err_tol) {
+            st.converged = 1;
+            st.active = 0;
+            s_conv = 1;
+        }
+        st.E = E;
+        st.max_err = mx;
+        st.Ehist[st.iter % RKS_NHIST] = E;
+    }
+    __syncthreads();
+    if (s_conv) {
+        if (threadIdx.x == 0) st.iter += 1;
+        return;
+    }
+    // ---- DIIS push
+    __shared__ int s_new;
+    if (threadIdx.x == 0) {
+        int slot;
+        if (st.diis_n < diis_space) {
+            slot = (st.diis_head + st.diis_n) % diis_space;
+            st.diis_n++;
+        } else {
+            slot = st.diis_head;
+            st.diis_head = (st.diis_head + 1) % diis_space;
+        }
+        s_new = slot;
+    }
+    __syncthreads();
+    double *Fh = b.mat + md.mat0 + (long long)(M_DIIS_F + s_new) * nn;
+    double *Eh = b.mat + md.mat0 + (long long)(M_DIIS_E + s_new) * nn;
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+        Fh[idx] = F[idx];
+        Eh[idx] = t2[idx];
+    }
+    __syncthreads();
+    for (int k = 0; k < st.diis_n; k++) {
+        int slot = (st.diis_head + k) % diis_space;
+        const double *Ek = b.mat + md.mat0 + (long long)(M_DIIS_E + slot) * nn;
+        double d = 0.0;
+        for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) d += Eh[idx] * Ek[idx];
+        d = la::block_sum(d, sm.red);
+        if (threadIdx.x == 0) {
+            st.B[s_new * RKS_DIIS_MAX + slot] = d;
+            st.B[slot * RKS_DIIS_MAX + s_new] = d;
+        }
+    }
+    __syncthreads();
+    // ---- DIIS solve (thread 0): bordered system, oldest -> newest
+    if (threadIdx.x == 0) {
+        s_ok = 0;
+        while (st.diis_n >= 2) {
+            int mm = st.diis_n;
+            double Mtx[(RKS_DIIS_MAX + 1) * (RKS_DIIS_MAX + 2)];
+            const int W = mm + 2;
+            for (int i = 0; i < mm; i++) {
+                int si = (st.diis_head + i) % diis_space;
+                s_slot[i] = si;
+                for (int j = 0; j < mm; j++) {
+                    int sj = (st.diis_head + j) % diis_space;
+                    Mtx[i * W + j] = st.B[si * RKS_DIIS_MAX + sj];
+                }
+                Mtx[i * W + mm] = -1.0;
+                Mtx[i * W + mm + 1] = 0.0;
+            }
+            for (int j = 0; j < mm; j++) Mtx[mm * W + j] = -1.0;
+            Mtx[mm * W + mm] = 0.0;
+            Mtx[mm * W + mm + 1] = -1.0;
+            bool sing = false;
+            const int N = mm + 1;
+            for (int c = 0; c < N && !sing; c++) {
+                int piv = c;
+                for (int r = c + 1; r < N; r++)
+                    if (fabs(Mtx[r * W + c]) > fabs(Mtx[piv * W + c])) piv = r;
+                if (Mtx[piv * W + c] == 0.0) { sing = true; break; }
+                if (piv != c)
+                    for (int k = 0; k < W; k++) { double t = Mtx[c * W + k]; Mtx[c * W + k] = Mtx[piv * W + k]; Mtx[piv * W + k] = t; }
+                for (int r = c + 1; r < N; r++) {
+                    double f = Mtx[r * W + c] / Mtx[c * W + c];
+                    for (int k = c; k < W; k++) Mtx[r * W + k] -= f * Mtx[c * W + k];
+                }
+            }
+            if (!sing) {
+                for (int r = N - 1; r >= 0; r--) {
+                    double v = Mtx[r * W + N];
+                    for (int k = r + 1; k < N; k++) v -= Mtx[r * W + k] * s_c[k];
+                    s_c[r] = v / Mtx[r * W + r];
+                }
+                bool fin = true;
+                for (int i = 0; i < N; i++) fin = fin && isfinite(s_c[i]);
+                if (fin) { s_ok = 1; s_nd = mm; break; }
+            }
+            // drop the oldest pair
+            st.diis_head = (st.diis_head + 1) % diis_space;
+            st.diis_n--;
+        }
+    }
+    __syncthreads();
+    const double *Fuse = F;
+    if (s_ok) {
+        for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+            double v = 0.0;
+            for (int k = 0; k < s_nd; k++) v += s_c[k] * b.mat[md.mat0 + (long long)(M_DIIS_F + s_slot[k]) * nn + idx];
+            FX[idx] = v;
+        }
+        __syncthreads();
+        Fuse = FX;
+    }
+    // ---- diagonalise, new density
+    int sw = diag_fock(Fuse, X, t1, C, sm, n);
+    density_from_C(C, D, n, md.nocc);
+    if (threadIdx.x == 0) {
+        if (sw < 0) st.eigh_fail++;
+        st.E_prev = E;
+        st.iter += 1;
+        for (int i = 0; i < n; i++) st.eps[i] = sm.w[i];
+        if (b.fixed_iters > 0 && st.iter >= b.fixed_iters) st.active = 0;
+        if (b.fixed_iters == 0 && st.iter >= b.max_iters) {
+            st.active = 0;
+            st.status = RKS_STATUS_NOT_CONVERGED_;
+        }
+    }
+}
+
+void launch_scf_step(const DevBatch &b, int acc_fp64, cudaStream_t s) {
+    if (acc_fp64 || b.precision == 0) {
+        cudaFuncSetAttribute(scf_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
+        scf_step_kernel<double><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accd);
+    } else {
+        cudaFuncSetAttribute(scf_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
+        scf_step_kernel<float><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accf);
+    }
+}
+
+// ------------------------------------------------------------ final
+// F[D] at the last density (final precision), E[D], plain diagonalisation:
+// eps, HOMO/LUMO, and the output density (written over M_D; the input
+// density is kept in M_TMP3).
+template <typename TA>
+__global__ void scf_final_kernel(DevBatch b, const TA *accbase) {
+    extern __shared__ unsigned char raw[];
+    ScfSmem sm = scf_smem(raw);
+    const int m = blockIdx.x;
+    const MolDesc &md = b.mol[m];
+    MolState &st = b.st[m];
+    const int n = md.nbf, nn = n * n;
+    double *X = b.mat + md.mat0 + (long long)M_X * nn;
+    double *D = b.mat + md.mat0 + (long long)M_D * nn;
+    double *F = b.mat + md.mat0 + (long long)M_F * nn;
+    double *C = b.mat + md.mat0 + (long long)M_C * nn;
+    double *t1 = b.mat + md.mat0 + (long long)M_TMP1 * nn;
+    double *t3 = b.mat + md.mat0 + (long long)M_TMP3 * nn;
+    const double E = assemble_fock<TA>(b, m, md, accbase + md.acc0, sm.red);
+    __syncthreads();
+    int sw = diag_fock(F, X, t1, C, sm, n);
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) t3[idx] = D[idx];
+    __syncthreads();
+    density_from_C(C, D, n, md.nocc);
+    if (threadIdx.x == 0) {
+        if (sw < 0) st.eigh_fail++;
+        st.E = E;
+        for (int i = 0; i < n; i++) st.eps[i] = sm.w[i];
+        st.eps_homo = sm.w[md.nocc - 1];
+        st.eps_lumo = md.nocc < n ? sm.w[md.nocc] : 0.0;
+        bool fin = isfinite(E);
+        for (int i = 0; i < n; i++) fin = fin && isfinite(sm.w[i]);
+        if (!fin) st.status = RKS_STATUS_NONFINITE_;
+        else if (st.eigh_fail && st.status == RKS_STATUS_OK_) st.status = RKS_STATUS_EIGH_;
+        st.active = 0;
+    }
+}
+
+void launch_scf_final(const DevBatch &b, int acc_fp64, cudaStream_t s) {
+    if (acc_fp64 || b.precision == 0) {
+        cudaFuncSetAttribute(scf_final_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
+        scf_final_kernel<double><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accd);
+    } else {
+        cudaFuncSetAttribute(scf_final_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
+        scf_final_kernel<float><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accf);
+    }
+}
+
+// ---------------------------------------------- Fock build at a given D
+template <typename TA>
+__global__ void fock_only_kernel(DevBatch b, const TA *accbase) {
+    __shared__ double red[32];
+    const int m = blockIdx.x;
+    const MolDesc &md = b.mol[m];
+    const double E = assemble_fock<TA>(b, m, md, accbase + md.acc0, red);
+    if (threadIdx.x == 0) b.st[m].E = E;
+}
+
+void launch_fock_only(const DevBatch &b, int acc_fp64, cudaStream_t s) {
+    if (acc_fp64 || b.precision == 0) fock_only_kernel<double><<<b.nmol, 256, 0, s>>>(b, b.accd);
+    else fock_only_kernel<float><<<b.nmol, 256, 0, s>>>(b, b.accf);
+}
+
+// Exc accumulators to zero before a grid pass.
+__global__ void reset_exc_kernel(DevBatch b) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < b.nmol) b.st[m].Exc = 0.0;
+}
+void launch_reset_exc(const DevBatch &b, cudaStream_t s) {
+    reset_exc_kernel<<<(b.nmol + 127) / 128, 128, 0, s>>>(b);
+}
