@@ -65,7 +65,11 @@ extern "C" {
 #define RKS_FP64 0  /* every step in FP64 */
 #define RKS_MIXED 1 /* FP32 ERIs / J/K / grid + FP64 linear algebra and energy, FP64 final correction */
 
-#define RKS_MAX_NBF 128 /* largest basis a molecule may have */
+#define RKS_MAX_NBF 96 /* largest basis a molecule may have */
+
+/* ---------------------------------------------------------- initial guess */
+#define RKS_GUESS_SAD 0  /* superposed neutral atoms: 1s/2s space full, 2p^(Z-4) spherically averaged */
+#define RKS_GUESS_CORE 1 /* diagonalise the core Hamiltonian T + V */
 
 typedef struct rks_ctx rks_ctx;
 typedef struct rks_batch rks_batch;
@@ -89,6 +93,14 @@ typedef struct rks_options {
     uint64_t hbm_budget_bytes; /* admission cap for resident molecules; 0 = 85% of free memory */
     int32_t device;         /* CUDA device ordinal, default 0 */
     int32_t use_graphs;     /* capture fixed-iteration loops in CUDA graphs, default 1 */
+    int32_t pad0;
+    double fix_theta;       /* RKS_MIXED final step: quartets with Schwarz bound Q_pq Q_rs >= fix_theta
+                               are recomputed in FP64 and replace their FP32 store values in J/K;
+                               0 disables; default 0.1 */
+    int32_t grid_tc;        /* RKS_MIXED: 1 = grid contractions on the tensor cores (tcgen05, 3xTF32)
+                               when every molecule has nbf <= 80 and <= 60 shells (default);
+                               0 = the CUDA-core grid kernel */
+    int32_t guess;          /* initial density: RKS_GUESS_SAD (default) or RKS_GUESS_CORE */
 } rks_options;
 
 typedef struct rks_result_t {

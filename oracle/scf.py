@@ -17,7 +17,12 @@ Readings where the paper is silent or terse:
 * Energy: E = tr rho (H + J/2 - a0 K_std/4) + E_xc + E_nuc.
 * Generalised eigenproblem via the symmetric (Loewdin) orthogonaliser
   X = S^-1/2 and LAPACK eigh of X^T F X.
-* Guess: diagonalise the core Hamiltonian H = T + V.
+* Guess: "core" diagonalises the core Hamiltonian H = T + V (the water case);
+  "sad" (default for larger molecules) superposes neutral-atom densities: for a
+  heavy atom the 1s and 2s functions hold 4 electrons (fully occupied s space:
+  D_ss = 2 S_ss^-1 over the atom's (1s, 2s) block) and each 2p function holds
+  (Z - 4)/3 electrons (spherical average; same-centre p functions are
+  orthonormal); for H, D = 1/S_11.
 * Pulay DIIS with error e = X^T (F rho S - S rho F) X, the last 8 (F, e)
   pairs, extrapolation once two pairs exist; the bordered system is solved by
   LU with partial pivoting, dropping the oldest pair while it is singular.
@@ -202,11 +207,33 @@ class System:
     def core_guess(self):
         return solve_fock(self.H, self.X, self.nocc)[2]
 
+    def sad_guess(self):
+        D = np.zeros((self.nbf, self.nbf))
+        i = 0
+        for z in self.Z:
+            if int(z) == 1:
+                D[i, i] = 1.0 / self.S[i, i]
+                i += 1
+                continue
+            ss = self.S[i:i + 2, i:i + 2]
+            D[i:i + 2, i:i + 2] = 2.0 * np.linalg.inv(ss)
+            for k in range(2, 5):
+                D[i + k, i + k] = (int(z) - 4) / 3.0
+            i += 5
+        return D
+
+    def guess(self, kind):
+        if kind == "core":
+            return self.core_guess()
+        if kind == "sad":
+            return self.sad_guess()
+        raise ValueError(kind)
+
 
 def run_scf(sysm: System, protocol="converge", n_iter=20, e_tol=1e-9, err_tol=1e-6,
-            max_iter=100, diis_space=8, use_diis=True, D0=None):
+            max_iter=100, diis_space=8, use_diis=True, D0=None, level_shift=0.0, guess="sad"):
     """Run one SCF per the module docstring; returns a result dict."""
-    D = sysm.core_guess() if D0 is None else D0
+    D = sysm.guess(guess) if D0 is None else D0
     diis = DIIS(diis_space)
     energies = []
     E_prev = None
@@ -227,6 +254,9 @@ def run_scf(sysm: System, protocol="converge", n_iter=20, e_tol=1e-9, err_tol=1e
             Fx = diis.extrapolate()
         else:
             Fx = F
+        if level_shift:
+            S = sysm.S
+            Fx = Fx + level_shift * (S - 0.5 * S @ D @ S)
         _, _, D = solve_fock(Fx, sysm.X, sysm.nocc)
     F, E, parts = sysm.fock(D)
     eps, C, D_out = solve_fock(F, sysm.X, sysm.nocc)

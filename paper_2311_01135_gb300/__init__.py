@@ -19,6 +19,7 @@ RKS_OK, RKS_EINVAL, RKS_ENOMEM, RKS_EAGAIN, RKS_ENOTREADY = 0, -1, -2, -3, -4
 RKS_ECUDA, RKS_ETIMEOUT, RKS_ENOTFOUND, RKS_EDEVICE = -5, -6, -7, -8
 RKS_PENDING, RKS_RUNNING, RKS_DONE, RKS_FAILED = 0, 1, 2, 3
 RKS_FP64, RKS_MIXED = 0, 1
+RKS_GUESS_SAD, RKS_GUESS_CORE = 0, 1
 RKS_STATUS = {0: "ok", 1: "not_converged", 2: "nonfinite", 3: "s_ill", 4: "eigh"}
 (RKS_DUMP_PAIRS, RKS_DUMP_PAIR_Q, RKS_DUMP_ROW_OFF, RKS_DUMP_STORE, RKS_DUMP_S, RKS_DUMP_T, RKS_DUMP_V,
  RKS_DUMP_GRID, RKS_DUMP_J, RKS_DUMP_K, RKS_DUMP_VXC, RKS_DUMP_D, RKS_DUMP_F, RKS_DUMP_EPS, RKS_DUMP_X,
@@ -32,7 +33,8 @@ class rks_options(ctypes.Structure):
                 ("err_tol", ctypes.c_double), ("diis_space", ctypes.c_int32),
                 ("coords_in_angstrom", ctypes.c_int32), ("xc", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("pad0", ctypes.c_int32), ("fix_theta", ctypes.c_double),
+                ("grid_tc", ctypes.c_int32), ("guess", ctypes.c_int32)]
 
 
 class rks_result_t(ctypes.Structure):

@@ -85,6 +85,8 @@ struct DevBatch {
     int *row_nq;            // kept quartets per kept row
     long long *row_off;     // exclusive prefix of row element counts; [pair0 + m + r], r <= npair
     void *store;            // packed ERIs (float or double)
+    void *pairprim;         // per kept pair: 9 primitive-pair records (K, zeta, P - A), float or double
+    void *pairprim64;       // FP64 copy for the final-step FP64 recompute of the mixed path (or null)
     // grid (SoA, padded blocks; padding points have w = 0)
     void *gx, *gy, *gz, *gw;
     // FP64 matrices
@@ -100,6 +102,7 @@ struct DevBatch {
     int n_rad, n_theta, n_phi, becke_iters;
     int diis_space;
     int fixed_iters, max_iters;
+    int guess;              // 0 superposed atoms, 1 core Hamiltonian
     double e_tol, err_tol;
 };
 

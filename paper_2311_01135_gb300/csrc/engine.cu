@@ -147,6 +147,9 @@ extern "C" int rks_options_default(rks_options *o) {
     o->hbm_budget_bytes = 0;
     o->device = 0;
     o->use_graphs = 1;
+    o->fix_theta = 0.1;
+    o->grid_tc = 1;
+    o->guess = RKS_GUESS_SAD;
     return RKS_OK;
 }
 
@@ -419,6 +422,7 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
     d.diis_space = std::max(1, std::min(o.diis_space, RKS_DIIS_MAX));
     d.fixed_iters = o.fixed_iters;
     d.max_iters = o.max_iters;
+    d.guess = o.guess;
     d.e_tol = o.e_tol;
     d.err_tol = o.err_tol;
     d.boys64 = ctx->boys64;
@@ -427,6 +431,7 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
     int rc = 0;
     MolDesc *dmol; MolState *dst; int *dZ, *dsa, *dsl, *dsao, *dcm, *dnp, *drnq; double *dax, *dsx, *dse, *dsc, *dcq, *dkq;
     int2 *dcand, *dkp; long long *droff; void *store; void *gx, *gy, *gz, *gw; double *mat, *accd; float *accf;
+    void *pairprim, *pairprim64 = nullptr;
     if ((rc = dalloc(b, &dmol, nmol)) || (rc = dalloc(b, &dst, nmol)) || (rc = dalloc(b, &dZ, atom_off)) ||
         (rc = dalloc(b, &dax, 3 * atom_off)) || (rc = dalloc(b, &dsa, sh_off)) || (rc = dalloc(b, &dsl, sh_off)) ||
         (rc = dalloc(b, &dsao, sh_off)) || (rc = dalloc(b, &dsx, 3 * sh_off)) || (rc = dalloc(b, &dse, 3 * sh_off)) ||
@@ -434,6 +439,9 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
         (rc = dalloc(b, &dcq, pair_off)) || (rc = dalloc(b, &dkp, pair_off)) || (rc = dalloc(b, &dkq, pair_off)) ||
         (rc = dalloc(b, &dnp, nmol)) || (rc = dalloc(b, &drnq, pair_off)) || (rc = dalloc(b, &droff, pair_off + nmol)) ||
         (rc = dalloc(b, (unsigned char **)&store, eri_off * esz)) ||
+        (rc = dalloc(b, (unsigned char **)&pairprim, pair_off * 9 * 5 * esz)) ||
+        (o.precision == RKS_MIXED && o.fix_theta > 0 &&
+         (rc = dalloc(b, (unsigned char **)&pairprim64, pair_off * 9 * 5 * sizeof(double)))) ||
         (rc = dalloc(b, (unsigned char **)&gx, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gy, pts_off * esz)) ||
         (rc = dalloc(b, (unsigned char **)&gz, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gw, pts_off * esz)) ||
         (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) || (rc = dalloc(b, &accf, acc_off)) ||
@@ -444,6 +452,8 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
     d.mol = dmol; d.st = dst; d.Z = dZ; d.axyz = dax; d.sh_atom = dsa; d.sh_l = dsl; d.sh_ao0 = dsao;
     d.sh_xyz = dsx; d.sh_ex = dse; d.sh_co = dsc; d.cand = dcand; d.cand_mol = dcm; d.cand_q = dcq;
     d.kpair = dkp; d.kq = dkq; d.npair = dnp; d.row_nq = drnq; d.row_off = droff; d.store = store;
+    d.pairprim = pairprim;
+    d.pairprim64 = pairprim64;
     d.gx = gx; d.gy = gy; d.gz = gz; d.gw = gw; d.mat = mat; d.accd = accd; d.accf = accf;
     cudaStream_t s = ctx->stream;
 #define UP(dst_, src_)                                                                                      \
@@ -494,6 +504,7 @@ extern "C" int rks_batch_setup(rks_batch *b) {
     { StageScope sc(c, "pairs", 0); launch_compact_pairs(d, s); }
     { StageScope sc(c, "row_count", 0); launch_row_count(d, (int)b->ncand, s); }
     { StageScope sc(c, "row_scan", 0); launch_row_scan(d, s); }
+    { StageScope sc(c, "pair_prim", 0); launch_pair_prim(d, (int)b->ncand, fp32, s); }
     { StageScope sc(c, "eri", 0); launch_eri_store(d, (int)b->ncand, fp32, s); }
     { StageScope sc(c, "grid_build", 0); launch_grid_build(d, b->nblk_total, b->blk_mol, c->rad, c->ang, b->max_atoms, s); }
     { StageScope sc(c, "scf_init", 0); launch_scf_init(d, s); }
@@ -517,10 +528,24 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
     launch_reset_exc(d, s);
     const int nchunk_jk = 8;
     { StageScope sc(c, acc_fp64 ? "jk_final" : "jk", 0); launch_jk(d, nchunk_jk, acc_fp64, mode, b->max_nbf, s); }
+    if (acc_fp64 && b->precision == RKS_MIXED && c->opt.fix_theta > 0) {
+        StageScope sc(c, "jk_fp64_fix", 0);
+        launch_jk_correct(d, nchunk_jk, c->opt.fix_theta, b->max_nbf, s);
+    }
     if (d.xc) {
-        const int nchunk_gx = 16;
-        StageScope sc(c, acc_fp64 ? "grid_xc_final" : "grid_xc", 0);
-        launch_grid_xc(d, nchunk_gx, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
+        // Tensor-core accumulation truncates (round toward zero): fine for the
+        // iterations, but the final step's energy uses the CUDA-core kernel,
+        // whose FP32 sums round to nearest and carry no bias.
+        if (!acc_fp64 && b->precision == RKS_MIXED && c->opt.grid_tc &&
+            grid_xc_tc_supported(b->max_nbf, b->max_nsh)) {
+            const int nchunk_tc = 4;
+            StageScope sc(c, acc_fp64 ? "grid_xc_tc_final" : "grid_xc_tc", 0);
+            launch_grid_xc_tc(d, nchunk_tc, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
+        } else {
+            const int nchunk_gx = 16;
+            StageScope sc(c, acc_fp64 ? "grid_xc_final" : "grid_xc", 0);
+            launch_grid_xc(d, nchunk_gx, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
+        }
     }
     return check_launch("fock pass");
 }
@@ -723,15 +748,22 @@ extern "C" int64_t rks_batch_dump(rks_batch *b, int32_t m, int32_t what, void *o
         return bytes;
     }
     case RKS_DUMP_GRID: {
+        // stored as offsets from the owning nucleus; returned as absolute positions
         int64_t bytes = (int64_t)md.npts * 32;
         if (cap < bytes) return RKS_EINVAL;
         const size_t esz = b->precision ? 4 : 8;
         std::vector<unsigned char> t(md.npts * esz);
+        std::vector<double> ax(3 * md.natom);
+        CUDA_OK(cudaMemcpy(ax.data(), d.axyz + 3 * md.atom0, ax.size() * 8, cudaMemcpyDeviceToHost));
+        const int npa = d.n_rad * d.n_theta * d.n_phi;
         void *src[4] = {d.gx, d.gy, d.gz, d.gw};
         for (int k = 0; k < 4; k++) {
             CUDA_OK(cudaMemcpy(t.data(), (unsigned char *)src[k] + md.pts0 * esz, md.npts * esz, cudaMemcpyDeviceToHost));
-            for (int i = 0; i < md.npts; i++)
-                ((double *)out)[4 * i + k] = esz == 4 ? (double)((float *)t.data())[i] : ((double *)t.data())[i];
+            for (int i = 0; i < md.npts; i++) {
+                double v = esz == 4 ? (double)((float *)t.data())[i] : ((double *)t.data())[i];
+                if (k < 3) v += ax[3 * (i / npa) + k];
+                ((double *)out)[4 * i + k] = v;
+            }
         }
         return bytes;
     }
@@ -843,7 +875,8 @@ extern "C" int rks_create(const rks_options *options, rks_ctx **out) {
     rks_options o;
     if (options) o = *options; else rks_options_default(&o);
     if (o.basis != 0 || o.n_rad <= 0 || o.n_theta <= 0 || o.n_theta > 64 || o.n_phi <= 0 || o.becke_iters < 0 ||
-        (o.precision != RKS_FP64 && o.precision != RKS_MIXED) || o.max_iters <= 0 || o.max_slots <= 0)
+        (o.precision != RKS_FP64 && o.precision != RKS_MIXED) || o.max_iters <= 0 || o.max_slots <= 0 ||
+        !(o.fix_theta >= 0) || (o.guess != RKS_GUESS_SAD && o.guess != RKS_GUESS_CORE))
         return fail(RKS_EINVAL, "bad options");
     int ndev = 0;
     CUDA_OK(cudaGetDeviceCount(&ndev));

@@ -33,7 +33,8 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
     T *cf = pt + 4 * BP;                   // [4][BP] coefficients
     T *shd = cf + 4 * BP;                  // [nsh][8]: x y z e0 e1 e2 (c's below)
     T *shc = shd + nsh * 8;                // [nsh][4]: c0 c1 c2 -
-    int *shi = (int *)(shc + nsh * 4);     // [nsh][2]: l, ao0
+    T *dlt = shc + nsh * 4;                // [2][nsh][3]: R_owner - C_shell for the sub-block's owners
+    int *shi = (int *)(dlt + 6 * nsh);     // [nsh][2]: l, ao0
     const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ds[i] = (T)D[i];
     for (int s = threadIdx.x; s < nsh; s += blockDim.x) {
@@ -58,20 +59,33 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
     const T *gx = (const T *)b.gx + md.pts0, *gy = (const T *)b.gy + md.pts0;
     const T *gz = (const T *)b.gz + md.pts0, *gw = (const T *)b.gw + md.pts0;
     const int nsub = md.nblk * (RKS_PTS_BLOCK / BP);
+    const int npa = b.n_rad * b.n_theta * b.n_phi;
     __syncthreads();
     for (int sb = chunk; sb < nsub; sb += nchunk) {
         const long long p0 = (long long)sb * BP;
+        const int own0 = min((int)(p0 / npa), md.natom - 1);
         for (int i = t; i < BP; i += blockDim.x) {
             pt[i] = gx[p0 + i];
             pt[BP + i] = gy[p0 + i];
             pt[2 * BP + i] = gz[p0 + i];
             pt[3 * BP + i] = gw[p0 + i];
         }
+        // centre offsets for the (at most two) atoms owning this sub-block's points
+        for (int i = t; i < 2 * nsh; i += blockDim.x) {
+            const int h = i / nsh, s = i % nsh;
+            const int A = min(own0 + h, md.natom - 1);
+            const double *ra = b.axyz + (md.atom0 + A) * 3, *rc = b.sh_xyz + (md.sh0 + s) * 3;
+            dlt[(h * nsh + s) * 3 + 0] = (T)(ra[0] - rc[0]);
+            dlt[(h * nsh + s) * 3 + 1] = (T)(ra[1] - rc[1]);
+            dlt[(h * nsh + s) * 3 + 2] = (T)(ra[2] - rc[2]);
+        }
         __syncthreads();
         // ---- AO values and gradients: phi[0..3][mu][p]
         for (int idx = t; idx < nsh * BP; idx += blockDim.x) {
             const int s = idx / BP, p = idx % BP;
-            const T dx = pt[p] - shd[s * 8], dy = pt[BP + p] - shd[s * 8 + 1], dz = pt[2 * BP + p] - shd[s * 8 + 2];
+            const int h = min((int)((p0 + p) / npa), md.natom - 1) - own0;
+            const T *dl = dlt + (h * nsh + s) * 3;
+            const T dx = dl[0] + pt[p], dy = dl[1] + pt[BP + p], dz = dl[2] + pt[2 * BP + p];
             const T r2 = dx * dx + dy * dy + dz * dz;
             T g = 0, gp = 0;
 #pragma unroll
@@ -137,7 +151,13 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
                               cf[2 * BP + p] * phi[(2 * n + nu) * BP + p] + cf[3 * BP + p] * phi[(3 * n + nu) * BP + p];
         }
         __syncthreads();
-        // ---- V'[mu][nu] += sum_p phi[mu][p] X[p][nu]
+        // ---- V'[mu][nu] += sum_p phi[mu][p] X[p][nu]; the sub-block sum is
+        // formed in T and folded into the TA accumulator once per sub-block
+        T part[TILE][TILE];
+#pragma unroll
+        for (int a = 0; a < TILE; a++)
+#pragma unroll
+            for (int c = 0; c < TILE; c++) part[a][c] = (T)0;
         for (int p = 0; p < BP; p++) {
             T fa[TILE], xb[TILE];
 #pragma unroll
@@ -153,8 +173,12 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
 #pragma unroll
             for (int a = 0; a < TILE; a++)
 #pragma unroll
-                for (int c = 0; c < TILE; c++) acc[a][c] += (TA)(fa[a] * xb[c]);
+                for (int c = 0; c < TILE; c++) part[a][c] += fa[a] * xb[c];
         }
+#pragma unroll
+        for (int a = 0; a < TILE; a++)
+#pragma unroll
+            for (int c = 0; c < TILE; c++) acc[a][c] += (TA)part[a][c];
         __syncthreads();
     }
     // ---- flush V' and E_xc
@@ -175,7 +199,7 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
 template <typename T, typename TA, int BP, int TILE>
 static void launch_gx(const DevBatch &b, int nchunk, int mode, int max_nbf, int max_nsh, cudaStream_t s) {
     const int n = max_nbf, XS = n | 1;
-    size_t sm = sizeof(T) * ((size_t)n * n + 4ull * n * BP + (size_t)BP * XS + 8ull * BP + 12ull * max_nsh) +
+    size_t sm = sizeof(T) * ((size_t)n * n + 4ull * n * BP + (size_t)BP * XS + 8ull * BP + 18ull * max_nsh) +
                 sizeof(int) * 2ull * max_nsh + 64;
     cudaFuncSetAttribute(grid_xc_kernel<T, TA, BP, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     grid_xc_kernel<T, TA, BP, TILE><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode);

@@ -1,0 +1,481 @@
+// Exchange-correlation quadrature with the two grid contractions on the
+// tensor cores (tcgen05, kind::tf32, 3xTF32 split products, FP32 accumulators
+// in tensor memory).  Same quantities as gridxc.cu (paper Section 3.1 V_xc,
+// Section 3.2 B3LYP, Section 6 AO recomputation):
+//   GEMM1  T = Phi D            (M = 128 points, N = K = nbf padded to 16)
+//   rho_p = sum_n T_pn phi_pn,  grad rho_p = 2 sum_n T_pn grad phi_pn
+//   GEMM2  V' += Phi^T X        (M = 128 AO rows, N = nbf padded, K = points)
+// Split products (Ootomo & Yokota 2022): a = a_hi + a_lo with a_hi the TF32
+// rounding of a; a b ~= a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32.
+//
+// All tcgen05 operands are K-major in the no-swizzle core-matrix layout: a
+// core is 8 rows x 16 bytes (4 FP32 values along K), 128 contiguous bytes;
+// core (row group g, K chunk c) sits at g * SBO + c * 128.  GEMM1 contracts
+// over AOs (Phi stored point-row / AO-column), GEMM2 over points (Phi^T and X
+// stored AO-row / point-column), so Phi is written in both arrangements.
+//
+// One thread block (256 threads) owns a molecule's share of 128-point grid
+// blocks and keeps V' in tensor memory across all of them.  Per block:
+//   A  radial parts g = sum c e^(-a r^2), g' = sum -2ac e^(-a r^2) per (shell, point) -> smem
+//   B  Phi (hi, lo) in GEMM1 layout;  one thread issues GEMM1 (3 MMAs per K step)
+//   D  after the commit barrier: each thread reads its point's T row from TMEM,
+//      forms rho, grad rho; B3LYP per point; coefficients to smem
+//   F  per half block (64 points): Phi^T and X (hi, lo) in GEMM2 layout; GEMM2
+// Waits on the MMA barriers are bounded: on expiry the block records an error
+// flag, waits (bounded) once more, frees its tensor memory and returns.
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "xc.cuh"
+
+#define TC_BP 128
+#define TC_NPMAX 80     // padded basis size this kernel handles
+#define TC_NSHMAX 60    // shells this kernel handles
+#define TC_TMEM_COLS 256
+#define TC_SPIN_LIMIT 50000000
+
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for sm_100-family tcgen05
+    return d;                // no swizzle, base offset 0, relative LBO
+}
+
+// kind::tf32 instruction descriptor: D F32, A/B TF32, both K-major, M and N.
+__device__ __forceinline__ uint32_t idesc(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(id), "r"(acc)
+                 : "memory");
+}
+
+__device__ __forceinline__ void commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// Bounded wait for the given phase; returns false on expiry.
+__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t phase) {
+    uint32_t done = 0;
+    for (int it = 0; it < TC_SPIN_LIMIT && !done; it++) {
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(smem_u32(bar)), "r"(phase)
+                     : "memory");
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ void ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void split4(const float *v, float4 &hi, float4 &lo) {
+    hi.x = tf32_hi(v[0]); hi.y = tf32_hi(v[1]); hi.z = tf32_hi(v[2]); hi.w = tf32_hi(v[3]);
+    lo.x = v[0] - hi.x; lo.y = v[1] - hi.y; lo.z = v[2] - hi.z; lo.w = v[3] - hi.w;
+}
+
+// byte offset of element (row, k) in a K-major core layout with row-group stride sg
+__device__ __forceinline__ uint32_t coff(int row, int k, uint32_t sg) {
+    return (uint32_t)(row >> 3) * sg + (uint32_t)(k >> 2) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 3) * 4u;
+}
+
+}  // namespace tc
+
+struct TcSmem {
+    // byte offsets inside the dynamic shared buffer
+    uint32_t D_hi, D_lo, R_g, R_gp, work, pts, coef, part, shf, shi;
+    uint32_t total;
+};
+
+__host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
+    TcSmem s;
+    uint32_t o = 0;
+    const uint32_t dsz = (uint32_t)np * np * 4;
+    s.D_hi = o; o += dsz;
+    s.D_lo = o; o += dsz;
+    s.R_g = o; o += (uint32_t)nsh * TC_BP * 4;
+    s.R_gp = o; o += (uint32_t)nsh * TC_BP * 4;
+    o = (o + 1023) & ~1023u;
+    s.work = o;
+    // GEMM1: Phi hi, lo (128 x np); GEMM2: Phi^T hi, lo and X hi, lo (np x 64 each)
+    // plus room for GEMM2's 128-row A reads past the last buffer.
+    uint32_t w1 = 2u * TC_BP * np * 4;
+    uint32_t w2 = 4u * np * 64 * 4 + (uint32_t)(128 - np) * 64 * 4;
+    o += (w1 > w2 ? w1 : w2);
+    s.pts = o; o += 4 * TC_BP * 4;
+    s.coef = o; o += 4 * TC_BP * 4;
+    s.part = o; o += 2 * 4 * TC_BP * 4;
+    s.shf = o; o += (uint32_t)nsh * 8 * 4;  // per shell: R_owner0 - C (3), R_owner1 - C (3), pad
+    s.shi = o; o += (uint32_t)np * 2 * 4;   // per AO: shell, component
+    s.total = o;
+    return s;
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar1, bar2;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail;
+    __shared__ int owner_h[TC_BP];
+    const int m = blockIdx.y, chunk = blockIdx.x;
+    const MolDesc md = b.mol[m];
+    if (mode == 0 && !b.st[m].active) return;
+    const int n = md.nbf, nsh = md.nsh;
+    const int np = (n + 15) & ~15;
+    const TcSmem L = tc_layout(np, nsh);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    unsigned char *sm = smem;
+    float *Rg = (float *)(sm + L.R_g), *Rgp = (float *)(sm + L.R_gp);
+    float *pt = (float *)(sm + L.pts), *cf = (float *)(sm + L.coef), *part = (float *)(sm + L.part);
+    float *shf = (float *)(sm + L.shf);
+    int *shi = (int *)(sm + L.shi);
+    const uint32_t sg1 = (uint32_t)(np / 4) * 128u;  // row-group stride, K = np (GEMM1 A and B)
+    const uint32_t sg2 = 16u * 128u;                  // row-group stride, K = 64 points (GEMM2)
+
+    // ---- per-block constants: D (hi, lo) as GEMM1's B (rows nu, K = mu), shells, AO map
+    const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
+    for (int i = t; i < np * np / 4; i += blockDim.x) {
+        const int row = i / (np / 4), kc = i % (np / 4);
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int k = kc * 4 + j;
+            v[j] = (row < n && k < n) ? (float)D[row * n + k] : 0.f;
+        }
+        float4 hi, lo;
+        tc::split4(v, hi, lo);
+        *(float4 *)(sm + L.D_hi + tc::coff(row, kc * 4, sg1)) = hi;
+        *(float4 *)(sm + L.D_lo + tc::coff(row, kc * 4, sg1)) = lo;
+    }
+    for (int s = t; s < nsh; s += blockDim.x) {
+        const int g = md.sh0 + s;
+        const int l = b.sh_l[g], a0 = b.sh_ao0[g];
+        for (int c = 0; c < (l ? 3 : 1); c++) {
+            shi[(a0 + c) * 2] = s;
+            shi[(a0 + c) * 2 + 1] = l ? c : -1;  // -1: s function
+        }
+    }
+    for (int mu = n + t; mu < np; mu += blockDim.x) {
+        shi[mu * 2] = -1;
+        shi[mu * 2 + 1] = -1;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar1)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar2)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t tT = tmem, tV = tmem + TC_NPMAX;  // column bases of T (GEMM1) and V (GEMM2)
+    const uint32_t id1 = tc::idesc(128, np), id2 = tc::idesc(128, np);
+    const uint32_t su = tc::smem_u32(sm);
+    uint32_t ph1 = 0, ph2 = 0, v_started = 0;
+    double exc = 0.0;
+
+    const float *gxp = (const float *)b.gx + md.pts0, *gyp = (const float *)b.gy + md.pts0;
+    const float *gzp = (const float *)b.gz + md.pts0, *gwp = (const float *)b.gw + md.pts0;
+    bool failed = false;
+    const int npa = b.n_rad * b.n_theta * b.n_phi;
+    for (int blk = chunk; blk < md.nblk && !failed; blk += nchunk) {
+        const long long p0 = (long long)blk * TC_BP;
+        const int own0 = min((int)(p0 / npa), md.natom - 1);
+        if (t < TC_BP) {
+            // point offsets from their own nucleus; the owner is folded into the
+            // offset (owner 0 or 1 of this block) by adding R_owner1 - R_owner0
+            const int h = min((int)((p0 + t) / npa), md.natom - 1) - own0;
+            float ox = gxp[p0 + t], oy = gyp[p0 + t], oz = gzp[p0 + t];
+            pt[t] = ox;
+            pt[TC_BP + t] = oy;
+            pt[2 * TC_BP + t] = oz;
+            pt[3 * TC_BP + t] = gwp[p0 + t];
+            owner_h[t] = h;
+        }
+        for (int i = t; i < 2 * nsh; i += blockDim.x) {
+            const int h = i / nsh, s = i % nsh;
+            const int A = min(own0 + h, md.natom - 1);
+            const double *ra = b.axyz + (md.atom0 + A) * 3, *rc = b.sh_xyz + (md.sh0 + s) * 3;
+            shf[s * 8 + h * 3 + 0] = (float)(ra[0] - rc[0]);
+            shf[s * 8 + h * 3 + 1] = (float)(ra[1] - rc[1]);
+            shf[s * 8 + h * 3 + 2] = (float)(ra[2] - rc[2]);
+        }
+        __syncthreads();
+        // ---- A: radial parts
+        for (int i = t; i < nsh * TC_BP; i += blockDim.x) {
+            const int s = i / TC_BP, p = i % TC_BP;
+            const int g = md.sh0 + s;
+            const float *dl = shf + s * 8 + owner_h[p] * 3;
+            const float dx = dl[0] + pt[p], dy = dl[1] + pt[TC_BP + p], dz = dl[2] + pt[2 * TC_BP + p];
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            float gg = 0.f, gp = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float a = (float)b.sh_ex[g * 3 + k];
+                const float e = (float)b.sh_co[g * 3 + k] * __expf(-a * r2);
+                gg += e;
+                gp -= 2.f * a * e;
+            }
+            Rg[s * TC_BP + p] = gg;
+            Rgp[s * TC_BP + p] = gp;
+        }
+        __syncthreads();
+        // ---- B: Phi (points x AOs) for GEMM1, hi and lo
+        {
+            const uint32_t phi_hi = L.work, phi_lo = L.work + (uint32_t)TC_BP * np * 4;
+            const int nitem = TC_BP * (np / 4);
+            for (int i = t; i < nitem; i += blockDim.x) {
+                // lanes: 8 consecutive points x 4 consecutive AO chunks (conflict-free 16-byte stores)
+                const int l = i & 31, wi = i >> 5;
+                const int pg = wi % (TC_BP / 8), cg = wi / (TC_BP / 8);
+                const int p = pg * 8 + (l & 7), kc = cg * 4 + (l >> 3);
+                float v[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int mu = kc * 4 + j;
+                    const int s = shi[mu * 2], c = shi[mu * 2 + 1];
+                    float val = 0.f;
+                    if (s >= 0) {
+                        const float gg = Rg[s * TC_BP + p];
+                        val = (c < 0) ? gg : (shf[s * 8 + owner_h[p] * 3 + c] + pt[c * TC_BP + p]) * gg;
+                    }
+                    v[j] = val;
+                }
+                float4 hi, lo;
+                tc::split4(v, hi, lo);
+                *(float4 *)(sm + phi_hi + tc::coff(p, kc * 4, sg1)) = hi;
+                *(float4 *)(sm + phi_lo + tc::coff(p, kc * 4, sg1)) = lo;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (t == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int s = 0; s < np / 8; s++) {
+                    const uint32_t ka = 2u * s * 128u;
+                    const uint64_t ah = tc::sdesc(su + phi_hi + ka, 128, sg1), al = tc::sdesc(su + phi_lo + ka, 128, sg1);
+                    const uint64_t bh = tc::sdesc(su + L.D_hi + ka, 128, sg1), bl = tc::sdesc(su + L.D_lo + ka, 128, sg1);
+                    tc::mma(tT, ah, bh, id1, s > 0);
+                    tc::mma(tT, ah, bl, id1, 1);
+                    tc::mma(tT, al, bh, id1, 1);
+                }
+                tc::commit(&bar1);
+            }
+        }
+        // ---- D: density from the T rows
+        // every thread waits (bounded); the block agrees on the outcome
+        const bool ok1 = __syncthreads_and(tc::wait(&bar1, ph1));
+        ph1 ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok1) {
+            failed = true;
+            break;
+        }
+        {
+            const int q = warp & 3, h = warp >> 2;
+            const int p = q * 32 + lane;
+            const float px = pt[p], py = pt[TC_BP + p], pz = pt[2 * TC_BP + p];
+            const int hp = owner_h[p];
+            float rho = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+            const int c0 = h * (np / 2), c1 = c0 + np / 2;
+            for (int cc = c0; cc < c1; cc += 8) {
+                float tv[8];
+                tc::ld8(tT + ((uint32_t)(q * 32) << 16) + cc, tv);
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int nu = cc + j;
+                    const int s = shi[nu * 2], c = shi[nu * 2 + 1];
+                    if (s < 0) continue;
+                    const float gg = Rg[s * TC_BP + p], gp = Rgp[s * TC_BP + p];
+                    const float *dl = shf + s * 8 + hp * 3;
+                    const float dx = dl[0] + px, dy = dl[1] + py, dz = dl[2] + pz;
+                    float f, fx, fy, fz;
+                    if (c < 0) {
+                        f = gg; fx = gp * dx; fy = gp * dy; fz = gp * dz;
+                    } else {
+                        const float dc = c == 0 ? dx : (c == 1 ? dy : dz);
+                        f = dc * gg;
+                        fx = gp * dc * dx + (c == 0 ? gg : 0.f);
+                        fy = gp * dc * dy + (c == 1 ? gg : 0.f);
+                        fz = gp * dc * dz + (c == 2 ? gg : 0.f);
+                    }
+                    rho += tv[j] * f;
+                    rx += tv[j] * fx;
+                    ry += tv[j] * fy;
+                    rz += tv[j] * fz;
+                }
+            }
+            part[(h * 4 + 0) * TC_BP + p] = rho;
+            part[(h * 4 + 1) * TC_BP + p] = rx;
+            part[(h * 4 + 2) * TC_BP + p] = ry;
+            part[(h * 4 + 3) * TC_BP + p] = rz;
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (t < TC_BP) {
+                const float r = part[t] + part[4 * TC_BP + t];
+                const float gx = 2.f * (part[TC_BP + t] + part[5 * TC_BP + t]);
+                const float gy = 2.f * (part[2 * TC_BP + t] + part[6 * TC_BP + t]);
+                const float gz = 2.f * (part[3 * TC_BP + t] + part[7 * TC_BP + t]);
+                const float w = pt[3 * TC_BP + t];
+                float e = 0.f, vr = 0.f, vs = 0.f;
+                if (w != 0.f) xc::b3lyp<float>(r, gx * gx + gy * gy + gz * gz, e, vr, vs);
+                exc += (double)w * (double)e;
+                cf[t] = 0.5f * w * vr;
+                cf[TC_BP + t] = 2.f * w * vs * gx;
+                cf[2 * TC_BP + t] = 2.f * w * vs * gy;
+                cf[3 * TC_BP + t] = 2.f * w * vs * gz;
+            }
+            __syncthreads();
+        }
+        // ---- F: GEMM2 operands per half block, then GEMM2
+        for (int hf = 0; hf < 2; hf++) {
+            const uint32_t at_hi = L.work, at_lo = at_hi + (uint32_t)np * 64 * 4;
+            const uint32_t x_hi = at_lo + (uint32_t)np * 64 * 4, x_lo = x_hi + (uint32_t)np * 64 * 4;
+            const int nitem = np * 16;  // rows (AOs) x 16 chunks of 4 points
+            for (int i = t; i < nitem; i += blockDim.x) {
+                // lanes: 8 consecutive rows x 4 consecutive point chunks
+                const int l = i & 31, wi = i >> 5;
+                const int rg = wi % (np / 8), pc4 = wi / (np / 8);
+                const int row = rg * 8 + (l & 7), pc = pc4 * 4 + (l >> 3);
+                const int s = shi[row * 2], c = shi[row * 2 + 1];
+                float fv[4], xv[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int p = hf * 64 + pc * 4 + j;
+                    float f = 0.f, x = 0.f;
+                    if (s >= 0) {
+                        const float gg = Rg[s * TC_BP + p], gp = Rgp[s * TC_BP + p];
+                        const float *dl = shf + s * 8 + owner_h[p] * 3;
+                        const float dx = dl[0] + pt[p], dy = dl[1] + pt[TC_BP + p], dz = dl[2] + pt[2 * TC_BP + p];
+                        const float a = cf[p], bx = cf[TC_BP + p], by = cf[2 * TC_BP + p], bz = cf[3 * TC_BP + p];
+                        const float bd = bx * dx + by * dy + bz * dz;
+                        if (c < 0) {
+                            f = gg;
+                            x = a * gg + gp * bd;
+                        } else {
+                            const float dc = c == 0 ? dx : (c == 1 ? dy : dz);
+                            const float bc = c == 0 ? bx : (c == 1 ? by : bz);
+                            f = dc * gg;
+                            x = a * f + gp * dc * bd + bc * gg;
+                        }
+                    }
+                    fv[j] = f;
+                    xv[j] = x;
+                }
+                float4 hi, lo;
+                tc::split4(fv, hi, lo);
+                *(float4 *)(sm + at_hi + tc::coff(row, pc * 4, sg2)) = hi;
+                *(float4 *)(sm + at_lo + tc::coff(row, pc * 4, sg2)) = lo;
+                tc::split4(xv, hi, lo);
+                *(float4 *)(sm + x_hi + tc::coff(row, pc * 4, sg2)) = hi;
+                *(float4 *)(sm + x_lo + tc::coff(row, pc * 4, sg2)) = lo;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (t == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int s = 0; s < 8; s++) {
+                    const uint32_t ka = 2u * s * 128u;
+                    const uint64_t ah = tc::sdesc(su + at_hi + ka, 128, sg2), al = tc::sdesc(su + at_lo + ka, 128, sg2);
+                    const uint64_t bh = tc::sdesc(su + x_hi + ka, 128, sg2), bl = tc::sdesc(su + x_lo + ka, 128, sg2);
+                    tc::mma(tV, ah, bh, id2, v_started);
+                    v_started = 1;
+                    tc::mma(tV, ah, bl, id2, 1);
+                    tc::mma(tV, al, bh, id2, 1);
+                }
+                tc::commit(&bar2);
+            }
+            const bool ok2 = __syncthreads_and(tc::wait(&bar2, ph2));
+            ph2 ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok2) {
+                failed = true;
+                break;
+            }
+        }
+        __syncthreads();
+    }
+    if (failed && t == 0) s_fail = 1;
+    __syncthreads();
+    // ---- flush V' (rows mu = TMEM lanes, columns nu) and E_xc
+    const bool started = __syncthreads_or(v_started);
+    if (!s_fail && started) {
+        const int q = warp & 3, h = warp >> 2;
+        const int mu = q * 32 + lane;
+        TA *gV;
+        if constexpr (sizeof(TA) == 8) gV = (TA *)(b.accd + md.acc0) + 2 * n * n;
+        else gV = (TA *)(b.accf + md.acc0) + 2 * n * n;
+        const int c0 = h * (np / 2), c1 = c0 + np / 2;
+        for (int cc = c0; cc < c1; cc += 8) {
+            float v[8];
+            tc::ld8(tV + ((uint32_t)(q * 32) << 16) + cc, v);
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int nu = cc + j;
+                if (mu < n && nu < n && v[j] != 0.f) atomicAdd(&gV[mu * n + nu], (TA)v[j]);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) exc += __shfl_xor_sync(0xffffffffu, exc, o);
+    if (lane == 0 && exc != 0.0) atomicAdd(&b.st[m].Exc, exc);
+    if (s_fail && t == 0) {
+        atomicOr(&b.st[m].err_flag, 4);
+        // give in-flight MMAs a bounded chance to drain before freeing tensor memory
+        tc::wait(&bar1, ph1);
+        tc::wait(&bar2, ph2);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+}
+
+bool grid_xc_tc_supported(int max_nbf, int max_nsh) {
+    return ((max_nbf + 15) & ~15) <= TC_NPMAX && max_nsh <= TC_NSHMAX;
+}
+
+void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
+                       cudaStream_t s) {
+    const int np = (max_nbf + 15) & ~15;
+    const size_t sm = tc_layout(np, max_nsh).total + 1024;
+    if (acc_fp64) {
+        cudaFuncSetAttribute(grid_xc_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        grid_xc_tc_kernel<double><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode);
+    } else {
+        cudaFuncSetAttribute(grid_xc_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        grid_xc_tc_kernel<float><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode);
+    }
+}

@@ -11,15 +11,24 @@ void launch_schwarz(const DevBatch &b, int ncand, cudaStream_t s);
 void launch_compact_pairs(const DevBatch &b, cudaStream_t s);
 void launch_row_count(const DevBatch &b, int ncand, cudaStream_t s);
 void launch_row_scan(const DevBatch &b, cudaStream_t s);
+void launch_pair_prim(const DevBatch &b, int ncand, int fp32, cudaStream_t s);
 void launch_eri_store(const DevBatch &b, int ncand, int fp32, cudaStream_t s);
 int launch_grid_build(const DevBatch &b, long long nblk_total, const int *blk_mol, const double *rad,
                       const double *ang, int max_atoms, cudaStream_t s);
 // J/K from the packed store.  acc_fp64: accumulate in FP64 (accd) instead of
 // FP32 (accf); mode 0: molecules still iterating, 1: every molecule.
 void launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, cudaStream_t s);
+// Final-step correction of the FP32 store: quartets with Q_pq Q_rs >= theta
+// recomputed in FP64, (I64 - I32) contracted with D into the FP64 accumulators.
+void launch_jk_correct(const DevBatch &b, int nchunk, double theta, int max_nbf, cudaStream_t s);
 // AO + density + B3LYP + V_xc on the grid; acc_fp64 and mode as above.
 void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
                     cudaStream_t s);
+// Tensor-core (tcgen05, 3xTF32) version for the mixed path; supported when
+// the padded basis is <= 80 and a molecule has <= 60 shells.
+bool grid_xc_tc_supported(int max_nbf, int max_nsh);
+void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
+                       cudaStream_t s);
 // Per-molecule FP64 SCF stages.
 void launch_scf_init(const DevBatch &b, cudaStream_t s);
 void launch_scf_guess(const DevBatch &b, cudaStream_t s);

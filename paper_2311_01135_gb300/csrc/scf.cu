@@ -129,8 +129,36 @@ __global__ void scf_guess_kernel(DevBatch b) {
     }
     __syncthreads();
     double smin = sm.w[0];
-    int sw2 = diag_fock(H, X, tmp, C, sm, n);
-    density_from_C(C, D, n, md.nocc);
+    int sw2 = 0;
+    if (b.guess == 1) {
+        // core Hamiltonian: diagonalise X^T H X, occupy the lowest n_occ
+        sw2 = diag_fock(H, X, tmp, C, sm, n);
+        density_from_C(C, D, n, md.nocc);
+    } else {
+        // superposed neutral atoms: per heavy atom D_ss = 2 S_ss^-1 over (1s, 2s)
+        // and (Z - 4)/3 on each 2p; per H 1/S_11; zero between atoms
+        for (int i = threadIdx.x; i < nn; i += blockDim.x) D[i] = 0.0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int i = 0;
+            for (int a = 0; a < md.natom; a++) {
+                const int z = b.Z[md.atom0 + a];
+                if (z == 1) {
+                    D[i * n + i] = 1.0 / S[i * n + i];
+                    i += 1;
+                    continue;
+                }
+                const double s00 = S[i * n + i], s01 = S[i * n + i + 1], s11 = S[(i + 1) * n + i + 1];
+                const double det = s00 * s11 - s01 * s01;
+                D[i * n + i] = 2.0 * s11 / det;
+                D[i * n + i + 1] = D[(i + 1) * n + i] = -2.0 * s01 / det;
+                D[(i + 1) * n + i + 1] = 2.0 * s00 / det;
+                for (int k = 2; k < 5; k++) D[(i + k) * n + i + k] = (z - 4) / 3.0;
+                i += 5;
+            }
+        }
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         MolState &st = b.st[m];
         st.smin = smin;

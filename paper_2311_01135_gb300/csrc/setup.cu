@@ -423,19 +423,66 @@ __global__ void row_scan_kernel(DevBatch b) {
 
 void launch_row_scan(const DevBatch &b, cudaStream_t s) { row_scan_kernel<<<b.nmol, 256, 0, s>>>(b); }
 
+// ------------------------------------------------------ primitive pairs
+// For every kept pair (P, Q) and primitive pair (a, b), in FP64:
+//   K = c_a c_b exp(-ab/(a+b) |A-B|^2), zeta = a + b, P - A = b (B - A)/zeta,
+// stored in the ERI precision.  The FP32 ERI path then never forms an
+// exponent or a Boys argument from rounded absolute coordinates.
+template <typename T>
+__global__ void pair_prim_kernel(DevBatch b, int ncand_total, void *dst) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ncand_total) return;
+    int m = b.cand_mol[g];
+    const MolDesc md = b.mol[m];
+    int r = g - md.pair0;
+    if (r >= b.npair[m]) return;
+    int2 pq = b.kpair[md.pair0 + r];
+    int P = md.sh0 + pq.x, Q = md.sh0 + pq.y;
+    double AB[3], ab2 = 0;
+    for (int k = 0; k < 3; k++) {
+        AB[k] = b.sh_xyz[P * 3 + k] - b.sh_xyz[Q * 3 + k];
+        ab2 += AB[k] * AB[k];
+    }
+    eri::PrimPair<T> *out = (eri::PrimPair<T> *)dst + (long long)(md.pair0 + r) * (RKS_MAXP * RKS_MAXP);
+    for (int ia = 0; ia < RKS_MAXP; ia++)
+        for (int ib = 0; ib < RKS_MAXP; ib++) {
+            const double a = b.sh_ex[P * 3 + ia], bb = b.sh_ex[Q * 3 + ib];
+            const double z = a + bb;
+            eri::PrimPair<T> pp;
+            pp.K = (T)(b.sh_co[P * 3 + ia] * b.sh_co[Q * 3 + ib] * exp(-a * bb / z * ab2));
+            pp.z = (T)z;
+            pp.px = (T)(-bb / z * AB[0]);
+            pp.py = (T)(-bb / z * AB[1]);
+            pp.pz = (T)(-bb / z * AB[2]);
+            out[ia * RKS_MAXP + ib] = pp;
+        }
+}
+
+void launch_pair_prim(const DevBatch &b, int ncand, int fp32, cudaStream_t s) {
+    if (fp32) {
+        pair_prim_kernel<float><<<(ncand + 127) / 128, 128, 0, s>>>(b, ncand, b.pairprim);
+        if (b.pairprim64) pair_prim_kernel<double><<<(ncand + 127) / 128, 128, 0, s>>>(b, ncand, b.pairprim64);
+    } else {
+        pair_prim_kernel<double><<<(ncand + 127) / 128, 128, 0, s>>>(b, ncand, b.pairprim);
+    }
+}
+
 // ------------------------------------------------------------ ERI store
 template <typename T, int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void quartet_to_store(const DevBatch &b, int P, int Q, int R, int S,
-                                                 const T *tab, T *dst) {
-    T A[3], B[3], C[3], D[3];
-    eri::Prim3<T> pa, pb, pc, pd;
-    load_shell<T>(b, P, A, pa);
-    load_shell<T>(b, Q, B, pb);
-    load_shell<T>(b, R, C, pc);
-    load_shell<T>(b, S, D, pd);
+__device__ __forceinline__ void quartet_to_store(const DevBatch &b, const MolDesc &md, int r, int s, int P, int Q,
+                                                 int R, int S, const T *tab, T *dst) {
+    T AB[3], CD[3], AC[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        AB[k] = (T)(b.sh_xyz[P * 3 + k] - b.sh_xyz[Q * 3 + k]);
+        CD[k] = (T)(b.sh_xyz[R * 3 + k] - b.sh_xyz[S * 3 + k]);
+        AC[k] = (T)(b.sh_xyz[P * 3 + k] - b.sh_xyz[R * 3 + k]);
+    }
+    const eri::PrimPair<T> *pp = (const eri::PrimPair<T> *)b.pairprim;
     constexpr int N = (LA ? 3 : 1) * (LB ? 3 : 1) * (LC ? 3 : 1) * (LD ? 3 : 1);
     T out[N];
-    eri::quartet<T, LA, LB, LC, LD>(A, B, C, D, pa, pb, pc, pd, tab, out);
+    eri::quartet_pd<T, LA, LB, LC, LD>(pp + (long long)(md.pair0 + r) * 9, pp + (long long)(md.pair0 + s) * 9, AB,
+                                       CD, AC, tab, out);
 #pragma unroll
     for (int x = 0; x < N; x++) dst[x] = out[x];
 }
@@ -483,12 +530,12 @@ __global__ void eri_store_kernel(DevBatch b, int ncand_total) {
             int lR = b.sh_l[R], lS = b.sh_l[S];
             int cls = (lP << 3) | (lQ << 2) | (lR << 1) | lS;
             switch (cls) {
-            case 0x0: quartet_to_store<T, 0, 0, 0, 0>(b, P, Q, R, S, tab, dst); break;
-            case 0x8: quartet_to_store<T, 1, 0, 0, 0>(b, P, Q, R, S, tab, dst); break;
-            case 0xA: quartet_to_store<T, 1, 0, 1, 0>(b, P, Q, R, S, tab, dst); break;
-            case 0xC: quartet_to_store<T, 1, 1, 0, 0>(b, P, Q, R, S, tab, dst); break;
-            case 0xE: quartet_to_store<T, 1, 1, 1, 0>(b, P, Q, R, S, tab, dst); break;
-            case 0xF: quartet_to_store<T, 1, 1, 1, 1>(b, P, Q, R, S, tab, dst); break;
+            case 0x0: quartet_to_store<T, 0, 0, 0, 0>(b, md, r, s, P, Q, R, S, tab, dst); break;
+            case 0x8: quartet_to_store<T, 1, 0, 0, 0>(b, md, r, s, P, Q, R, S, tab, dst); break;
+            case 0xA: quartet_to_store<T, 1, 0, 1, 0>(b, md, r, s, P, Q, R, S, tab, dst); break;
+            case 0xC: quartet_to_store<T, 1, 1, 0, 0>(b, md, r, s, P, Q, R, S, tab, dst); break;
+            case 0xE: quartet_to_store<T, 1, 1, 1, 0>(b, md, r, s, P, Q, R, S, tab, dst); break;
+            case 0xF: quartet_to_store<T, 1, 1, 1, 1>(b, md, r, s, P, Q, R, S, tab, dst); break;
             default: atomicOr(&b.st[m].err_flag, 2); break;  // class outside the packing order
             }
         }
@@ -506,6 +553,10 @@ void launch_eri_store(const DevBatch &b, int ncand, int fp32, cudaStream_t s) {
 // ------------------------------------------------------------------ grid
 // Thread per grid point (blocks of 128 belong to one molecule).  Point p of a
 // molecule: atom A = p / (n_rad n_ang), then radial index, then angular index.
+// Points are stored as offsets r * u from their own nucleus (A is implied by
+// the index), so every point-to-centre vector is formed as
+// (R_A - R_B) [from FP64 coordinates] + offset and keeps full relative
+// precision near nuclei even in FP32.
 // Becke partition (A. D. Becke, J. Chem. Phys. 88, 2547 (1988)):
 //   mu_BC = (|r - R_B| - |r - R_C|)/|R_B - R_C|, f = p(p(p(mu))), p(x) = 1.5x - 0.5x^3,
 //   s = (1 - f)/2, P_B = prod_{C != B} s(mu_BC), w = w_rad w_ang P_A / sum_B P_B.
@@ -516,14 +567,12 @@ __global__ void grid_build_kernel(DevBatch b, const int *blk_mol, const double *
     int m = blk_mol[blk];
     const MolDesc md = b.mol[m];
     const int nat = md.natom;
-    T *ax = (T *)smem_raw;              // [nat][3]
-    T *invR = ax + 3 * nat;             // [nat][nat]
-    for (int i = threadIdx.x; i < nat * 3; i += blockDim.x) ax[i] = (T)b.axyz[(md.atom0) * 3 + i];
-    __syncthreads();
+    T *invR = (T *)smem_raw;            // [nat][nat]
+    const double *ax = b.axyz + md.atom0 * 3;
     for (int i = threadIdx.x; i < nat * nat; i += blockDim.x) {
         int B = i / nat, C = i % nat;
-        T dx = ax[B * 3] - ax[C * 3], dy = ax[B * 3 + 1] - ax[C * 3 + 1], dz = ax[B * 3 + 2] - ax[C * 3 + 2];
-        invR[i] = (B == C) ? (T)0 : (T)1 / dev_sqrt(dx * dx + dy * dy + dz * dz);
+        double dx = ax[B * 3] - ax[C * 3], dy = ax[B * 3 + 1] - ax[C * 3 + 1], dz = ax[B * 3 + 2] - ax[C * 3 + 2];
+        invR[i] = (B == C) ? (T)0 : (T)(1.0 / sqrt(dx * dx + dy * dy + dz * dz));
     }
     __syncthreads();
     long long gp = blk * RKS_PTS_BLOCK + threadIdx.x;  // global point index
@@ -531,8 +580,8 @@ __global__ void grid_build_kernel(DevBatch b, const int *blk_mol, const double *
     T *gx = (T *)b.gx, *gy = (T *)b.gy, *gz = (T *)b.gz, *gw = (T *)b.gw;
     const int nang = b.n_theta * b.n_phi;
     const int npa = b.n_rad * nang;
-    if (lp >= md.npts) {  // padding: weight 0 at the first nucleus
-        gx[gp] = ax[0]; gy[gp] = ax[1]; gz[gp] = ax[2]; gw[gp] = (T)0;
+    if (lp >= md.npts) {  // padding: weight 0 at the last nucleus (owner index clamps there)
+        gx[gp] = (T)0; gy[gp] = (T)0; gz[gp] = (T)0; gw[gp] = (T)0;
         return;
     }
     int A = (int)(lp / npa);
@@ -542,11 +591,12 @@ __global__ void grid_build_kernel(DevBatch b, const int *blk_mol, const double *
     int e = z == 1 ? 0 : (z == 6 ? 1 : (z == 7 ? 2 : (z == 8 ? 3 : 4)));
     double r = rad[(e * b.n_rad + ir) * 2 + 0], wr = rad[(e * b.n_rad + ir) * 2 + 1];
     double dxn = ang[ia * 4 + 0], dyn = ang[ia * 4 + 1], dzn = ang[ia * 4 + 2], wa = ang[ia * 4 + 3];
-    T px = ax[A * 3] + (T)(r * dxn), py = ax[A * 3 + 1] + (T)(r * dyn), pz = ax[A * 3 + 2] + (T)(r * dzn);
+    const T ox = (T)(r * dxn), oy = (T)(r * dyn), oz = (T)(r * dzn);
     // distances to every nucleus (local array)
     T dist[128];
     for (int B = 0; B < nat; B++) {
-        T dx = px - ax[B * 3], dy = py - ax[B * 3 + 1], dz = pz - ax[B * 3 + 2];
+        T dx = (T)(ax[A * 3] - ax[B * 3]) + ox, dy = (T)(ax[A * 3 + 1] - ax[B * 3 + 1]) + oy;
+        T dz = (T)(ax[A * 3 + 2] - ax[B * 3 + 2]) + oz;
         dist[B] = dev_sqrt(dx * dx + dy * dy + dz * dz);
     }
     T sumP = 0, PA = 0;
@@ -562,13 +612,13 @@ __global__ void grid_build_kernel(DevBatch b, const int *blk_mol, const double *
         sumP += P;
         if (B == A) PA = P;
     }
-    gx[gp] = px; gy[gp] = py; gz[gp] = pz;
+    gx[gp] = ox; gy[gp] = oy; gz[gp] = oz;
     gw[gp] = (T)(wr * wa) * PA / sumP;
 }
 
 int launch_grid_build(const DevBatch &b, long long nblk_total, const int *blk_mol, const double *rad,
                       const double *ang, int max_atoms, cudaStream_t s) {
-    size_t sm = (size_t)(3 * max_atoms + max_atoms * max_atoms) * (b.precision ? sizeof(float) : sizeof(double));
+    size_t sm = (size_t)(max_atoms * max_atoms) * (b.precision ? sizeof(float) : sizeof(double));
     if (b.precision) {
         cudaFuncSetAttribute(grid_build_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         grid_build_kernel<float><<<(unsigned)nblk_total, RKS_PTS_BLOCK, sm, s>>>(b, blk_mol, rad, ang);

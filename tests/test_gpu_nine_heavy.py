@@ -1,0 +1,117 @@
+"""GPU parity on the seeded 9-heavy-atom molecule (seed 1) and a few workload
+molecules (9-11 heavy atoms, seed 2): stage by stage at a fixed density
+(the oracle's core-Hamiltonian guess), then the whole SCF.
+
+Tolerances as in test_gpu_parity.py; stage values at a fixed density use the
+FP64 path (<= 1e-10 abs on J/K/V_xc/E) and the mixed path (<= 2e-5 abs on the
+energy at that density, which is not variational there).
+"""
+import numpy as np
+import pytest
+
+import molgen
+
+pytestmark = pytest.mark.gpu
+g = pytest.importorskip("paper_2311_01135_gb300")
+
+
+@pytest.fixture(scope="module")
+def c1():
+    from oracle import scf
+    Z, xyz = molgen.nine_heavy(1)
+    s = scf.System(Z, xyz)
+    D0 = s.core_guess()
+    F0, E0, parts0 = s.fock(D0)
+    return Z, xyz, s, D0, F0, E0, parts0
+
+
+def _schwarz_scale(ps):
+    """Per-element bound |(ij|kl)| <= Q_pq Q_rs of the element's quartet."""
+    qb = ps.q[ps.quart_pairs[:, 0]] * ps.q[ps.quart_pairs[:, 1]]
+    return np.repeat(qb, ps.block)
+
+
+def _check_store(B, s):
+    ps = s.store
+    pairs = B.dump(0, g.RKS_DUMP_PAIRS, np.int32).reshape(-1, 2)
+    assert np.array_equal(pairs, ps.pairs)
+    nq = B.dump(0, g.RKS_DUMP_QUARTETS, np.int32)
+    assert np.array_equal(nq, np.bincount(ps.quart_pairs[:, 0], minlength=len(ps.pairs)))
+    sc = B.dump(0, g.RKS_DUMP_SCALARS)
+    assert sc[7] == 0, "near-tie quartets present"
+    return B.dump(0, g.RKS_DUMP_STORE)
+
+
+def test_c1_setup_and_fock_fp64(c1):
+    Z, xyz, s, D0, F0, E0, parts0 = c1
+    with g.Context(precision=g.RKS_FP64) as c, g.Batch(c, [(Z, xyz)]) as B:
+        B.fock([D0])
+        st = _check_store(B, s)
+        ps = s.store
+        assert np.max(np.abs(st - ps.values) / _schwarz_scale(ps)) < 1e-12
+        for what, ref in ((g.RKS_DUMP_S, s.S), (g.RKS_DUMP_T, s.T), (g.RKS_DUMP_V, s.V)):
+            assert np.max(np.abs(B.matrix(0, what) - ref)) < 1e-11
+        grid = B.dump(0, g.RKS_DUMP_GRID).reshape(-1, 4)
+        assert np.max(np.abs(grid[:, :3] - s.pts)) < 1e-11
+        assert np.max(np.abs(grid[:, 3] - s.w)) < 1e-12 * np.max(s.w)
+        assert np.max(np.abs(B.matrix(0, g.RKS_DUMP_J) - parts0["J"])) < 1e-10
+        assert np.max(np.abs(B.matrix(0, g.RKS_DUMP_K) - parts0["K"])) < 1e-10
+        assert np.max(np.abs(B.matrix(0, g.RKS_DUMP_VXC) - parts0["Vxc"])) < 1e-10
+        sc = B.dump(0, g.RKS_DUMP_SCALARS)
+        assert abs(sc[1] - parts0["Exc"]) < 1e-10
+        assert abs(sc[0] - E0) < 1e-9
+
+
+def test_c1_setup_and_fock_mixed(c1):
+    Z, xyz, s, D0, F0, E0, parts0 = c1
+    with g.Context(precision=g.RKS_MIXED) as c, g.Batch(c, [(Z, xyz)]) as B:
+        B.fock([D0], final_step=True)
+        st = _check_store(B, s)
+        ps = s.store
+        store_err = np.max(np.abs(st - ps.values) / _schwarz_scale(ps))
+        grid = B.dump(0, g.RKS_DUMP_GRID).reshape(-1, 4)
+        J = B.matrix(0, g.RKS_DUMP_J)
+        K = B.matrix(0, g.RKS_DUMP_K)
+        V = B.matrix(0, g.RKS_DUMP_VXC)
+        sc = B.dump(0, g.RKS_DUMP_SCALARS)
+        # energy pieces at D0: Coulomb, exchange, XC
+        dEJ = 0.5 * np.sum(D0 * (J - parts0["J"]))
+        dEK = -0.05 * np.sum(D0 * (K - parts0["K"]))
+        print(f"mixed@D0: store {store_err:.2e} dEJ {dEJ:.2e} dEK {dEK:.2e} dExc {sc[1] - parts0['Exc']:.2e} "
+              f"dE {sc[0] - E0:.2e} |dJ| {np.max(np.abs(J - parts0['J'])):.1e} |dVxc| {np.max(np.abs(V - parts0['Vxc'])):.1e}")
+        assert store_err < 1e-5  # relative to the Schwarz bound; dominated by tiny integrals
+        assert np.max(np.abs(grid[:, 3] - s.w)) < 1e-6 * np.max(s.w)
+        assert np.max(np.abs(J - parts0["J"])) < 2e-5
+        assert np.max(np.abs(K - parts0["K"])) < 2e-5
+        assert np.max(np.abs(V - parts0["Vxc"])) < 2e-5
+        assert abs(sc[0] - E0) < 2e-4
+
+
+@pytest.fixture(scope="module")
+def c1_scf(c1):
+    from oracle import scf
+    Z, xyz, s, *_ = c1
+    return scf.run_scf(s, protocol="fixed", n_iter=20)
+
+
+def test_c1_scf_fp64(c1, c1_scf):
+    Z, xyz, s, *_ = c1
+    r = c1_scf
+    with g.Context(precision=g.RKS_FP64, fixed_iters=20) as c, g.Batch(c, [(Z, xyz)]) as B:
+        B.run()
+        B.sync()
+        o = B.result(0)
+    assert abs(o["E"] - r["E"]) < 1e-8
+    assert np.max(np.abs(o["eps"] - r["eps"])) < 1e-8
+    assert np.max(np.abs(o["D"] - r["D"])) < 1e-7
+
+
+def test_c1_scf_mixed(c1, c1_scf):
+    Z, xyz, s, *_ = c1
+    r = c1_scf
+    with g.Context(precision=g.RKS_MIXED, fixed_iters=20) as c, g.Batch(c, [(Z, xyz)]) as B:
+        B.run()
+        B.sync()
+        o = B.result(0)
+    assert abs(o["E"] - r["E"]) < 1e-5
+    assert abs(o["gap"] - r["gap"]) < 1e-4

@@ -2,7 +2,7 @@
 
 Tolerances (written here, derived from the arithmetic):
 * FP64 path: Boys <= 5e-14 rel; B3LYP e/v <= 1e-12 rel; S/T/V, grid <= 1e-12;
-  ERI store <= 1e-12 relative to the largest element of its block (the oracle
+  ERI store <= 1e-12 relative to the Schwarz bound Q_pq Q_rs of the element (the oracle
   uses McMurchie-Davidson, the kernel Obara-Saika/HGP: different rounding);
   pairs, masks, offsets bit-exact; whole SCF |dE| <= 1e-8 Ha, max|d eps| <= 1e-8,
   max|dD| <= 1e-7.
@@ -83,9 +83,9 @@ def _store_parity(B, m, s, tol_rel):
     assert np.array_equal(roff, np.cumsum(orow)), "row offsets differ"
     st = B.dump(m, g.RKS_DUMP_STORE)
     assert len(st) == ps.size
-    # error relative to the largest magnitude in each block
-    scale = np.repeat(np.maximum.reduceat(np.abs(ps.values), ps.offsets), ps.block)
-    err = np.abs(st - ps.values) / np.maximum(scale, 1e-300)
+    # error relative to the Schwarz bound Q_pq Q_rs of each element's quartet
+    qb = np.repeat(ps.q[ps.quart_pairs[:, 0]] * ps.q[ps.quart_pairs[:, 1]], ps.block)
+    err = np.abs(st - ps.values) / qb
     assert np.max(err) < tol_rel, np.max(err)
 
 

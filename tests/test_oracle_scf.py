@@ -121,6 +121,19 @@ def test_diis_and_plain_iteration_same_fixed_point():
     assert np.max(np.abs(a["D"] - b["D"])) < 1e-6
 
 
+def test_sad_guess_electron_count_and_blocks():
+    """The superposed neutral-atom density holds N_el electrons (tr D S) and is
+    block diagonal by atom; the H block is 1 and a heavy atom's s block is
+    2 S_ss^-1 (fully occupied 1s/2s space)."""
+    Z, xyz = molgen.nine_heavy(1)
+    s = scf.System(Z, xyz, xc=False)
+    D = s.sad_guess()
+    assert np.sum(D * s.S) == pytest.approx(float(np.sum(Z)), abs=1e-12)
+    ss = s.S[0:2, 0:2]
+    assert np.allclose(D[0:2, 0:2] @ ss, 2 * np.eye(2), atol=1e-13)
+    assert D[0, 5] == 0.0
+
+
 def test_fixed_protocol_runs_exactly_n():
     Z, xyz = molgen.h2o()
     s = scf.System(Z, xyz)
