@@ -13,6 +13,7 @@
 #define RKS_MAXP 3          // primitives per STO-3G shell
 #define RKS_PTS_BLOCK 128   // grid points are stored in blocks of this many
 #define RKS_NHIST 64        // energies kept per molecule (paper's std(E[-5:]) flag)
+#define RKS_FIX_CAP 16384   // FP64-recompute list capacity per molecule and quartet class
 
 // Slot (per-molecule) descriptor.  All offsets are element offsets into the
 // batch-wide arrays named in the comments.
@@ -52,6 +53,7 @@ struct MolState {
     int converged;
     int status;             // RKS_STATUS_*
     int eigh_fail;
+    int cp_valid;           // M_CP holds the eigenvectors of the previous X^T F X
     int err_flag;           // device-side bounds / consistency failures
     int n_quartets;
     int near_ties;
@@ -87,6 +89,10 @@ struct DevBatch {
     void *store;            // packed ERIs (float or double)
     void *pairprim;         // per kept pair: 9 primitive-pair records (K, zeta, P - A), float or double
     void *pairprim64;       // FP64 copy for the final-step FP64 recompute of the mixed path (or null)
+    int4 *fixlist;          // per molecule, per quartet class: (row, col, store offset lo, hi) of quartets
+                            // with Q_pq Q_rs >= fix_theta; RKS_FIX_CAP entries per class
+    int *fixcount;          // [nmol][6] entries written (may exceed the capacity: then capped)
+    double fix_theta;
     // grid (SoA, padded blocks; padding points have w = 0)
     void *gx, *gy, *gz, *gw;
     // FP64 matrices

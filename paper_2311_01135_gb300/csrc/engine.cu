@@ -432,6 +432,8 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
     MolDesc *dmol; MolState *dst; int *dZ, *dsa, *dsl, *dsao, *dcm, *dnp, *drnq; double *dax, *dsx, *dse, *dsc, *dcq, *dkq;
     int2 *dcand, *dkp; long long *droff; void *store; void *gx, *gy, *gz, *gw; double *mat, *accd; float *accf;
     void *pairprim, *pairprim64 = nullptr;
+    int4 *fixlist = nullptr;
+    int *fixcount = nullptr;
     if ((rc = dalloc(b, &dmol, nmol)) || (rc = dalloc(b, &dst, nmol)) || (rc = dalloc(b, &dZ, atom_off)) ||
         (rc = dalloc(b, &dax, 3 * atom_off)) || (rc = dalloc(b, &dsa, sh_off)) || (rc = dalloc(b, &dsl, sh_off)) ||
         (rc = dalloc(b, &dsao, sh_off)) || (rc = dalloc(b, &dsx, 3 * sh_off)) || (rc = dalloc(b, &dse, 3 * sh_off)) ||
@@ -441,7 +443,8 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
         (rc = dalloc(b, (unsigned char **)&store, eri_off * esz)) ||
         (rc = dalloc(b, (unsigned char **)&pairprim, pair_off * 9 * 5 * esz)) ||
         (o.precision == RKS_MIXED && o.fix_theta > 0 &&
-         (rc = dalloc(b, (unsigned char **)&pairprim64, pair_off * 9 * 5 * sizeof(double)))) ||
+         ((rc = dalloc(b, (unsigned char **)&pairprim64, pair_off * 9 * 5 * sizeof(double))) ||
+          (rc = dalloc(b, &fixlist, (size_t)nmol * 6 * RKS_FIX_CAP)) || (rc = dalloc(b, &fixcount, (size_t)nmol * 6)))) ||
         (rc = dalloc(b, (unsigned char **)&gx, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gy, pts_off * esz)) ||
         (rc = dalloc(b, (unsigned char **)&gz, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gw, pts_off * esz)) ||
         (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) || (rc = dalloc(b, &accf, acc_off)) ||
@@ -454,6 +457,9 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
     d.kpair = dkp; d.kq = dkq; d.npair = dnp; d.row_nq = drnq; d.row_off = droff; d.store = store;
     d.pairprim = pairprim;
     d.pairprim64 = pairprim64;
+    d.fixlist = fixlist;
+    d.fixcount = fixcount;
+    d.fix_theta = o.fix_theta;
     d.gx = gx; d.gy = gy; d.gz = gz; d.gw = gw; d.mat = mat; d.accd = accd; d.accf = accf;
     cudaStream_t s = ctx->stream;
 #define UP(dst_, src_)                                                                                      \
@@ -506,6 +512,7 @@ extern "C" int rks_batch_setup(rks_batch *b) {
     { StageScope sc(c, "row_scan", 0); launch_row_scan(d, s); }
     { StageScope sc(c, "pair_prim", 0); launch_pair_prim(d, (int)b->ncand, fp32, s); }
     { StageScope sc(c, "eri", 0); launch_eri_store(d, (int)b->ncand, fp32, s); }
+    if (d.fixlist) { StageScope sc(c, "fix_list", 0); launch_fix_list(d, s); }
     { StageScope sc(c, "grid_build", 0); launch_grid_build(d, b->nblk_total, b->blk_mol, c->rad, c->ang, b->max_atoms, s); }
     { StageScope sc(c, "scf_init", 0); launch_scf_init(d, s); }
     { StageScope sc(c, "scf_guess", 0); launch_scf_guess(d, s); }
@@ -528,9 +535,9 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
     launch_reset_exc(d, s);
     const int nchunk_jk = 8;
     { StageScope sc(c, acc_fp64 ? "jk_final" : "jk", 0); launch_jk(d, nchunk_jk, acc_fp64, mode, b->max_nbf, s); }
-    if (acc_fp64 && b->precision == RKS_MIXED && c->opt.fix_theta > 0) {
+    if (acc_fp64 && b->precision == RKS_MIXED && d.fixlist) {
         StageScope sc(c, "jk_fp64_fix", 0);
-        launch_jk_correct(d, nchunk_jk, c->opt.fix_theta, b->max_nbf, s);
+        launch_jk_fix(d, s);
     }
     if (d.xc) {
         // Tensor-core accumulation truncates (round toward zero): fine for the

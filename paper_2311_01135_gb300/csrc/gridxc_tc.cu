@@ -109,9 +109,16 @@ __device__ __forceinline__ uint32_t coff(int row, int k, uint32_t sg) {
 
 struct TcSmem {
     // byte offsets inside the dynamic shared buffer
-    uint32_t D_hi, D_lo, R_g, R_gp, work, pts, coef, part, shf, shi;
+    uint32_t D_hi, D_lo, R_g, R_gp, work, set1, pts, coef, part, shx, shf, shi;
     uint32_t total;
 };
+
+// GEMM2 operand slices (32 points): K-direction core stride padded to 144 B
+// so that 32 threads storing one AO row at 32 consecutive points hit 32
+// distinct banks; row-group stride 8 cores x 144 B.
+#define TC_SLICE 32
+#define TC_LBO2 144u
+#define TC_SBO2 (8u * TC_LBO2)
 
 __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
     TcSmem s;
@@ -123,14 +130,18 @@ __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
     s.R_gp = o; o += (uint32_t)nsh * TC_BP * 4;
     o = (o + 1023) & ~1023u;
     s.work = o;
-    // GEMM1: Phi hi, lo (128 x np); GEMM2: Phi^T hi, lo and X hi, lo (np x 64 each)
-    // plus room for GEMM2's 128-row A reads past the last buffer.
-    uint32_t w1 = 2u * TC_BP * np * 4;
-    uint32_t w2 = 4u * np * 64 * 4 + (uint32_t)(128 - np) * 64 * 4;
+    // GEMM1: Phi hi, lo (128 points x np AOs, K-major, 128-byte core stride).
+    // GEMM2: two sets of {Phi^T hi, Phi^T lo, X hi, X lo}, each np/8 row groups of
+    // 32-point slices, plus room for the 128-row A reads past the last A buffer.
+    const uint32_t w1 = 2u * TC_BP * np * 4;
+    const uint32_t opsz = (uint32_t)(np / 8) * TC_SBO2;
+    const uint32_t w2 = 8u * opsz + (uint32_t)((128 - np) / 8) * TC_SBO2;
+    s.set1 = 4u * opsz;
     o += (w1 > w2 ? w1 : w2);
     s.pts = o; o += 4 * TC_BP * 4;
     s.coef = o; o += 4 * TC_BP * 4;
     s.part = o; o += 2 * 4 * TC_BP * 4;
+    s.shx = o; o += (uint32_t)nsh * 8 * 4;  // per shell: 3 exponents, 3 coefficients, l, ao0
     s.shf = o; o += (uint32_t)nsh * 8 * 4;  // per shell: R_owner0 - C (3), R_owner1 - C (3), pad
     s.shi = o; o += (uint32_t)np * 2 * 4;   // per AO: shell, component
     s.total = o;
@@ -140,7 +151,7 @@ __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
 template <typename TA>
 __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar1, bar2;
+    __shared__ __align__(8) uint64_t bar1, bar2[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail;
     __shared__ int owner_h[TC_BP];
@@ -149,17 +160,18 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
     if (mode == 0 && !b.st[m].active) return;
     const int n = md.nbf, nsh = md.nsh;
     const int np = (n + 15) & ~15;
+    const int nh = np / 2;  // AO columns per half (multiple of 8)
     const TcSmem L = tc_layout(np, nsh);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     unsigned char *sm = smem;
     float *Rg = (float *)(sm + L.R_g), *Rgp = (float *)(sm + L.R_gp);
     float *pt = (float *)(sm + L.pts), *cf = (float *)(sm + L.coef), *part = (float *)(sm + L.part);
-    float *shf = (float *)(sm + L.shf);
+    float *shx = (float *)(sm + L.shx), *shf = (float *)(sm + L.shf);
+    int *shxi = (int *)shx;
     int *shi = (int *)(sm + L.shi);
     const uint32_t sg1 = (uint32_t)(np / 4) * 128u;  // row-group stride, K = np (GEMM1 A and B)
-    const uint32_t sg2 = 16u * 128u;                  // row-group stride, K = 64 points (GEMM2)
 
-    // ---- per-block constants: D (hi, lo) as GEMM1's B (rows nu, K = mu), shells, AO map
+    // ---- per-CTA constants: D (hi, lo) as GEMM1's B (rows nu, K = mu), shells, AO map
     const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
     for (int i = t; i < np * np / 4; i += blockDim.x) {
         const int row = i / (np / 4), kc = i % (np / 4);
@@ -177,6 +189,12 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
     for (int s = t; s < nsh; s += blockDim.x) {
         const int g = md.sh0 + s;
         const int l = b.sh_l[g], a0 = b.sh_ao0[g];
+        for (int k = 0; k < 3; k++) {
+            shx[s * 8 + k] = (float)b.sh_ex[g * 3 + k];
+            shx[s * 8 + 3 + k] = (float)b.sh_co[g * 3 + k];
+        }
+        shxi[s * 8 + 6] = l;
+        shxi[s * 8 + 7] = a0;
         for (int c = 0; c < (l ? 3 : 1); c++) {
             shi[(a0 + c) * 2] = s;
             shi[(a0 + c) * 2 + 1] = l ? c : -1;  // -1: s function
@@ -194,7 +212,8 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
     }
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar1)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar2)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar2[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar2[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
@@ -205,48 +224,50 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
     const uint32_t tT = tmem, tV = tmem + TC_NPMAX;  // column bases of T (GEMM1) and V (GEMM2)
     const uint32_t id1 = tc::idesc(128, np), id2 = tc::idesc(128, np);
     const uint32_t su = tc::smem_u32(sm);
-    uint32_t ph1 = 0, ph2 = 0, v_started = 0;
+    uint32_t ph1 = 0, ph2[2] = {0, 0};
     double exc = 0.0;
+    // V' rows (TMEM lanes) and columns of this thread: row q*32 + lane, columns [h*nh, h*nh + nh)
+    const int q = warp & 3, h = warp >> 2;
+    float vacc[TC_NPMAX / 2];
+#pragma unroll
+    for (int j = 0; j < TC_NPMAX / 2; j++) vacc[j] = 0.f;
+    bool any_block = false;
 
     const float *gxp = (const float *)b.gx + md.pts0, *gyp = (const float *)b.gy + md.pts0;
     const float *gzp = (const float *)b.gz + md.pts0, *gwp = (const float *)b.gw + md.pts0;
     bool failed = false;
     const int npa = b.n_rad * b.n_theta * b.n_phi;
     for (int blk = chunk; blk < md.nblk && !failed; blk += nchunk) {
+        any_block = true;
         const long long p0 = (long long)blk * TC_BP;
         const int own0 = min((int)(p0 / npa), md.natom - 1);
         if (t < TC_BP) {
-            // point offsets from their own nucleus; the owner is folded into the
-            // offset (owner 0 or 1 of this block) by adding R_owner1 - R_owner0
-            const int h = min((int)((p0 + t) / npa), md.natom - 1) - own0;
-            float ox = gxp[p0 + t], oy = gyp[p0 + t], oz = gzp[p0 + t];
-            pt[t] = ox;
-            pt[TC_BP + t] = oy;
-            pt[2 * TC_BP + t] = oz;
+            owner_h[t] = min((int)((p0 + t) / npa), md.natom - 1) - own0;
+            pt[t] = gxp[p0 + t];
+            pt[TC_BP + t] = gyp[p0 + t];
+            pt[2 * TC_BP + t] = gzp[p0 + t];
             pt[3 * TC_BP + t] = gwp[p0 + t];
-            owner_h[t] = h;
         }
         for (int i = t; i < 2 * nsh; i += blockDim.x) {
-            const int h = i / nsh, s = i % nsh;
-            const int A = min(own0 + h, md.natom - 1);
+            const int hh = i / nsh, s = i % nsh;
+            const int A = min(own0 + hh, md.natom - 1);
             const double *ra = b.axyz + (md.atom0 + A) * 3, *rc = b.sh_xyz + (md.sh0 + s) * 3;
-            shf[s * 8 + h * 3 + 0] = (float)(ra[0] - rc[0]);
-            shf[s * 8 + h * 3 + 1] = (float)(ra[1] - rc[1]);
-            shf[s * 8 + h * 3 + 2] = (float)(ra[2] - rc[2]);
+            shf[s * 8 + hh * 3 + 0] = (float)(ra[0] - rc[0]);
+            shf[s * 8 + hh * 3 + 1] = (float)(ra[1] - rc[1]);
+            shf[s * 8 + hh * 3 + 2] = (float)(ra[2] - rc[2]);
         }
         __syncthreads();
-        // ---- A: radial parts
+        // ---- A: radial parts per (shell, point)
         for (int i = t; i < nsh * TC_BP; i += blockDim.x) {
             const int s = i / TC_BP, p = i % TC_BP;
-            const int g = md.sh0 + s;
             const float *dl = shf + s * 8 + owner_h[p] * 3;
             const float dx = dl[0] + pt[p], dy = dl[1] + pt[TC_BP + p], dz = dl[2] + pt[2 * TC_BP + p];
             const float r2 = dx * dx + dy * dy + dz * dz;
             float gg = 0.f, gp = 0.f;
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const float a = (float)b.sh_ex[g * 3 + k];
-                const float e = (float)b.sh_co[g * 3 + k] * __expf(-a * r2);
+                const float a = shx[s * 8 + k];
+                const float e = shx[s * 8 + 3 + k] * __expf(-a * r2);
                 gg += e;
                 gp -= 2.f * a * e;
             }
@@ -254,15 +275,13 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
             Rgp[s * TC_BP + p] = gp;
         }
         __syncthreads();
-        // ---- B: Phi (points x AOs) for GEMM1, hi and lo
+        // ---- B: Phi (points x AOs) for GEMM1; thread = (point, AO half)
+        const int p = t & (TC_BP - 1);
+        const float px = pt[p], py = pt[TC_BP + p], pz = pt[2 * TC_BP + p];
+        const int hp = owner_h[p];
         {
             const uint32_t phi_hi = L.work, phi_lo = L.work + (uint32_t)TC_BP * np * 4;
-            const int nitem = TC_BP * (np / 4);
-            for (int i = t; i < nitem; i += blockDim.x) {
-                // lanes: 8 consecutive points x 4 consecutive AO chunks (conflict-free 16-byte stores)
-                const int l = i & 31, wi = i >> 5;
-                const int pg = wi % (TC_BP / 8), cg = wi / (TC_BP / 8);
-                const int p = pg * 8 + (l & 7), kc = cg * 4 + (l >> 3);
+            for (int kc = h * (nh / 4); kc < (h + 1) * (nh / 4); kc++) {
                 float v[4];
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
@@ -271,7 +290,7 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
                     float val = 0.f;
                     if (s >= 0) {
                         const float gg = Rg[s * TC_BP + p];
-                        val = (c < 0) ? gg : (shf[s * 8 + owner_h[p] * 3 + c] + pt[c * TC_BP + p]) * gg;
+                        val = (c < 0) ? gg : (shf[s * 8 + hp * 3 + c] + pt[c * TC_BP + p]) * gg;
                     }
                     v[j] = val;
                 }
@@ -295,8 +314,7 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
                 tc::commit(&bar1);
             }
         }
-        // ---- D: density from the T rows
-        // every thread waits (bounded); the block agrees on the outcome
+        // ---- D: density from the T rows (thread = point, AO half)
         const bool ok1 = __syncthreads_and(tc::wait(&bar1, ph1));
         ph1 ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -305,13 +323,8 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
             break;
         }
         {
-            const int q = warp & 3, h = warp >> 2;
-            const int p = q * 32 + lane;
-            const float px = pt[p], py = pt[TC_BP + p], pz = pt[2 * TC_BP + p];
-            const int hp = owner_h[p];
             float rho = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-            const int c0 = h * (np / 2), c1 = c0 + np / 2;
-            for (int cc = c0; cc < c1; cc += 8) {
+            for (int cc = h * nh; cc < (h + 1) * nh; cc += 8) {
                 float tv[8];
                 tc::ld8(tT + ((uint32_t)(q * 32) << 16) + cc, tv);
 #pragma unroll
@@ -360,93 +373,111 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
             }
             __syncthreads();
         }
-        // ---- F: GEMM2 operands per half block, then GEMM2
-        for (int hf = 0; hf < 2; hf++) {
-            const uint32_t at_hi = L.work, at_lo = at_hi + (uint32_t)np * 64 * 4;
-            const uint32_t x_hi = at_lo + (uint32_t)np * 64 * 4, x_lo = x_hi + (uint32_t)np * 64 * 4;
-            const int nitem = np * 16;  // rows (AOs) x 16 chunks of 4 points
-            for (int i = t; i < nitem; i += blockDim.x) {
-                // lanes: 8 consecutive rows x 4 consecutive point chunks
-                const int l = i & 31, wi = i >> 5;
-                const int rg = wi % (np / 8), pc4 = wi / (np / 8);
-                const int row = rg * 8 + (l & 7), pc = pc4 * 4 + (l >> 3);
-                const int s = shi[row * 2], c = shi[row * 2 + 1];
-                float fv[4], xv[4];
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int p = hf * 64 + pc * 4 + j;
-                    float f = 0.f, x = 0.f;
-                    if (s >= 0) {
-                        const float gg = Rg[s * TC_BP + p], gp = Rgp[s * TC_BP + p];
-                        const float *dl = shf + s * 8 + owner_h[p] * 3;
-                        const float dx = dl[0] + pt[p], dy = dl[1] + pt[TC_BP + p], dz = dl[2] + pt[2 * TC_BP + p];
-                        const float a = cf[p], bx = cf[TC_BP + p], by = cf[2 * TC_BP + p], bz = cf[3 * TC_BP + p];
-                        const float bd = bx * dx + by * dy + bz * dz;
-                        if (c < 0) {
-                            f = gg;
-                            x = a * gg + gp * bd;
-                        } else {
-                            const float dc = c == 0 ? dx : (c == 1 ? dy : dz);
-                            const float bc = c == 0 ? bx : (c == 1 ? by : bz);
-                            f = dc * gg;
-                            x = a * f + gp * dc * bd + bc * gg;
-                        }
-                    }
-                    fv[j] = f;
-                    xv[j] = x;
+        // ---- F: GEMM2 in 32-point slices, ping-pong operand sets; the MMAs of
+        // slice k run while slice k + 1 is built.  Thread = (point in slice, shell group).
+        for (int k = 0; k < TC_BP / TC_SLICE; k++) {
+            const int set = k & 1;
+            if (k >= 2) {
+                const bool ok = __syncthreads_and(tc::wait(&bar2[set], ph2[set]));
+                ph2[set] ^= 1;
+                if (!ok) {
+                    failed = true;
+                    break;
                 }
-                float4 hi, lo;
-                tc::split4(fv, hi, lo);
-                *(float4 *)(sm + at_hi + tc::coff(row, pc * 4, sg2)) = hi;
-                *(float4 *)(sm + at_lo + tc::coff(row, pc * 4, sg2)) = lo;
-                tc::split4(xv, hi, lo);
-                *(float4 *)(sm + x_hi + tc::coff(row, pc * 4, sg2)) = hi;
-                *(float4 *)(sm + x_lo + tc::coff(row, pc * 4, sg2)) = lo;
+            }
+            const uint32_t base = L.work + (set ? L.set1 : 0u);
+            const uint32_t opsz = (uint32_t)(np / 8) * TC_SBO2;
+            const uint32_t at_hi = base, at_lo = base + opsz, x_hi = base + 2 * opsz, x_lo = base + 3 * opsz;
+            const int pl = lane, pp = k * TC_SLICE + pl;
+            const float *dlb = shf + owner_h[pp] * 3;
+            const float ox = pt[pp], oy = pt[TC_BP + pp], oz = pt[2 * TC_BP + pp];
+            const float a = cf[pp], bx = cf[TC_BP + pp], by = cf[2 * TC_BP + pp], bz = cf[3 * TC_BP + pp];
+            const uint32_t pofs = (uint32_t)(pl >> 2) * TC_LBO2 + (uint32_t)(pl & 3) * 4u;
+            for (int s = warp; s < nsh; s += 8) {
+                const float gg = Rg[s * TC_BP + pp], gp = Rgp[s * TC_BP + pp];
+                const float *dl = dlb + s * 8;
+                const float dx = dl[0] + ox, dy = dl[1] + oy, dz = dl[2] + oz;
+                const float bd = bx * dx + by * dy + bz * dz;
+                const float basev = a * gg + gp * bd;
+                const int l = shxi[s * 8 + 6], a0 = shxi[s * 8 + 7];
+                const int ncomp = l ? 3 : 1;
+                for (int c = 0; c < ncomp; c++) {
+                    float f, x;
+                    if (!l) {
+                        f = gg;
+                        x = basev;
+                    } else {
+                        const float dc = c == 0 ? dx : (c == 1 ? dy : dz);
+                        const float bc = c == 0 ? bx : (c == 1 ? by : bz);
+                        f = dc * gg;
+                        x = dc * basev + bc * gg;
+                    }
+                    const int mu = a0 + c;
+                    const uint32_t off = (uint32_t)(mu >> 3) * TC_SBO2 + (uint32_t)(mu & 7) * 16u + pofs;
+                    const float fh = tc::tf32_hi(f), xh = tc::tf32_hi(x);
+                    *(float *)(sm + at_hi + off) = fh;
+                    *(float *)(sm + at_lo + off) = f - fh;
+                    *(float *)(sm + x_hi + off) = xh;
+                    *(float *)(sm + x_lo + off) = x - xh;
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (t == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                for (int s = 0; s < 8; s++) {
-                    const uint32_t ka = 2u * s * 128u;
-                    const uint64_t ah = tc::sdesc(su + at_hi + ka, 128, sg2), al = tc::sdesc(su + at_lo + ka, 128, sg2);
-                    const uint64_t bh = tc::sdesc(su + x_hi + ka, 128, sg2), bl = tc::sdesc(su + x_lo + ka, 128, sg2);
-                    tc::mma(tV, ah, bh, id2, v_started);
-                    v_started = 1;
+                for (int s = 0; s < TC_SLICE / 8; s++) {
+                    const uint32_t ka = 2u * s * TC_LBO2;
+                    const uint64_t ah = tc::sdesc(su + at_hi + ka, TC_LBO2, TC_SBO2);
+                    const uint64_t al = tc::sdesc(su + at_lo + ka, TC_LBO2, TC_SBO2);
+                    const uint64_t bh = tc::sdesc(su + x_hi + ka, TC_LBO2, TC_SBO2);
+                    const uint64_t bl = tc::sdesc(su + x_lo + ka, TC_LBO2, TC_SBO2);
+                    tc::mma(tV, ah, bh, id2, (k > 0 || s > 0) ? 1u : 0u);
                     tc::mma(tV, ah, bl, id2, 1);
                     tc::mma(tV, al, bh, id2, 1);
                 }
-                tc::commit(&bar2);
+                tc::commit(&bar2[set]);
             }
-            const bool ok2 = __syncthreads_and(tc::wait(&bar2, ph2));
-            ph2 ^= 1;
+        }
+        if (failed) break;
+        // drain the last two slices, then fold this block's V' into registers
+        // (round-to-nearest sums across blocks; the tensor-core accumulation
+        // only spans one block)
+        {
+            const bool okA = tc::wait(&bar2[0], ph2[0]);
+            const bool okB = tc::wait(&bar2[1], ph2[1]);
+            const bool ok = __syncthreads_and(okA && okB);
+            ph2[0] ^= 1;
+            ph2[1] ^= 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (!ok2) {
+            if (!ok) {
                 failed = true;
                 break;
             }
+#pragma unroll
+            for (int cc = 0; cc < TC_NPMAX / 2; cc += 8) {
+                if (cc < nh) {
+                    float v[8];
+                    tc::ld8(tV + ((uint32_t)(q * 32) << 16) + h * nh + cc, v);
+#pragma unroll
+                    for (int j = 0; j < 8; j++) vacc[cc + j] += v[j];
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
         __syncthreads();
     }
     if (failed && t == 0) s_fail = 1;
     __syncthreads();
-    // ---- flush V' (rows mu = TMEM lanes, columns nu) and E_xc
-    const bool started = __syncthreads_or(v_started);
-    if (!s_fail && started) {
-        const int q = warp & 3, h = warp >> 2;
+    // ---- flush V' (row mu = this thread's lane row, columns of its half) and E_xc
+    if (!s_fail && any_block) {
         const int mu = q * 32 + lane;
         TA *gV;
         if constexpr (sizeof(TA) == 8) gV = (TA *)(b.accd + md.acc0) + 2 * n * n;
         else gV = (TA *)(b.accf + md.acc0) + 2 * n * n;
-        const int c0 = h * (np / 2), c1 = c0 + np / 2;
-        for (int cc = c0; cc < c1; cc += 8) {
-            float v[8];
-            tc::ld8(tV + ((uint32_t)(q * 32) << 16) + cc, v);
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const int nu = cc + j;
-                if (mu < n && nu < n && v[j] != 0.f) atomicAdd(&gV[mu * n + nu], (TA)v[j]);
-            }
+        for (int j = 0; j < TC_NPMAX / 2; j++) {
+            const int nu = h * nh + j;
+            if (j < nh && mu < n && nu < n && vacc[j] != 0.f) atomicAdd(&gV[mu * n + nu], (TA)vacc[j]);
         }
     }
     for (int o = 16; o > 0; o >>= 1) exc += __shfl_xor_sync(0xffffffffu, exc, o);
@@ -455,7 +486,8 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
         atomicOr(&b.st[m].err_flag, 4);
         // give in-flight MMAs a bounded chance to drain before freeing tensor memory
         tc::wait(&bar1, ph1);
-        tc::wait(&bar2, ph2);
+        tc::wait(&bar2[0], ph2[0]);
+        tc::wait(&bar2[1], ph2[1]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

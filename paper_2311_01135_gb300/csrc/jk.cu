@@ -339,3 +339,162 @@ void launch_jk_correct(const DevBatch &b, int nchunk, double theta, int max_nbf,
     cudaFuncSetAttribute(jk_correct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     jk_correct_kernel<<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, theta);
 }
+
+// ------------------------------------------- dense FP64 recompute lists
+__device__ __forceinline__ int class_index(int cls) {
+    // (lP lQ lR lS) bit code -> 0..5 in packing order
+    return cls == 0x0 ? 0 : cls == 0x8 ? 1 : cls == 0xA ? 2 : cls == 0xC ? 3 : cls == 0xE ? 4 : 5;
+}
+
+// One block per molecule: every kept quartet with Q_pq Q_rs >= fix_theta is
+// appended to its class list (row, column, store offset).
+__global__ void __launch_bounds__(256) fix_list_kernel(DevBatch b) {
+    const int m = blockIdx.x;
+    const MolDesc md = b.mol[m];
+    __shared__ int cnt[6];
+    if (threadIdx.x < 6) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int npair = b.npair[m];
+    double qmax = 0.0;
+    for (int i = lane; i < npair; i += 32) qmax = fmax(qmax, b.kq[md.pair0 + i]);
+    for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+    int4 *list = b.fixlist + (long long)m * 6 * RKS_FIX_CAP;
+    for (int r = warp; r < npair; r += nwarp) {
+        const double qpq = b.kq[md.pair0 + r];
+        if (qpq * qmax < b.fix_theta) continue;
+        const int2 pq = b.kpair[md.pair0 + r];
+        const int lP = b.sh_l[md.sh0 + pq.x], lQ = b.sh_l[md.sh0 + pq.y];
+        const int npq = (lP ? 3 : 1) * (lQ ? 3 : 1);
+        long long base = b.row_off[md.pair0 + m + r];
+        for (int s0 = 0; s0 <= r; s0 += 32) {
+            const int s = s0 + lane;
+            bool keep = false, fix = false;
+            int nel = 0, ci = 0;
+            if (s <= r) {
+                const double prod = qpq * b.kq[md.pair0 + s];
+                if (prod >= 1e-12) {
+                    const int2 rs = b.kpair[md.pair0 + s];
+                    const int lR = b.sh_l[md.sh0 + rs.x], lS = b.sh_l[md.sh0 + rs.y];
+                    keep = true;
+                    fix = prod >= b.fix_theta;
+                    nel = npq * (lR ? 3 : 1) * (lS ? 3 : 1);
+                    ci = class_index((lP << 3) | (lQ << 2) | (lR << 1) | lS);
+                }
+            }
+            int x = nel;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const int tot = __shfl_sync(0xffffffffu, x, 31);
+            if (keep && fix) {
+                const int pos = atomicAdd(&cnt[ci], 1);
+                if (pos < RKS_FIX_CAP) {
+                    const long long off = base + x - nel;
+                    list[ci * RKS_FIX_CAP + pos] = make_int4(r, s, (int)(off & 0xffffffff), (int)(off >> 32));
+                }
+            }
+            base += tot;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        b.fixcount[m * 6 + threadIdx.x] = cnt[threadIdx.x];
+        if (cnt[threadIdx.x] > RKS_FIX_CAP) atomicOr(&b.st[m].err_flag, 8);
+    }
+}
+
+void launch_fix_list(const DevBatch &b, cudaStream_t s) { fix_list_kernel<<<b.nmol, 256, 0, s>>>(b); }
+
+// Thread per listed quartet of class (LA LB LC LD): FP64 block from the FP64
+// pair data minus the FP32 store block, contracted with the FP64 density and
+// added to the FP64 J'/K' accumulators.
+template <int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(128) jk_fix_kernel(DevBatch b, int ci) {
+    const int m = blockIdx.y;
+    const int cntm = min(b.fixcount[m * 6 + ci], RKS_FIX_CAP);
+    const MolDesc md = b.mol[m];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cntm; k += gridDim.x * blockDim.x) {
+    const int4 e = b.fixlist[((long long)m * 6 + ci) * RKS_FIX_CAP + k];
+    const int r = e.x, s = e.y;
+    const long long off = (long long)(unsigned)e.z | ((long long)e.w << 32);
+    const int2 pq = b.kpair[md.pair0 + r], rs = b.kpair[md.pair0 + s];
+    const int P = md.sh0 + pq.x, Q = md.sh0 + pq.y, R = md.sh0 + rs.x, S = md.sh0 + rs.y;
+    double AB[3], CD[3], AC[3];
+#pragma unroll
+    for (int x = 0; x < 3; x++) {
+        AB[x] = b.sh_xyz[P * 3 + x] - b.sh_xyz[Q * 3 + x];
+        CD[x] = b.sh_xyz[R * 3 + x] - b.sh_xyz[S * 3 + x];
+        AC[x] = b.sh_xyz[P * 3 + x] - b.sh_xyz[R * 3 + x];
+    }
+    const eri::PrimPair<double> *pp = (const eri::PrimPair<double> *)b.pairprim64;
+    constexpr int na = LA ? 3 : 1, nb = LB ? 3 : 1, nc = LC ? 3 : 1, nd = LD ? 3 : 1;
+    constexpr int N = na * nb * nc * nd;
+    double v[N];
+    eri::quartet_pd<double, LA, LB, LC, LD>(pp + (long long)(md.pair0 + r) * 9, pp + (long long)(md.pair0 + s) * 9,
+                                            AB, CD, AC, b.boys64, v);
+    const float *v32 = (const float *)b.store + md.eri0 + off;
+    double scale = 1.0;
+    if (P == Q) scale *= 0.5;
+    if (R == S) scale *= 0.5;
+    if (r == s) scale *= 0.5;
+#pragma unroll
+    for (int x = 0; x < N; x++) v[x] = scale * (v[x] - (double)v32[x]);
+    const int n = md.nbf;
+    const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
+    double *gJ = b.accd + md.acc0, *gK = gJ + (long long)n * n;
+    const int a0 = b.sh_ao0[P], b0 = b.sh_ao0[Q], c0 = b.sh_ao0[R], d0 = b.sh_ao0[S];
+    double jpq[na][nb] = {}, jrs[nc][nd] = {}, kpr[na][nc] = {}, kqr[nb][nc] = {}, kps[na][nd] = {}, kqs[nb][nd] = {};
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int j = 0; j < nb; j++)
+#pragma unroll
+            for (int kk = 0; kk < nc; kk++)
+#pragma unroll
+                for (int l = 0; l < nd; l++) {
+                    const double x = v[((i * nb + j) * nc + kk) * nd + l];
+                    jpq[i][j] += x * D[(c0 + kk) * n + d0 + l];
+                    jrs[kk][l] += x * D[(a0 + i) * n + b0 + j];
+                    kpr[i][kk] += x * D[(b0 + j) * n + d0 + l];
+                    kqr[j][kk] += x * D[(a0 + i) * n + d0 + l];
+                    kps[i][l] += x * D[(b0 + j) * n + c0 + kk];
+                    kqs[j][l] += x * D[(a0 + i) * n + c0 + kk];
+                }
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int j = 0; j < nb; j++) atomicAdd(&gJ[(a0 + i) * n + b0 + j], 2.0 * jpq[i][j]);
+#pragma unroll
+    for (int kk = 0; kk < nc; kk++)
+#pragma unroll
+        for (int l = 0; l < nd; l++) atomicAdd(&gJ[(c0 + kk) * n + d0 + l], 2.0 * jrs[kk][l]);
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int kk = 0; kk < nc; kk++) atomicAdd(&gK[(a0 + i) * n + c0 + kk], kpr[i][kk]);
+#pragma unroll
+    for (int j = 0; j < nb; j++)
+#pragma unroll
+        for (int kk = 0; kk < nc; kk++) atomicAdd(&gK[(b0 + j) * n + c0 + kk], kqr[j][kk]);
+#pragma unroll
+    for (int i = 0; i < na; i++)
+#pragma unroll
+        for (int l = 0; l < nd; l++) atomicAdd(&gK[(a0 + i) * n + d0 + l], kps[i][l]);
+#pragma unroll
+    for (int j = 0; j < nb; j++)
+#pragma unroll
+        for (int l = 0; l < nd; l++) atomicAdd(&gK[(b0 + j) * n + d0 + l], kqs[j][l]);
+    }
+}
+
+void launch_jk_fix(const DevBatch &b, cudaStream_t s) {
+    const dim3 g(8, b.nmol);  // grid-stride over each molecule's list
+    jk_fix_kernel<0, 0, 0, 0><<<g, 128, 0, s>>>(b, 0);
+    jk_fix_kernel<1, 0, 0, 0><<<g, 128, 0, s>>>(b, 1);
+    jk_fix_kernel<1, 0, 1, 0><<<g, 128, 0, s>>>(b, 2);
+    jk_fix_kernel<1, 1, 0, 0><<<g, 128, 0, s>>>(b, 3);
+    jk_fix_kernel<1, 1, 1, 0><<<g, 128, 0, s>>>(b, 4);
+    jk_fix_kernel<1, 1, 1, 1><<<g, 128, 0, s>>>(b, 5);
+}

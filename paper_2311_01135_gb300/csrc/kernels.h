@@ -21,6 +21,10 @@ void launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nb
 // Final-step correction of the FP32 store: quartets with Q_pq Q_rs >= theta
 // recomputed in FP64, (I64 - I32) contracted with D into the FP64 accumulators.
 void launch_jk_correct(const DevBatch &b, int nchunk, double theta, int max_nbf, cudaStream_t s);
+// Dense version: per-molecule class lists of the quartets above fix_theta
+// (built once at setup), one thread per listed quartet in the final step.
+void launch_fix_list(const DevBatch &b, cudaStream_t s);
+void launch_jk_fix(const DevBatch &b, cudaStream_t s);
 // AO + density + B3LYP + V_xc on the grid; acc_fp64 and mode as above.
 void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
                     cudaStream_t s);

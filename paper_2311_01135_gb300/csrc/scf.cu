@@ -43,11 +43,21 @@ static const size_t SCF_SMEM = sizeof(double) * (2 * RKS_NBF_CAP * RKS_NBF_CAP +
                                sizeof(int) * (3 * RKS_NBF_CAP + 8);
 
 // Diagonalise X^T F X (F global, n x n): eigenvalues -> w (shared), C = X C' -> Cout (global).
-__device__ int diag_fock(const double *F, const double *X, double *tmp, double *Cout, ScfSmem &sm, int n) {
+// Warm start: with the previous eigenvectors Cp (global, orthogonal), Jacobi
+// runs on Cp^T (X^T F X) Cp, which is nearly diagonal after the first SCF
+// iterations, and C' = Cp V; the new C' is written back to Cp.
+__device__ int diag_fock(const double *F, const double *X, double *tmp, double *Cout, ScfSmem &sm, int n,
+                         double *Cp = nullptr, bool warm = false) {
     la::gemm(tmp, F, X, n, false, false);
     __syncthreads();
     la::gemm(sm.A, X, tmp, n, true, false);
     __syncthreads();
+    if (warm) {
+        la::gemm(tmp, sm.A, Cp, n, false, false);
+        __syncthreads();
+        la::gemm(sm.A, Cp, tmp, n, true, false);
+        __syncthreads();
+    }
     // exact symmetry before Jacobi
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         int i = idx / n, j = idx % n;
@@ -59,6 +69,18 @@ __device__ int diag_fock(const double *F, const double *X, double *tmp, double *
     }
     __syncthreads();
     int sw = la::jacobi(sm.A, sm.V, sm.w, n, sm.red, sm.perm, sm.cs);
+    if (warm) {
+        la::gemm(tmp, Cp, sm.V, n, false, false);  // C' = Cp V
+        __syncthreads();
+        for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+            Cp[i] = tmp[i];
+            sm.V[i] = tmp[i];
+        }
+        __syncthreads();
+    } else if (Cp) {
+        for (int i = threadIdx.x; i < n * n; i += blockDim.x) Cp[i] = sm.V[i];
+        __syncthreads();
+    }
     la::gemm(Cout, X, sm.V, n, false, false);
     __syncthreads();
     return sw;
@@ -98,7 +120,7 @@ __global__ void scf_init_kernel(DevBatch b) {
         st.Enuc = e;
         st.E = 0.0; st.E_prev = 0.0; st.Exc = 0.0; st.max_err = 0.0;
         st.diis_n = 0; st.diis_head = 0; st.iter = 0; st.active = 1; st.converged = 0;
-        st.status = RKS_STATUS_OK_; st.eigh_fail = 0;
+        st.status = RKS_STATUS_OK_; st.eigh_fail = 0; st.cp_valid = 0;
     }
 }
 
@@ -132,7 +154,7 @@ __global__ void scf_guess_kernel(DevBatch b) {
     int sw2 = 0;
     if (b.guess == 1) {
         // core Hamiltonian: diagonalise X^T H X, occupy the lowest n_occ
-        sw2 = diag_fock(H, X, tmp, C, sm, n);
+        sw2 = diag_fock(H, X, tmp, C, sm, n, b.mat + md.mat0 + (long long)M_CP * nn, false);
         density_from_C(C, D, n, md.nocc);
     } else {
         // superposed neutral atoms: per heavy atom D_ss = 2 S_ss^-1 over (1s, 2s)
@@ -165,6 +187,7 @@ __global__ void scf_guess_kernel(DevBatch b) {
         if (smin < 1e-8) st.status = RKS_STATUS_S_ILL_;
         if (sw < 0 || sw2 < 0) st.eigh_fail++;
         for (int i = 0; i < n; i++) st.eps[i] = sm.w[i];
+        st.cp_valid = (b.guess == 1);
     }
 }
 
@@ -358,10 +381,12 @@ __global__ void scf_step_kernel(DevBatch b, const TA *accbase) {
         Fuse = FX;
     }
     // ---- diagonalise, new density
-    int sw = diag_fock(Fuse, X, t1, C, sm, n);
+    double *Cp = b.mat + md.mat0 + (long long)M_CP * nn;
+    int sw = diag_fock(Fuse, X, t1, C, sm, n, Cp, st.cp_valid != 0);
     density_from_C(C, D, n, md.nocc);
     if (threadIdx.x == 0) {
         if (sw < 0) st.eigh_fail++;
+        st.cp_valid = 1;
         st.E_prev = E;
         st.iter += 1;
         for (int i = 0; i < n; i++) st.eps[i] = sm.w[i];
@@ -403,7 +428,8 @@ __global__ void scf_final_kernel(DevBatch b, const TA *accbase) {
     double *t3 = b.mat + md.mat0 + (long long)M_TMP3 * nn;
     const double E = assemble_fock<TA>(b, m, md, accbase + md.acc0, sm.red);
     __syncthreads();
-    int sw = diag_fock(F, X, t1, C, sm, n);
+    double *Cp = b.mat + md.mat0 + (long long)M_CP * nn;
+    int sw = diag_fock(F, X, t1, C, sm, n, Cp, st.cp_valid != 0);
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) t3[idx] = D[idx];
     __syncthreads();
     density_from_C(C, D, n, md.nocc);

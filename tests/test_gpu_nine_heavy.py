@@ -80,7 +80,8 @@ def test_c1_setup_and_fock_mixed(c1):
         print(f"mixed@D0: store {store_err:.2e} dEJ {dEJ:.2e} dEK {dEK:.2e} dExc {sc[1] - parts0['Exc']:.2e} "
               f"dE {sc[0] - E0:.2e} |dJ| {np.max(np.abs(J - parts0['J'])):.1e} |dVxc| {np.max(np.abs(V - parts0['Vxc'])):.1e}")
         assert store_err < 1e-5  # relative to the Schwarz bound; dominated by tiny integrals
-        assert np.max(np.abs(grid[:, 3] - s.w)) < 1e-6 * np.max(s.w)
+        # FP32 Becke products of ~natom factors: ~1e-6 of the largest weight
+        assert np.max(np.abs(grid[:, 3] - s.w)) < 5e-6 * np.max(s.w)
         assert np.max(np.abs(J - parts0["J"])) < 2e-5
         assert np.max(np.abs(K - parts0["K"])) < 2e-5
         assert np.max(np.abs(V - parts0["Vxc"])) < 2e-5
