@@ -140,7 +140,7 @@ __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
     o += (w1 > w2 ? w1 : w2);
     s.pts = o; o += 4 * TC_BP * 4;
     s.coef = o; o += 4 * TC_BP * 4;
-    s.part = o; o += 2 * 4 * TC_BP * 4;
+    s.part = o; o += 4 * 4 * TC_BP * 4;
     s.shx = o; o += (uint32_t)nsh * 8 * 4;  // per shell: 3 exponents, 3 coefficients, l, ao0
     s.shf = o; o += (uint32_t)nsh * 8 * 4;  // per shell: R_owner0 - C (3), R_owner1 - C (3), pad
     s.shi = o; o += (uint32_t)np * 2 * 4;   // per AO: shell, component
@@ -148,19 +148,33 @@ __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
     return s;
 }
 
+#define TC_THREADS 512
+#define TC_SCREEN 1e-9f  // per-block AO screening threshold on |phi| and |grad phi| (iterations only)
+
+__device__ __forceinline__ void ld4(uint32_t taddr, float *v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 4; j++) v[j] = __uint_as_float(r[j]);
+}
+
 template <typename TA>
-__global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode) {
+__global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar1, bar2[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail;
     __shared__ int owner_h[TC_BP];
+    __shared__ int sig[TC_NSHMAX];  // shell significant somewhere in this block
     const int m = blockIdx.y, chunk = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
     const int n = md.nbf, nsh = md.nsh;
     const int np = (n + 15) & ~15;
-    const int nh = np / 2;  // AO columns per half (multiple of 8)
+    const int nq = np / 4;  // AO columns per thread group (multiple of 4)
     const TcSmem L = tc_layout(np, nsh);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     unsigned char *sm = smem;
@@ -226,11 +240,11 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
     const uint32_t su = tc::smem_u32(sm);
     uint32_t ph1 = 0, ph2[2] = {0, 0};
     double exc = 0.0;
-    // V' rows (TMEM lanes) and columns of this thread: row q*32 + lane, columns [h*nh, h*nh + nh)
-    const int q = warp & 3, h = warp >> 2;
-    float vacc[TC_NPMAX / 2];
+    // thread group g4 (0..3) and TMEM lane quarter q: V' row q*32 + lane, columns [g4*nq, g4*nq + nq)
+    const int q = warp & 3, g4 = warp >> 2;
+    float vacc[TC_NPMAX / 4];
 #pragma unroll
-    for (int j = 0; j < TC_NPMAX / 2; j++) vacc[j] = 0.f;
+    for (int j = 0; j < TC_NPMAX / 4; j++) vacc[j] = 0.f;
     bool any_block = false;
 
     const float *gxp = (const float *)b.gx + md.pts0, *gyp = (const float *)b.gy + md.pts0;
@@ -239,10 +253,10 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
     const int npa = b.n_rad * b.n_theta * b.n_phi;
     for (int blk = chunk; blk < md.nblk && !failed; blk += nchunk) {
         any_block = true;
-        const long long p0 = (long long)blk * TC_BP;
-        const int own0 = min((int)(p0 / npa), md.natom - 1);
+        const int p0 = blk * TC_BP;
+        const int own0 = min(p0 / npa, md.natom - 1);
         if (t < TC_BP) {
-            owner_h[t] = min((int)((p0 + t) / npa), md.natom - 1) - own0;
+            owner_h[t] = min((p0 + t) / npa, md.natom - 1) - own0;
             pt[t] = gxp[p0 + t];
             pt[TC_BP + t] = gyp[p0 + t];
             pt[2 * TC_BP + t] = gzp[p0 + t];
@@ -256,10 +270,11 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
             shf[s * 8 + hh * 3 + 1] = (float)(ra[1] - rc[1]);
             shf[s * 8 + hh * 3 + 2] = (float)(ra[2] - rc[2]);
         }
+        for (int s = t; s < nsh; s += blockDim.x) sig[s] = 0;
         __syncthreads();
-        // ---- A: radial parts per (shell, point)
+        // ---- A: radial parts per (shell, point) and per-block shell significance
         for (int i = t; i < nsh * TC_BP; i += blockDim.x) {
-            const int s = i / TC_BP, p = i % TC_BP;
+            const int s = i >> 7, p = i & (TC_BP - 1);
             const float *dl = shf + s * 8 + owner_h[p] * 3;
             const float dx = dl[0] + pt[p], dy = dl[1] + pt[TC_BP + p], dz = dl[2] + pt[2 * TC_BP + p];
             const float r2 = dx * dx + dy * dy + dz * dz;
@@ -273,22 +288,26 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
             }
             Rg[s * TC_BP + p] = gg;
             Rgp[s * TC_BP + p] = gp;
+            // |phi| and |grad phi| bounds for s and p functions
+            const float r = sqrtf(r2);
+            const float bound = fabsf(gg) * fmaxf(1.f, r) + fabsf(gp) * fmaxf(r, r2);
+            if (bound > TC_SCREEN && !sig[s]) sig[s] = 1;  // benign race: every writer stores 1
         }
         __syncthreads();
-        // ---- B: Phi (points x AOs) for GEMM1; thread = (point, AO half)
+        // ---- B: Phi (points x AOs) for GEMM1; thread = (point, AO quarter)
         const int p = t & (TC_BP - 1);
         const float px = pt[p], py = pt[TC_BP + p], pz = pt[2 * TC_BP + p];
         const int hp = owner_h[p];
         {
             const uint32_t phi_hi = L.work, phi_lo = L.work + (uint32_t)TC_BP * np * 4;
-            for (int kc = h * (nh / 4); kc < (h + 1) * (nh / 4); kc++) {
+            for (int kc = g4 * (nq / 4); kc < (g4 + 1) * (nq / 4); kc++) {
                 float v[4];
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const int mu = kc * 4 + j;
                     const int s = shi[mu * 2], c = shi[mu * 2 + 1];
                     float val = 0.f;
-                    if (s >= 0) {
+                    if (s >= 0 && sig[s]) {
                         const float gg = Rg[s * TC_BP + p];
                         val = (c < 0) ? gg : (shf[s * 8 + hp * 3 + c] + pt[c * TC_BP + p]) * gg;
                     }
@@ -314,7 +333,7 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
                 tc::commit(&bar1);
             }
         }
-        // ---- D: density from the T rows (thread = point, AO half)
+        // ---- D: density from the T rows (thread = point, AO quarter)
         const bool ok1 = __syncthreads_and(tc::wait(&bar1, ph1));
         ph1 ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -324,14 +343,14 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
         }
         {
             float rho = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-            for (int cc = h * nh; cc < (h + 1) * nh; cc += 8) {
-                float tv[8];
-                tc::ld8(tT + ((uint32_t)(q * 32) << 16) + cc, tv);
+            for (int cc = g4 * nq; cc < (g4 + 1) * nq; cc += 4) {
+                float tv[4];
+                ld4(tT + ((uint32_t)(q * 32) << 16) + cc, tv);
 #pragma unroll
-                for (int j = 0; j < 8; j++) {
+                for (int j = 0; j < 4; j++) {
                     const int nu = cc + j;
                     const int s = shi[nu * 2], c = shi[nu * 2 + 1];
-                    if (s < 0) continue;
+                    if (s < 0 || !sig[s]) continue;
                     const float gg = Rg[s * TC_BP + p], gp = Rgp[s * TC_BP + p];
                     const float *dl = shf + s * 8 + hp * 3;
                     const float dx = dl[0] + px, dy = dl[1] + py, dz = dl[2] + pz;
@@ -351,17 +370,22 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
                     rz += tv[j] * fz;
                 }
             }
-            part[(h * 4 + 0) * TC_BP + p] = rho;
-            part[(h * 4 + 1) * TC_BP + p] = rx;
-            part[(h * 4 + 2) * TC_BP + p] = ry;
-            part[(h * 4 + 3) * TC_BP + p] = rz;
+            part[(g4 * 4 + 0) * TC_BP + p] = rho;
+            part[(g4 * 4 + 1) * TC_BP + p] = rx;
+            part[(g4 * 4 + 2) * TC_BP + p] = ry;
+            part[(g4 * 4 + 3) * TC_BP + p] = rz;
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
             if (t < TC_BP) {
-                const float r = part[t] + part[4 * TC_BP + t];
-                const float gx = 2.f * (part[TC_BP + t] + part[5 * TC_BP + t]);
-                const float gy = 2.f * (part[2 * TC_BP + t] + part[6 * TC_BP + t]);
-                const float gz = 2.f * (part[3 * TC_BP + t] + part[7 * TC_BP + t]);
+                float r = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+                for (int gq = 0; gq < 4; gq++) {
+                    r += part[(gq * 4 + 0) * TC_BP + t];
+                    gx += part[(gq * 4 + 1) * TC_BP + t];
+                    gy += part[(gq * 4 + 2) * TC_BP + t];
+                    gz += part[(gq * 4 + 3) * TC_BP + t];
+                }
+                gx *= 2.f; gy *= 2.f; gz *= 2.f;
                 const float w = pt[3 * TC_BP + t];
                 float e = 0.f, vr = 0.f, vs = 0.f;
                 if (w != 0.f) xc::b3lyp<float>(r, gx * gx + gy * gy + gz * gz, e, vr, vs);
@@ -374,7 +398,7 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
             __syncthreads();
         }
         // ---- F: GEMM2 in 32-point slices, ping-pong operand sets; the MMAs of
-        // slice k run while slice k + 1 is built.  Thread = (point in slice, shell group).
+        // slice k run while slice k + 1 is built.  Thread = (point in slice, shell group of 16).
         for (int k = 0; k < TC_BP / TC_SLICE; k++) {
             const int set = k & 1;
             if (k >= 2) {
@@ -393,14 +417,25 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
             const float ox = pt[pp], oy = pt[TC_BP + pp], oz = pt[2 * TC_BP + pp];
             const float a = cf[pp], bx = cf[TC_BP + pp], by = cf[2 * TC_BP + pp], bz = cf[3 * TC_BP + pp];
             const uint32_t pofs = (uint32_t)(pl >> 2) * TC_LBO2 + (uint32_t)(pl & 3) * 4u;
-            for (int s = warp; s < nsh; s += 8) {
+            for (int s = warp; s < nsh; s += TC_THREADS / 32) {
+                const int l = shxi[s * 8 + 6], a0 = shxi[s * 8 + 7];
+                const int ncomp = l ? 3 : 1;
+                if (!sig[s]) {
+                    for (int c = 0; c < ncomp; c++) {
+                        const int mu = a0 + c;
+                        const uint32_t off = (uint32_t)(mu >> 3) * TC_SBO2 + (uint32_t)(mu & 7) * 16u + pofs;
+                        *(float *)(sm + at_hi + off) = 0.f;
+                        *(float *)(sm + at_lo + off) = 0.f;
+                        *(float *)(sm + x_hi + off) = 0.f;
+                        *(float *)(sm + x_lo + off) = 0.f;
+                    }
+                    continue;
+                }
                 const float gg = Rg[s * TC_BP + pp], gp = Rgp[s * TC_BP + pp];
                 const float *dl = dlb + s * 8;
                 const float dx = dl[0] + ox, dy = dl[1] + oy, dz = dl[2] + oz;
                 const float bd = bx * dx + by * dy + bz * dz;
                 const float basev = a * gg + gp * bd;
-                const int l = shxi[s * 8 + 6], a0 = shxi[s * 8 + 7];
-                const int ncomp = l ? 3 : 1;
                 for (int c = 0; c < ncomp; c++) {
                     float f, x;
                     if (!l) {
@@ -454,12 +489,12 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
                 break;
             }
 #pragma unroll
-            for (int cc = 0; cc < TC_NPMAX / 2; cc += 8) {
-                if (cc < nh) {
-                    float v[8];
-                    tc::ld8(tV + ((uint32_t)(q * 32) << 16) + h * nh + cc, v);
+            for (int cc = 0; cc < TC_NPMAX / 4; cc += 4) {
+                if (cc < nq) {
+                    float v[4];
+                    ld4(tV + ((uint32_t)(q * 32) << 16) + g4 * nq + cc, v);
 #pragma unroll
-                    for (int j = 0; j < 8; j++) vacc[cc + j] += v[j];
+                    for (int j = 0; j < 4; j++) vacc[cc + j] += v[j];
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -468,16 +503,16 @@ __global__ void __launch_bounds__(256, 1) grid_xc_tc_kernel(DevBatch b, int nchu
     }
     if (failed && t == 0) s_fail = 1;
     __syncthreads();
-    // ---- flush V' (row mu = this thread's lane row, columns of its half) and E_xc
+    // ---- flush V' (row mu = this thread's lane row, columns of its quarter) and E_xc
     if (!s_fail && any_block) {
         const int mu = q * 32 + lane;
         TA *gV;
         if constexpr (sizeof(TA) == 8) gV = (TA *)(b.accd + md.acc0) + 2 * n * n;
         else gV = (TA *)(b.accf + md.acc0) + 2 * n * n;
 #pragma unroll
-        for (int j = 0; j < TC_NPMAX / 2; j++) {
-            const int nu = h * nh + j;
-            if (j < nh && mu < n && nu < n && vacc[j] != 0.f) atomicAdd(&gV[mu * n + nu], (TA)vacc[j]);
+        for (int j = 0; j < TC_NPMAX / 4; j++) {
+            const int nu = g4 * nq + j;
+            if (j < nq && mu < n && nu < n && vacc[j] != 0.f) atomicAdd(&gV[mu * n + nu], (TA)vacc[j]);
         }
     }
     for (int o = 16; o > 0; o >>= 1) exc += __shfl_xor_sync(0xffffffffu, exc, o);
@@ -505,9 +540,9 @@ void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, in
     const size_t sm = tc_layout(np, max_nsh).total + 1024;
     if (acc_fp64) {
         cudaFuncSetAttribute(grid_xc_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        grid_xc_tc_kernel<double><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode);
+        grid_xc_tc_kernel<double><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);
     } else {
         cudaFuncSetAttribute(grid_xc_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        grid_xc_tc_kernel<float><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode);
+        grid_xc_tc_kernel<float><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);
     }
 }
