@@ -89,8 +89,9 @@ typedef struct rks_options {
     int32_t diis_space;     /* DIIS history length (1..8), default 8 */
     int32_t coords_in_angstrom;
     int32_t xc;             /* 1 = B3LYP (default); 0 = Hartree-Fock test mode (a0 = 1, no V_xc) */
-    int32_t max_slots;      /* most molecules resident on the device at once, default 4096 */
-    uint64_t hbm_budget_bytes; /* admission cap for resident molecules; 0 = 85% of free memory */
+    int32_t max_slots;      /* serving: most molecules in one cohort, default 4096 */
+    uint64_t hbm_budget_bytes; /* serving: cap on the device memory of all cohorts in flight;
+                                  0 = 85% of the memory free when the context is created */
     int32_t device;         /* CUDA device ordinal, default 0 */
     int32_t use_graphs;     /* capture fixed-iteration loops in CUDA graphs, default 1 */
     int32_t pad0;
@@ -101,6 +102,11 @@ typedef struct rks_options {
                                when every molecule has nbf <= 80 and <= 60 shells (default);
                                0 = the CUDA-core grid kernel */
     int32_t guess;          /* initial density: RKS_GUESS_SAD (default) or RKS_GUESS_CORE */
+    int32_t max_cohorts;    /* serving: most batches ("cohorts") in flight at once, each on its own
+                               stream, default 4 */
+    int32_t admit_wait_us;  /* serving: while other cohorts run, a partial cohort (fewer than
+                               max_slots molecules) is admitted once its oldest request has waited
+                               this long (microseconds), default 20000 */
 } rks_options;
 
 typedef struct rks_result_t {
@@ -135,19 +141,33 @@ const char *rks_last_error(rks_ctx *ctx);
  * tables (Boys function table), starts the serving worker thread.
  * Errors: RKS_EINVAL (bad options), RKS_ECUDA, RKS_ENOMEM. */
 int rks_create(const rks_options *options, rks_ctx **out);
-/* Stops the worker (pending tickets are failed), frees device memory. */
+/* Stops the worker (queued and in-flight tickets are failed), frees device memory. */
 int rks_destroy(rks_ctx *ctx);
 /* The context's compute stream (a cudaStream_t), for timing with events. */
 void *rks_stream(rks_ctx *ctx);
 
 /* ------------------------------------------------------- serving API */
 /* Queue one molecule.  Non-blocking: copies Z[natom] and xyz[natom*3]
- * (row-major) and returns a ticket.  The worker admits queued molecules into
- * device slots as memory frees up (continuous batching: molecules admitted
- * while others are mid-SCF join the next iteration tick).
+ * (row-major) and returns a ticket.  Continuous batching: the worker thread
+ * keeps up to max_cohorts batches in flight, each on its own CUDA stream, and
+ * admits queued molecules as a new cohort whenever the HBM budget has room
+ * (a full cohort at once, a partial one when the GPU is idle or the oldest
+ * request has waited admit_wait_us).  It advances every cohort a few SCF
+ * iterations at a time without blocking (CUDA events and an asynchronous
+ * read of the count of molecules still iterating); converged molecules drop
+ * out of the work at once, and a cohort retires, publishing its tickets and
+ * returning its memory for back-fill, after its final step.  A molecule's
+ * result does not depend on which cohort it ran in.
  * Errors: RKS_EINVAL (validation as above), RKS_EAGAIN (queue full). */
 int rks_submit(rks_ctx *ctx, int32_t natom, const int32_t *Z, const double *xyz,
                uint64_t *ticket_out);
+/* Queue nmol molecules at once (Z and xyz concatenated, natom[m] atoms each),
+ * all-or-nothing: every molecule is validated before any is queued, and they
+ * reach the worker together (one admission decision).  tickets_out[nmol].
+ * Errors: RKS_EINVAL (first invalid molecule named by rks_last_error),
+ * RKS_EAGAIN. */
+int rks_submit_batch(rks_ctx *ctx, int32_t nmol, const int32_t *natom, const int32_t *Z,
+                     const double *xyz, uint64_t *tickets_out);
 /* Non-blocking state query: RKS_PENDING / RKS_RUNNING / RKS_DONE / RKS_FAILED. */
 int rks_poll(rks_ctx *ctx, uint64_t ticket, int32_t *state_out);
 /* Block the calling host thread until the ticket is done or timeout_s passes. */
@@ -155,7 +175,9 @@ int rks_wait(rks_ctx *ctx, uint64_t ticket, double timeout_s);
 /* Copy the result of a finished ticket and release it.  eps_out (nbf values,
  * ascending) and D_out (nbf*nbf, the output total density) may be NULL;
  * cap_nbf is their capacity in basis functions (RKS_EINVAL if smaller than
- * nbf).  Errors: RKS_ENOTREADY, RKS_ENOTFOUND. */
+ * nbf).  Errors: RKS_ENOTREADY, RKS_ENOTFOUND; for a failed ticket (released
+ * by this call) RKS_ENOMEM when the molecule alone exceeds the HBM budget,
+ * RKS_ECUDA otherwise. */
 int rks_result(rks_ctx *ctx, uint64_t ticket, rks_result_t *out, double *eps_out,
                double *D_out, int32_t cap_nbf);
 
@@ -169,7 +191,8 @@ int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom, const int
                      const double *xyz, rks_batch **out);
 /* Enqueue the whole method (integrals, grid, SCF iterations, final step) on
  * the context stream and return without waiting (for the converge protocol the
- * call waits for convergence checks every few iterations). */
+ * call reads the count of molecules still iterating every 4 iterations and
+ * stops when it reaches zero). */
 int rks_batch_run(rks_batch *b);
 /* Wait for the batch's work to finish; RKS_EDEVICE if a kernel reported a
  * bounded-wait or bounds failure. */

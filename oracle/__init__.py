@@ -13,7 +13,7 @@ Modules:
            atom-centred grids with Becke partitioning
   xc     - B3LYP(VWN5) energy density; potentials by complex-step
            differentiation of the energy density
-  scf    - AO evaluation, J/K, V_xc and the SCF driver (core guess, DIIS)
+  scf    - AO evaluation, J/K, V_xc and the SCF driver (SAD or core guess, DIIS)
 
 Parity status per function is listed in the module headers; every function
 here has at least one pin in tests/test_oracle_*.py except the whole-method

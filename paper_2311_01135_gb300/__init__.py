@@ -34,7 +34,8 @@ class rks_options(ctypes.Structure):
                 ("coords_in_angstrom", ctypes.c_int32), ("xc", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("pad0", ctypes.c_int32), ("fix_theta", ctypes.c_double),
-                ("grid_tc", ctypes.c_int32), ("guess", ctypes.c_int32)]
+                ("grid_tc", ctypes.c_int32), ("guess", ctypes.c_int32),
+                ("max_cohorts", ctypes.c_int32), ("admit_wait_us", ctypes.c_int32)]
 
 
 class rks_result_t(ctypes.Structure):
@@ -61,6 +62,7 @@ _SIGS = {
     "rks_destroy": (ctypes.c_int, [_P]),
     "rks_stream": (_P, [_P]),
     "rks_submit": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "rks_submit_batch": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
     "rks_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]),
     "rks_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double]),
     "rks_result": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(rks_result_t), _P, _P, ctypes.c_int32]),
@@ -161,6 +163,17 @@ class Context:
         t = ctypes.c_uint64()
         _chk(lib().rks_submit(self.h, len(Z), _ptr(Z), _ptr(xyz), ctypes.byref(t)), "rks_submit")
         return t.value
+
+    def submit_many(self, mols):
+        """Queue [(Z, xyz), ...] in one call (rks_submit_batch); returns the tickets."""
+        na = np.array([len(Z) for Z, _ in mols], np.int32)
+        Z = np.ascontiguousarray(np.concatenate([np.asarray(z, np.int32) for z, _ in mols]), np.int32)
+        xyz = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1, 3)
+                                                   for _, x in mols]), np.float64)
+        t = np.zeros(len(mols), np.uint64)
+        _chk(lib().rks_submit_batch(self.h, len(mols), _ptr(na), _ptr(Z), _ptr(xyz), _ptr(t)),
+             "rks_submit_batch")
+        return [int(x) for x in t]
 
     def poll(self, ticket):
         s = ctypes.c_int32()

@@ -150,6 +150,8 @@ extern "C" int rks_options_default(rks_options *o) {
     o->fix_theta = 0.1;
     o->grid_tc = 1;
     o->guess = RKS_GUESS_SAD;
+    o->max_cohorts = 4;
+    o->admit_wait_us = 20000;
     return RKS_OK;
 }
 
@@ -164,6 +166,7 @@ struct StageRec {
 struct rks_batch;
 struct Ticket {
     int state = RKS_PENDING;
+    int err = RKS_ECUDA;  // error rks_result reports for a failed ticket
     std::vector<int> Z;
     std::vector<double> xyz;
     rks_result_t res{};
@@ -180,6 +183,7 @@ struct rks_ctx {
     std::string err;
     // profiling
     bool prof = false;
+    std::mutex prof_mu;
     std::vector<StageRec> recs;
     std::map<std::string, rks_stage_time> totals;
     // serving
@@ -191,7 +195,12 @@ struct rks_ctx {
     bool stop = false;
     std::thread worker;
     size_t queue_cap = 1 << 20;
+    size_t budget = 0;          // device bytes all cohorts in flight may hold
+    // pinned host words for asynchronous readbacks, one per live batch
+    int *pin = nullptr;
+    std::vector<int> pin_free;
 };
+static const int kPinSlots = 256;
 
 extern "C" const char *rks_last_error(rks_ctx *ctx) {
     (void)ctx;
@@ -202,20 +211,23 @@ extern "C" void *rks_stream(rks_ctx *ctx) { return ctx ? (void *)ctx->stream : n
 
 struct StageScope {
     rks_ctx *c;
+    cudaStream_t st;
     StageRec r;
     bool on;
-    StageScope(rks_ctx *ctx, const char *name, double units) : c(ctx), on(ctx->prof) {
+    StageScope(rks_ctx *ctx, cudaStream_t stream, const char *name, double units)
+        : c(ctx), st(stream), on(ctx->prof) {
         if (on) {
             r.name = name;
             r.units = units;
             cudaEventCreate(&r.a);
             cudaEventCreate(&r.b);
-            cudaEventRecord(r.a, c->stream);
+            cudaEventRecord(r.a, st);
         }
     }
     ~StageScope() {
         if (on) {
-            cudaEventRecord(r.b, c->stream);
+            cudaEventRecord(r.b, st);
+            std::lock_guard<std::mutex> lk(c->prof_mu);
             c->recs.push_back(r);
         }
     }
@@ -229,7 +241,8 @@ extern "C" int rks_profile_enable(rks_ctx *ctx, int32_t on) {
 
 extern "C" int rks_profile_read(rks_ctx *ctx, rks_stage_time *out, int32_t cap) {
     if (!ctx) return RKS_EINVAL;
-    CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    CUDA_OK(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(ctx->prof_mu);
     for (auto &r : ctx->recs) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.a, r.b);
@@ -260,6 +273,9 @@ struct HostMol {
 
 struct rks_batch {
     rks_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;  // the context stream, or a private one (serving cohorts)
+    bool own_stream = false;
+    size_t bytes = 0;               // device memory held
     int nmol = 0;
     int precision = 0;
     int max_nbf = 0, max_nsh = 0, max_atoms = 0;
@@ -273,15 +289,21 @@ struct rks_batch {
     double wall_s = 0.0;
     std::vector<MolState> st_host;
     bool st_valid = false;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;   // one SCF iteration, captured on first use
+    bool graph_failed = false;
+    int pin_slot = -1;                 // ctx->pin word receiving the active count
+    int *active_d = nullptr;
+    int it_enq = 0;                    // SCF iterations enqueued so far
 };
 
 template <typename T> static int dalloc(rks_batch *b, T **p, size_t n) {
     void *q = nullptr;
     size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&q, bytes);
-    if (e != cudaSuccess) return rks_cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+    // stream-ordered: no device-wide synchronisation when cohorts come and go
+    cudaError_t e = cudaMallocAsync(&q, bytes, b->stream);
+    if (e != cudaSuccess) return rks_cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
     b->allocs.push_back(q);
+    b->bytes += bytes;
     *p = (T *)q;
     return RKS_OK;
 }
@@ -305,19 +327,79 @@ static int validate(int natom, const int *Z, const double *xyz, int *nbf_out) {
 extern "C" int rks_batch_destroy(rks_batch *b) {
     if (!b) return RKS_EINVAL;
     if (b->graph) cudaGraphExecDestroy(b->graph);
-    for (void *p : b->allocs) cudaFree(p);
+    for (void *p : b->allocs) cudaFreeAsync(p, b->stream);
+    cudaStreamSynchronize(b->stream);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    if (b->pin_slot >= 0) {
+        std::lock_guard<std::mutex> lk(b->ctx->mu);
+        b->ctx->pin_free.push_back(b->pin_slot);
+    }
     delete b;
     return RKS_OK;
 }
 
-extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom, const int32_t *Z,
-                                const double *xyz, rks_batch **out) {
-    if (!ctx || nmol <= 0 || !natom || !Z || !xyz || !out) return fail(RKS_EINVAL, "null argument");
+// Unscreened size of the packed store: candidate pairs in (l_P + l_Q, P, Q)
+// order (s shells before p), row r holds n_r * sum_{s <= r} n_s elements.
+static long long store_cap(int ns, int np) {
+    long long cap = 0, pref = 0;
+    const long long cnt[3] = {(long long)ns * (ns + 1) / 2, (long long)ns * np, (long long)np * (np + 1) / 2};
+    const long long nr[3] = {1, 3, 9};
+    for (int cls = 0; cls < 3; cls++)
+        for (long long k = 0; k < cnt[cls]; k++) {
+            pref += nr[cls];
+            cap += nr[cls] * pref;
+        }
+    return cap;
+}
+
+// Device bytes one molecule adds to a batch (the allocations of
+// batch_create_on, per molecule); the serving worker admits by this figure.
+static size_t mol_bytes(const rks_options &o, int na, const int32_t *Z) {
+    int ns = 0, np = 0, nbf = 0;
+    for (int i = 0; i < na; i++) {
+        const ElemDef *E = elem_of(Z[i]);
+        if (!E) return 0;
+        for (int k = 0; k < E->nsh; k++) {
+            if (E->sh[k].l) np++; else ns++;
+            nbf += E->sh[k].l ? 3 : 1;
+        }
+    }
+    const size_t esz = o.precision ? 4 : 8;
+    const long long nsh = ns + np, npair = nsh * (nsh + 1) / 2;
+    const long long npts = (long long)na * o.n_rad * o.n_theta * o.n_phi;
+    const long long nblk = (npts + RKS_PTS_BLOCK - 1) / RKS_PTS_BLOCK;
+    size_t b = sizeof(MolDesc) + sizeof(MolState) + 8 + (size_t)na * 28 + (size_t)nsh * 84;
+    b += (size_t)npair * (8 + 4 + 8 + 8 + 8 + 4 + 8 + 45 * esz);
+    if (o.precision == RKS_MIXED && o.fix_theta > 0) b += (size_t)npair * 45 * 8 + 6 * (RKS_FIX_CAP * 16 + 4);
+    b += (size_t)((store_cap(ns, np) + 3) & ~3LL) * esz;
+    b += (size_t)nblk * RKS_PTS_BLOCK * 4 * esz + (size_t)nblk * 4;
+    b += (size_t)nbf * nbf * (M_COUNT * 8 + 3 * 12);
+    return b;
+}
+
+static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, int32_t nmol, const int32_t *natom,
+                           const int32_t *Z, const double *xyz, rks_batch **out) {
+    if (!ctx || nmol <= 0 || !natom || !Z || !xyz || !out) {
+        if (own_stream) cudaStreamDestroy(stream);
+        return fail(RKS_EINVAL, "null argument");
+    }
     std::call_once(g_basis_once, init_basis);
     const rks_options &o = ctx->opt;
     const double conv = o.coords_in_angstrom ? 1.0 / 0.52917721092 : 1.0;
     rks_batch *b = new rks_batch();
     b->ctx = ctx;
+    b->stream = stream;
+    b->own_stream = own_stream;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (ctx->pin_free.empty()) {
+            delete b;
+            if (own_stream) cudaStreamDestroy(stream);
+            return fail(RKS_ENOMEM, "too many live batches");
+        }
+        b->pin_slot = ctx->pin_free.back();
+        ctx->pin_free.pop_back();
+    }
     b->nmol = nmol;
     b->precision = o.precision;
     b->hm.resize(nmol);
@@ -378,13 +460,9 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
                 for (int Q = 0; Q <= P; Q++)
                     if (sh[P].l + sh[Q].l == cls) pr.push_back(make_int2(P, Q));
         const int npair_all = (int)pr.size();
-        // unscreened store bound: sum over rows r of n_r * sum_{s <= r} n_s
-        long long cap = 0, pref = 0;
-        for (auto &p : pr) {
-            long long nr = (long long)(sh[p.x].l ? 3 : 1) * (sh[p.y].l ? 3 : 1);
-            pref += nr;
-            cap += nr * pref;
-        }
+        int ns = 0;
+        for (auto &x : sh) ns += x.l == 0;
+        const long long cap = store_cap(ns, nsh - ns);
         for (auto &p : pr) {
             hcand.push_back(p);
             hcand_mol.push_back(m);
@@ -448,7 +526,7 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
         (rc = dalloc(b, (unsigned char **)&gx, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gy, pts_off * esz)) ||
         (rc = dalloc(b, (unsigned char **)&gz, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gw, pts_off * esz)) ||
         (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) || (rc = dalloc(b, &accf, acc_off)) ||
-        (rc = dalloc(b, &b->blk_mol, b->nblk_total))) {
+        (rc = dalloc(b, &b->blk_mol, b->nblk_total)) || (rc = dalloc(b, &b->active_d, 1))) {
         rks_batch_destroy(b);
         return rc;
     }
@@ -461,7 +539,7 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
     d.fixcount = fixcount;
     d.fix_theta = o.fix_theta;
     d.gx = gx; d.gy = gy; d.gz = gz; d.gw = gw; d.mat = mat; d.accd = accd; d.accf = accf;
-    cudaStream_t s = ctx->stream;
+    cudaStream_t s = b->stream;
 #define UP(dst_, src_)                                                                                      \
     if (!(src_).empty()) {                                                                                  \
         cudaError_t e_ = cudaMemcpyAsync(dst_, (src_).data(), (src_).size() * sizeof((src_)[0]),          \
@@ -492,6 +570,12 @@ extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom
     return RKS_OK;
 }
 
+extern "C" int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom, const int32_t *Z,
+                                const double *xyz, rks_batch **out) {
+    if (!ctx) return fail(RKS_EINVAL, "null context");
+    return batch_create_on(ctx, ctx->stream, false, nmol, natom, Z, xyz, out);
+}
+
 // -------------------------------------------------------------- stages
 static int check_launch(const char *what) {
     cudaError_t e = cudaGetLastError();
@@ -502,22 +586,23 @@ static int check_launch(const char *what) {
 extern "C" int rks_batch_setup(rks_batch *b) {
     if (!b) return RKS_EINVAL;
     rks_ctx *c = b->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = b->stream;
     const DevBatch &d = b->d;
     const int fp32 = b->precision;
-    { StageScope sc(c, "onee", 0); launch_onee(d, (int)b->ncand, s); }
-    { StageScope sc(c, "schwarz", 0); launch_schwarz(d, (int)b->ncand, s); }
-    { StageScope sc(c, "pairs", 0); launch_compact_pairs(d, s); }
-    { StageScope sc(c, "row_count", 0); launch_row_count(d, (int)b->ncand, s); }
-    { StageScope sc(c, "row_scan", 0); launch_row_scan(d, s); }
-    { StageScope sc(c, "pair_prim", 0); launch_pair_prim(d, (int)b->ncand, fp32, s); }
-    { StageScope sc(c, "eri", 0); launch_eri_store(d, (int)b->ncand, fp32, s); }
-    if (d.fixlist) { StageScope sc(c, "fix_list", 0); launch_fix_list(d, s); }
-    { StageScope sc(c, "grid_build", 0); launch_grid_build(d, b->nblk_total, b->blk_mol, c->rad, c->ang, b->max_atoms, s); }
-    { StageScope sc(c, "scf_init", 0); launch_scf_init(d, s); }
-    { StageScope sc(c, "scf_guess", 0); launch_scf_guess(d, s); }
+    { StageScope sc(c, s, "onee", 0); launch_onee(d, (int)b->ncand, s); }
+    { StageScope sc(c, s, "schwarz", 0); launch_schwarz(d, (int)b->ncand, s); }
+    { StageScope sc(c, s, "pairs", 0); launch_compact_pairs(d, s); }
+    { StageScope sc(c, s, "row_count", 0); launch_row_count(d, (int)b->ncand, s); }
+    { StageScope sc(c, s, "row_scan", 0); launch_row_scan(d, s); }
+    { StageScope sc(c, s, "pair_prim", 0); launch_pair_prim(d, (int)b->ncand, fp32, s); }
+    { StageScope sc(c, s, "eri", 0); launch_eri_store(d, (int)b->ncand, fp32, s); }
+    if (d.fixlist) { StageScope sc(c, s, "fix_list", 0); launch_fix_list(d, s); }
+    { StageScope sc(c, s, "grid_build", 0); launch_grid_build(d, b->nblk_total, b->blk_mol, c->rad, c->ang, b->max_atoms, s); }
+    { StageScope sc(c, s, "scf_init", 0); launch_scf_init(d, s); }
+    { StageScope sc(c, s, "scf_guess", 0); launch_scf_guess(d, s); }
     int rc = check_launch("setup kernels");
     if (rc) return rc;
+    b->it_enq = 0;
     b->set_up = true;
     b->st_valid = false;
     return RKS_OK;
@@ -526,7 +611,7 @@ extern "C" int rks_batch_setup(rks_batch *b) {
 // One Fock build for every (active when mode 0) molecule.
 static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
     rks_ctx *c = b->ctx;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = b->stream;
     const DevBatch &d = b->d;
     long long acc_elems = 0;
     for (auto &m : b->md) acc_elems += 3LL * m.nbf * m.nbf;
@@ -534,9 +619,9 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
     else CUDA_OK(cudaMemsetAsync(d.accf, 0, sizeof(float) * acc_elems, s));
     launch_reset_exc(d, s);
     const int nchunk_jk = 8;
-    { StageScope sc(c, acc_fp64 ? "jk_final" : "jk", 0); launch_jk(d, nchunk_jk, acc_fp64, mode, b->max_nbf, s); }
+    { StageScope sc(c, s, acc_fp64 ? "jk_final" : "jk", 0); launch_jk(d, nchunk_jk, acc_fp64, mode, b->max_nbf, s); }
     if (acc_fp64 && b->precision == RKS_MIXED && d.fixlist) {
-        StageScope sc(c, "jk_fp64_fix", 0);
+        StageScope sc(c, s, "jk_fp64_fix", 0);
         launch_jk_fix(d, s);
     }
     if (d.xc) {
@@ -546,74 +631,110 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
         if (!acc_fp64 && b->precision == RKS_MIXED && c->opt.grid_tc &&
             grid_xc_tc_supported(b->max_nbf, b->max_nsh)) {
             const int nchunk_tc = 4;
-            StageScope sc(c, acc_fp64 ? "grid_xc_tc_final" : "grid_xc_tc", 0);
+            StageScope sc(c, s, acc_fp64 ? "grid_xc_tc_final" : "grid_xc_tc", 0);
             launch_grid_xc_tc(d, nchunk_tc, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
         } else {
             const int nchunk_gx = 16;
-            StageScope sc(c, acc_fp64 ? "grid_xc_final" : "grid_xc", 0);
+            StageScope sc(c, s, acc_fp64 ? "grid_xc_final" : "grid_xc", 0);
             launch_grid_xc(d, nchunk_gx, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
         }
     }
     return check_launch("fock pass");
 }
 
-static int count_active(rks_batch *b, int *n_active) {
-    b->st_host.resize(b->nmol);
-    CUDA_OK(cudaMemcpyAsync(b->st_host.data(), b->d.st, sizeof(MolState) * b->nmol, cudaMemcpyDeviceToHost,
-                            b->ctx->stream));
-    CUDA_OK(cudaStreamSynchronize(b->ctx->stream));
-    int n = 0;
-    for (auto &st : b->st_host) n += st.active;
-    *n_active = n;
+// One SCF iteration for every molecule still iterating: Fock build and the
+// per-molecule step (DIIS, diagonalisation, density, convergence flags).
+static int enqueue_one_iter(rks_batch *b) {
+    const int fp64_iter = b->precision == 0;
+    int rc = fock_pass(b, fp64_iter, 0);
+    if (rc) return rc;
+    StageScope sc(b->ctx, b->stream, "scf_step", 0);
+    launch_scf_step(b->d, fp64_iter, b->stream);
+    return check_launch("scf step");
+}
+
+// Enqueue n iterations.  The iteration is the same launch sequence every time
+// (inactive molecules are skipped by the kernels, not by the host), so after
+// the first one it is captured once as a CUDA graph and replayed; stage
+// profiling needs per-launch events and turns the graph off.
+static int enqueue_iters(rks_batch *b, int n) {
+    rks_ctx *c = b->ctx;
+    cudaStream_t s = b->stream;
+    int rc;
+    for (int k = 0; k < n; k++, b->it_enq++) {
+        const bool use_graph = c->opt.use_graphs && !c->prof && !b->graph_failed && b->it_enq > 0;
+        if (use_graph && !b->graph) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                rc = enqueue_one_iter(b);
+                e = cudaStreamEndCapture(s, &g);
+                if (e == cudaSuccess && rc == RKS_OK) e = cudaGraphInstantiate(&b->graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+            }
+            if (e != cudaSuccess || !b->graph) {
+                // capture is an optimisation: fall back to direct launches
+                cudaGetLastError();
+                b->graph = nullptr;
+                b->graph_failed = true;
+            }
+        }
+        if (b->graph && use_graph) {
+            CUDA_OK(cudaGraphLaunch(b->graph, s));
+        } else if ((rc = enqueue_one_iter(b))) {
+            return rc;
+        }
+    }
     return RKS_OK;
 }
 
+// Count of molecules still iterating, copied to the batch's pinned word.
+static int enqueue_active_count(rks_batch *b) {
+    launch_count_active(b->d, b->active_d, b->stream);
+    CUDA_OK(cudaMemcpyAsync(b->ctx->pin + b->pin_slot, b->active_d, sizeof(int), cudaMemcpyDeviceToHost,
+                            b->stream));
+    return check_launch("count active");
+}
+
+// Final step: every molecule, FP64 accumulation.
+static int enqueue_final(rks_batch *b) {
+    int rc = fock_pass(b, 1, 1);
+    if (rc) return rc;
+    StageScope sc(b->ctx, b->stream, "scf_final", 0);
+    launch_scf_final(b->d, 1, b->stream);
+    b->st_valid = false;
+    return check_launch("final");
+}
+
+static const int kCheckEvery = 4;
+
 extern "C" int rks_batch_run(rks_batch *b) {
     if (!b) return RKS_EINVAL;
-    rks_ctx *c = b->ctx;
     auto t0 = std::chrono::steady_clock::now();
     int rc;
     if (!b->set_up && (rc = rks_batch_setup(b))) return rc;
     const DevBatch &d = b->d;
-    const int fp64_iter = b->precision == 0;
     if (d.fixed_iters > 0) {
-        for (int it = 0; it < d.fixed_iters; it++) {
-            if ((rc = fock_pass(b, fp64_iter, 0))) return rc;
-            StageScope sc(c, "scf_step", 0);
-            launch_scf_step(d, fp64_iter, c->stream);
-        }
+        if ((rc = enqueue_iters(b, d.fixed_iters))) return rc;
     } else {
-        for (int it = 0; it < d.max_iters; it++) {
-            if ((rc = fock_pass(b, fp64_iter, 0))) return rc;
-            {
-                StageScope sc(c, "scf_step", 0);
-                launch_scf_step(d, fp64_iter, c->stream);
-            }
-            if ((rc = check_launch("scf step"))) return rc;
-            if (it % 4 == 3 || it == d.max_iters - 1) {
-                int na = 0;
-                if ((rc = count_active(b, &na))) return rc;
-                if (na == 0) break;
-            }
+        while (b->it_enq < d.max_iters) {
+            if ((rc = enqueue_iters(b, std::min(kCheckEvery, d.max_iters - b->it_enq)))) return rc;
+            if ((rc = enqueue_active_count(b))) return rc;
+            CUDA_OK(cudaStreamSynchronize(b->stream));
+            if (b->ctx->pin[b->pin_slot] == 0) break;
         }
     }
-    // final step: every molecule, FP64 accumulation
-    if ((rc = fock_pass(b, 1, 1))) return rc;
-    {
-        StageScope sc(c, "scf_final", 0);
-        launch_scf_final(d, 1, c->stream);
-    }
-    if ((rc = check_launch("final"))) return rc;
-    b->st_valid = false;
+    if ((rc = enqueue_final(b))) return rc;
     b->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return RKS_OK;
 }
 
 extern "C" int rks_batch_sync(rks_batch *b) {
     if (!b) return RKS_EINVAL;
-    CUDA_OK(cudaStreamSynchronize(b->ctx->stream));
     b->st_host.resize(b->nmol);
-    CUDA_OK(cudaMemcpy(b->st_host.data(), b->d.st, sizeof(MolState) * b->nmol, cudaMemcpyDeviceToHost));
+    CUDA_OK(cudaMemcpyAsync(b->st_host.data(), b->d.st, sizeof(MolState) * b->nmol, cudaMemcpyDeviceToHost,
+                            b->stream));
+    CUDA_OK(cudaStreamSynchronize(b->stream));
     b->st_valid = true;
     for (auto &st : b->st_host)
         if (st.err_flag) return fail(RKS_EDEVICE, "device-side consistency flag set");
@@ -629,12 +750,12 @@ extern "C" int rks_batch_fock(rks_batch *b, const double *D_all, int32_t final_s
         const MolDesc &md = b->md[m];
         long long nn = (long long)md.nbf * md.nbf;
         CUDA_OK(cudaMemcpyAsync(b->d.mat + md.mat0 + (long long)M_D * nn, D_all + off, nn * sizeof(double),
-                                cudaMemcpyHostToDevice, b->ctx->stream));
+                                cudaMemcpyHostToDevice, b->stream));
         off += nn;
     }
     const int acc64 = final_step || b->precision == 0;
     if ((rc = fock_pass(b, acc64, 1))) return rc;
-    launch_fock_only(b->d, acc64, b->ctx->stream);
+    launch_fock_only(b->d, acc64, b->stream);
     b->st_valid = false;
     return check_launch("fock only");
 }
@@ -679,15 +800,16 @@ extern "C" int rks_batch_result(rks_batch *b, int32_t m, rks_result_t *out, doub
     if (eps_out) memcpy(eps_out, st.eps, sizeof(double) * md.nbf);
     if (D_out) {
         long long nn = (long long)md.nbf * md.nbf;
-        CUDA_OK(cudaMemcpy(D_out, b->d.mat + md.mat0 + (long long)M_D * nn, nn * sizeof(double),
-                           cudaMemcpyDeviceToHost));
+        CUDA_OK(cudaMemcpyAsync(D_out, b->d.mat + md.mat0 + (long long)M_D * nn, nn * sizeof(double),
+                                cudaMemcpyDeviceToHost, b->stream));
+        CUDA_OK(cudaStreamSynchronize(b->stream));
     }
     return RKS_OK;
 }
 
 extern "C" int64_t rks_batch_dump(rks_batch *b, int32_t m, int32_t what, void *out, int64_t cap) {
     if (!b || m < 0 || m >= b->nmol || !out) return RKS_EINVAL;
-    CUDA_OK(cudaStreamSynchronize(b->ctx->stream));
+    CUDA_OK(cudaStreamSynchronize(b->stream));
     const MolDesc &md = b->md[m];
     const DevBatch &d = b->d;
     const long long nn = (long long)md.nbf * md.nbf;
@@ -825,54 +947,204 @@ extern "C" int rks_eval_xc(rks_ctx *ctx, int32_t n, const double *rho, const dou
 }
 
 // ----------------------------------------------------- serving worker
-// Admits queued tickets into a batch (up to max_slots), runs it, and
-// publishes the results; molecules arriving meanwhile wait for the next batch.
+// Continuous batching.  The worker keeps up to max_cohorts batches in flight,
+// each on its own stream, so a request that arrives while others are
+// mid-SCF starts at once instead of waiting for the running batch to finish.
+// Each pass of the loop (1) admits queued molecules as a new cohort when the
+// HBM budget has room, (2) advances every cohort whose last enqueued chunk has
+// completed (CUDA event query, no blocking): a few more SCF iterations, or the
+// final step once its pinned active count reads zero (or the protocol's
+// iteration count is reached), and (3) retires cohorts whose final step is
+// done: results go to their tickets and the memory returns to the budget.
+struct Cohort {
+    rks_batch *b = nullptr;
+    std::vector<uint64_t> ids;
+    int phase = 0;  // 0 iterating, 1 final step enqueued
+    bool counted = false;  // the last chunk ended with an active-count readback
+    cudaEvent_t ev = nullptr;
+};
+
+static void fail_tickets(rks_ctx *c, const std::vector<uint64_t> &ids, int err = RKS_ECUDA) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (auto id : ids) {
+        auto it = c->tickets.find(id);
+        if (it != c->tickets.end()) {
+            it->second.state = RKS_FAILED;
+            it->second.err = err;
+        }
+    }
+    c->cv_done.notify_all();
+}
+
+// Enqueue the cohort's next chunk and record its event.
+static int cohort_next(Cohort &h) {
+    rks_batch *b = h.b;
+    const DevBatch &d = b->d;
+    int rc = RKS_OK;
+    if (h.phase == 0) {
+        bool done;
+        if (d.fixed_iters > 0) done = b->it_enq >= d.fixed_iters;
+        else done = b->it_enq >= d.max_iters || (h.counted && b->ctx->pin[b->pin_slot] == 0);
+        if (done) {
+            rc = enqueue_final(b);
+            h.phase = 1;
+        } else {
+            const int lim = d.fixed_iters > 0 ? d.fixed_iters : d.max_iters;
+            rc = enqueue_iters(b, std::min(kCheckEvery, lim - b->it_enq));
+            if (!rc && d.fixed_iters == 0) {
+                rc = enqueue_active_count(b);
+                h.counted = true;
+            }
+        }
+    }
+    if (rc) return rc;
+    CUDA_OK(cudaEventRecord(h.ev, b->stream));
+    return RKS_OK;
+}
+
+static int cohort_start(rks_ctx *c, Cohort &h, const std::vector<int32_t> &na, const std::vector<int32_t> &Z,
+                        const std::vector<double> &xyz) {
+    cudaStream_t st = nullptr;
+    CUDA_OK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    int rc = batch_create_on(c, st, true, (int)na.size(), na.data(), Z.data(), xyz.data(), &h.b);
+    if (rc) return rc;
+    if ((rc = rks_batch_setup(h.b))) return rc;
+    CUDA_OK(cudaEventCreateWithFlags(&h.ev, cudaEventDisableTiming));
+    return cohort_next(h);
+}
+
+static void cohort_free(Cohort &h) {
+    if (h.b) rks_batch_destroy(h.b);
+    if (h.ev) cudaEventDestroy(h.ev);
+    h.b = nullptr;
+    h.ev = nullptr;
+}
+
+// Copy results to the cohort's tickets (its stream is idle).
+static void cohort_publish(rks_ctx *c, Cohort &h) {
+    rks_batch *b = h.b;
+    const int rc = rks_batch_sync(b);
+    if (rc && rc != RKS_EDEVICE) {
+        fail_tickets(c, h.ids);
+        return;
+    }
+    std::vector<rks_result_t> res(h.ids.size());
+    std::vector<std::vector<double>> eps(h.ids.size()), D(h.ids.size());
+    std::vector<int> ok(h.ids.size(), 0);
+    for (size_t k = 0; k < h.ids.size(); k++) {
+        const int nbf = b->md[k].nbf;
+        eps[k].resize(nbf);
+        D[k].resize((size_t)nbf * nbf);
+        ok[k] = rks_batch_result(b, (int)k, &res[k], eps[k].data(), D[k].data(), nbf) == RKS_OK;
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto now = std::chrono::steady_clock::now();
+    for (size_t k = 0; k < h.ids.size(); k++) {
+        auto it = c->tickets.find(h.ids[k]);
+        if (it == c->tickets.end()) continue;
+        Ticket &t = it->second;
+        if (!ok[k]) {
+            t.state = RKS_FAILED;
+            continue;
+        }
+        t.res = res[k];
+        t.res.latency_s = std::chrono::duration<double>(now - t.t_submit).count();
+        t.eps.swap(eps[k]);
+        t.D.swap(D[k]);
+        t.state = RKS_DONE;
+    }
+    c->cv_done.notify_all();
+}
+
 static void worker_main(rks_ctx *c) {
     cudaSetDevice(c->opt.device);
+    std::vector<Cohort> live;
+    const auto admit_wait = std::chrono::microseconds(std::max(0, c->opt.admit_wait_us));
     for (;;) {
-        std::vector<uint64_t> ids;
-        {
-            std::unique_lock<std::mutex> lk(c->mu);
-            c->cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
-            if (c->stop) break;
-            while (!c->queue.empty() && (int)ids.size() < c->opt.max_slots) {
-                ids.push_back(c->queue.front());
-                c->queue.pop_front();
-            }
-            for (auto id : ids) c->tickets[id].state = RKS_RUNNING;
-        }
+        // (1) admission
+        std::vector<uint64_t> ids, rejected;
         std::vector<int32_t> na, Z;
         std::vector<double> xyz;
         {
-            std::lock_guard<std::mutex> lk(c->mu);
-            for (auto id : ids) {
+            std::unique_lock<std::mutex> lk(c->mu);
+            if (live.empty()) c->cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+            if (c->stop) break;
+            size_t inflight = 0;
+            for (auto &h : live) inflight += h.b->bytes;
+            const bool room = (int)live.size() < std::max(1, c->opt.max_cohorts);
+            bool admit = room && !c->queue.empty();
+            if (admit && !live.empty() && (int)c->queue.size() < c->opt.max_slots) {
+                auto waited = std::chrono::steady_clock::now() - c->tickets[c->queue.front()].t_submit;
+                admit = waited >= admit_wait;
+            }
+            size_t need = 0;
+            while (admit && !c->queue.empty() && (int)ids.size() < c->opt.max_slots) {
+                const uint64_t id = c->queue.front();
                 Ticket &t = c->tickets[id];
+                const size_t mb = mol_bytes(c->opt, (int)t.Z.size(), t.Z.data());
+                if (inflight + need + mb > c->budget) {
+                    // larger than the whole budget: it can never run
+                    if (live.empty() && ids.empty()) {
+                        c->queue.pop_front();
+                        rejected.push_back(id);
+                        continue;
+                    }
+                    break;
+                }
+                need += mb;
+                c->queue.pop_front();
+                ids.push_back(id);
+                t.state = RKS_RUNNING;
                 na.push_back((int)t.Z.size());
                 Z.insert(Z.end(), t.Z.begin(), t.Z.end());
                 xyz.insert(xyz.end(), t.xyz.begin(), t.xyz.end());
             }
         }
-        rks_batch *b = nullptr;
-        int rc = rks_batch_create(c, (int)ids.size(), na.data(), Z.data(), xyz.data(), &b);
-        if (!rc) rc = rks_batch_run(b);
-        if (!rc) rc = rks_batch_sync(b);
-        std::lock_guard<std::mutex> lk(c->mu);
-        auto now = std::chrono::steady_clock::now();
-        for (size_t k = 0; k < ids.size(); k++) {
-            Ticket &t = c->tickets[ids[k]];
-            if (rc && rc != RKS_EDEVICE) {
-                t.state = RKS_FAILED;
+        if (!rejected.empty()) fail_tickets(c, rejected, RKS_ENOMEM);
+        bool progressed = !ids.empty();
+        if (!ids.empty()) {
+            Cohort h;
+            h.ids = ids;
+            if (cohort_start(c, h, na, Z, xyz) == RKS_OK) {
+                live.push_back(h);
+            } else {
+                fail_tickets(c, h.ids);
+                cohort_free(h);
+            }
+        }
+        // (2) advance, (3) retire
+        for (size_t k = 0; k < live.size();) {
+            Cohort &h = live[k];
+            const cudaError_t q = cudaEventQuery(h.ev);
+            if (q == cudaErrorNotReady) {
+                k++;
                 continue;
             }
-            int nbf = b->md[k].nbf;
-            t.eps.resize(nbf);
-            t.D.resize((size_t)nbf * nbf);
-            rks_batch_result(b, (int)k, &t.res, t.eps.data(), t.D.data(), nbf);
-            t.res.latency_s = std::chrono::duration<double>(now - t.t_submit).count();
-            t.state = RKS_DONE;
+            progressed = true;
+            int rc = q == cudaSuccess ? RKS_OK : rks_cuda_fail(q, "cohort", __FILE__, __LINE__);
+            if (!rc && h.phase == 0) rc = cohort_next(h);
+            else if (!rc) {
+                cohort_publish(c, h);
+                cohort_free(h);
+                live.erase(live.begin() + k);
+                continue;
+            }
+            if (rc) {
+                fail_tickets(c, h.ids);
+                cohort_free(h);
+                live.erase(live.begin() + k);
+                continue;
+            }
+            k++;
         }
-        if (b) rks_batch_destroy(b);
-        c->cv_done.notify_all();
+        if (!progressed) {
+            std::unique_lock<std::mutex> lk(c->mu);
+            if (!c->stop) c->cv.wait_for(lk, std::chrono::microseconds(200));
+        }
+    }
+    for (auto &h : live) {
+        fail_tickets(c, h.ids);
+        cohort_free(h);
     }
 }
 
@@ -883,7 +1155,8 @@ extern "C" int rks_create(const rks_options *options, rks_ctx **out) {
     if (options) o = *options; else rks_options_default(&o);
     if (o.basis != 0 || o.n_rad <= 0 || o.n_theta <= 0 || o.n_theta > 64 || o.n_phi <= 0 || o.becke_iters < 0 ||
         (o.precision != RKS_FP64 && o.precision != RKS_MIXED) || o.max_iters <= 0 || o.max_slots <= 0 ||
-        !(o.fix_theta >= 0) || (o.guess != RKS_GUESS_SAD && o.guess != RKS_GUESS_CORE))
+        !(o.fix_theta >= 0) || (o.guess != RKS_GUESS_SAD && o.guess != RKS_GUESS_CORE) || o.max_cohorts <= 0 ||
+        o.admit_wait_us < 0)
         return fail(RKS_EINVAL, "bad options");
     int ndev = 0;
     CUDA_OK(cudaGetDeviceCount(&ndev));
@@ -896,6 +1169,7 @@ extern "C" int rks_create(const rks_options *options, rks_ctx **out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->boys32, sizeof(float) * BOYS_N32 * BOYS_COL32);
     if (e == cudaSuccess) e = cudaMalloc(&c->rad, sizeof(double) * 5 * o.n_rad * 2);
     if (e == cudaSuccess) e = cudaMalloc(&c->ang, sizeof(double) * o.n_theta * o.n_phi * 4);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->pin, sizeof(int) * kPinSlots, cudaHostAllocDefault);
     if (e != cudaSuccess) {
         delete c;
         return rks_cuda_fail(e, "context allocation", __FILE__, __LINE__);
@@ -907,6 +1181,14 @@ extern "C" int rks_create(const rks_options *options, rks_ctx **out) {
     if (e != cudaSuccess) {
         delete c;
         return rks_cuda_fail(e, "context tables", __FILE__, __LINE__);
+    }
+    for (int k = kPinSlots - 1; k >= 0; k--) c->pin_free.push_back(k);
+    if (o.hbm_budget_bytes) {
+        c->budget = o.hbm_budget_bytes;
+    } else {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        c->budget = (size_t)(0.85 * (double)fr);
     }
     c->worker = std::thread(worker_main, c);
     *out = c;
@@ -932,6 +1214,7 @@ extern "C" int rks_destroy(rks_ctx *c) {
     cudaFree(c->boys32);
     cudaFree(c->rad);
     cudaFree(c->ang);
+    if (c->pin) cudaFreeHost(c->pin);
     cudaStreamDestroy(c->stream);
     delete c;
     return RKS_OK;
@@ -950,6 +1233,33 @@ extern "C" int rks_submit(rks_ctx *c, int32_t natom, const int32_t *Z, const dou
     t.t_submit = std::chrono::steady_clock::now();
     c->queue.push_back(id);
     *ticket_out = id;
+    c->cv.notify_one();
+    return RKS_OK;
+}
+
+extern "C" int rks_submit_batch(rks_ctx *c, int32_t nmol, const int32_t *natom, const int32_t *Z,
+                                const double *xyz, uint64_t *tickets_out) {
+    if (!c || nmol < 0 || (nmol > 0 && (!natom || !Z || !xyz || !tickets_out))) return RKS_EINVAL;
+    long long off = 0;
+    for (int m = 0; m < nmol; m++) {
+        int rc = validate(natom[m], Z + off, xyz + 3 * off, nullptr);
+        if (rc) return fail(rc, "molecule " + std::to_string(m) + ": " + g_err);
+        off += natom[m];
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->queue.size() + (size_t)nmol > c->queue_cap) return RKS_EAGAIN;
+    const auto now = std::chrono::steady_clock::now();
+    off = 0;
+    for (int m = 0; m < nmol; m++) {
+        const uint64_t id = c->next_ticket++;
+        Ticket &t = c->tickets[id];
+        t.Z.assign(Z + off, Z + off + natom[m]);
+        t.xyz.assign(xyz + 3 * off, xyz + 3 * (off + natom[m]));
+        t.t_submit = now;
+        c->queue.push_back(id);
+        tickets_out[m] = id;
+        off += natom[m];
+    }
     c->cv.notify_one();
     return RKS_OK;
 }
@@ -983,8 +1293,9 @@ extern "C" int rks_result(rks_ctx *c, uint64_t ticket, rks_result_t *out, double
     if (it == c->tickets.end()) return RKS_ENOTFOUND;
     Ticket &t = it->second;
     if (t.state == RKS_FAILED) {
+        const int err = t.err;
         c->tickets.erase(it);
-        return fail(RKS_ECUDA, "ticket failed");
+        return fail(err, err == RKS_ENOMEM ? "molecule exceeds the HBM budget" : "ticket failed");
     }
     if (t.state != RKS_DONE) return RKS_ENOTREADY;
     if ((eps_out || D_out) && cap_nbf < t.res.nbf) return RKS_EINVAL;

@@ -40,4 +40,5 @@ void launch_scf_step(const DevBatch &b, int acc_fp64, cudaStream_t s);
 void launch_scf_final(const DevBatch &b, int acc_fp64, cudaStream_t s);
 void launch_fock_only(const DevBatch &b, int acc_fp64, cudaStream_t s);
 void launch_reset_exc(const DevBatch &b, cudaStream_t s);
+void launch_count_active(const DevBatch &b, int *out, cudaStream_t s);
 void launch_eval_xc(int n, const double *rho, const double *sigma, double *out, int fp32, cudaStream_t s);

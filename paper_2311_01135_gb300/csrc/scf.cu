@@ -480,3 +480,19 @@ __global__ void reset_exc_kernel(DevBatch b) {
 void launch_reset_exc(const DevBatch &b, cudaStream_t s) {
     reset_exc_kernel<<<(b.nmol + 127) / 128, 128, 0, s>>>(b);
 }
+
+// Number of molecules still iterating, for the host's convergence polling
+// (one int instead of the whole state array).
+__global__ void count_active_kernel(DevBatch b, int *out) {
+    __shared__ int tot;
+    if (threadIdx.x == 0) tot = 0;
+    __syncthreads();
+    int n = 0;
+    for (int m = threadIdx.x; m < b.nmol; m += blockDim.x) n += b.st[m].active != 0;
+    if (n) atomicAdd(&tot, n);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = tot;
+}
+void launch_count_active(const DevBatch &b, int *out, cudaStream_t s) {
+    count_active_kernel<<<1, 256, 0, s>>>(b, out);
+}
