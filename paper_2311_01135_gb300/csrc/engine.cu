@@ -913,7 +913,9 @@ extern "C" int rks_eval_boys(rks_ctx *ctx, int32_t mmax, int32_t n, const double
     double *dT, *dO;
     CUDA_OK(cudaMalloc(&dT, n * sizeof(double)));
     CUDA_OK(cudaMalloc(&dO, (size_t)n * (mmax + 1) * sizeof(double)));
-    CUDA_OK(cudaMemcpy(dT, T, n * sizeof(double), cudaMemcpyHostToDevice));
+    // on the context stream: a legacy-stream copy from pageable memory may
+    // return before its DMA lands, and that stream does not order the kernel
+    CUDA_OK(cudaMemcpyAsync(dT, T, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     launch_boys_eval(mmax, n, dT, dO, precision == RKS_MIXED, ctx->boys64, ctx->boys32, ctx->stream);
     CUDA_OK(cudaStreamSynchronize(ctx->stream));
     CUDA_OK(cudaMemcpy(out, dO, (size_t)n * (mmax + 1) * sizeof(double), cudaMemcpyDeviceToHost));
@@ -929,8 +931,8 @@ extern "C" int rks_eval_xc(rks_ctx *ctx, int32_t n, const double *rho, const dou
     CUDA_OK(cudaMalloc(&dr, n * sizeof(double)));
     CUDA_OK(cudaMalloc(&ds, n * sizeof(double)));
     CUDA_OK(cudaMalloc(&dO, 3ull * n * sizeof(double)));
-    CUDA_OK(cudaMemcpy(dr, rho, n * sizeof(double), cudaMemcpyHostToDevice));
-    CUDA_OK(cudaMemcpy(ds, sigma, n * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpyAsync(dr, rho, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_OK(cudaMemcpyAsync(ds, sigma, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     launch_eval_xc(n, dr, ds, dO, precision == RKS_MIXED, ctx->stream);
     CUDA_OK(cudaStreamSynchronize(ctx->stream));
     std::vector<double> o(3ull * n);
