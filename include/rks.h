@@ -256,6 +256,29 @@ int rks_eval_boys(rks_ctx *ctx, int32_t mmax, int32_t n, const double *T, double
 int rks_eval_xc(rks_ctx *ctx, int32_t n, const double *rho, const double *sigma, double *e,
                 double *v_rho, double *v_sigma, int32_t precision);
 
+/* ------------------------------------------- allocation-free XC entry */
+/* The paper has no counterpart: this is a deployment variant of rks_eval_xc.
+ * Same arguments, same kernel, same results (bit-identical), but it allocates
+ * nothing: inputs and outputs are staged through one static device array
+ * of 5 * RKS_XC_NOALLOC_MAX doubles (2.5 MiB) that the library holds per
+ * device, so no cudaMalloc / cudaFree runs.  It is for callers that cannot
+ * allocate device memory (a process whose memory is promised to the serving
+ * budget) or cannot afford cudaFree's wait for the whole device (cohorts in
+ * flight on other streams).
+ *  - n must be 1 .. RKS_XC_NOALLOC_MAX; larger n returns RKS_EINVAL with the
+ *    limit named by rks_last_error (split the call).
+ *  - The first call on a device does the set-up (the address lookup of the
+ *    static array, with that device made current for the call); make it
+ *    before any stream capture on that device.
+ *  - The scratch is shared by every call in the process on that device:
+ *    overlapping calls would race on it, so the library serialises them with
+ *    a lock (a second thread waits for the first call to return).
+ *  - Nothing needs to start at zero; the call is synchronous (returns with
+ *    the outputs in the caller's host arrays). */
+#define RKS_XC_NOALLOC_MAX 65536
+int rks_eval_xc_noalloc(rks_ctx *ctx, int32_t n, const double *rho, const double *sigma, double *e,
+                        double *v_rho, double *v_sigma, int32_t precision);
+
 #ifdef __cplusplus
 }
 #endif

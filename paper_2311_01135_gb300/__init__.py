@@ -20,6 +20,7 @@ RKS_ECUDA, RKS_ETIMEOUT, RKS_ENOTFOUND, RKS_EDEVICE = -5, -6, -7, -8
 RKS_PENDING, RKS_RUNNING, RKS_DONE, RKS_FAILED = 0, 1, 2, 3
 RKS_FP64, RKS_MIXED = 0, 1
 RKS_GUESS_SAD, RKS_GUESS_CORE = 0, 1
+RKS_XC_NOALLOC_MAX = 65536
 RKS_STATUS = {0: "ok", 1: "not_converged", 2: "nonfinite", 3: "s_ill", 4: "eigh"}
 (RKS_DUMP_PAIRS, RKS_DUMP_PAIR_Q, RKS_DUMP_ROW_OFF, RKS_DUMP_STORE, RKS_DUMP_S, RKS_DUMP_T, RKS_DUMP_V,
  RKS_DUMP_GRID, RKS_DUMP_J, RKS_DUMP_K, RKS_DUMP_VXC, RKS_DUMP_D, RKS_DUMP_F, RKS_DUMP_EPS, RKS_DUMP_X,
@@ -79,6 +80,7 @@ _SIGS = {
     "rks_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(rks_stage_time), ctypes.c_int32]),
     "rks_eval_boys": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32]),
     "rks_eval_xc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32]),
+    "rks_eval_xc_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32]),
 }
 
 _lib = None
@@ -213,6 +215,15 @@ class Context:
         e, vr, vs = (np.zeros(len(rho)) for _ in range(3))
         _chk(lib().rks_eval_xc(self.h, len(rho), _ptr(rho), _ptr(sigma), _ptr(e), _ptr(vr), _ptr(vs),
                                precision), "rks_eval_xc")
+        return e, vr, vs
+
+    def eval_xc_noalloc(self, rho, sigma, precision=RKS_FP64):
+        """rks_eval_xc_noalloc: as eval_xc, staged through the library's static scratch."""
+        rho = np.ascontiguousarray(rho, np.float64)
+        sigma = np.ascontiguousarray(sigma, np.float64)
+        e, vr, vs = (np.zeros(len(rho)) for _ in range(3))
+        _chk(lib().rks_eval_xc_noalloc(self.h, len(rho), _ptr(rho), _ptr(sigma), _ptr(e), _ptr(vr), _ptr(vs),
+                                       precision), "rks_eval_xc_noalloc")
         return e, vr, vs
 
 

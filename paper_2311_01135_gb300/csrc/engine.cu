@@ -948,6 +948,61 @@ extern "C" int rks_eval_xc(rks_ctx *ctx, int32_t n, const double *rho, const dou
     return RKS_OK;
 }
 
+// ------------------------------------------- allocation-free XC entry
+// The same B3LYP kernel as rks_eval_xc, staged through one file-scope device
+// array instead of cudaMalloc'd buffers.  For callers that must not allocate:
+// a process whose device memory is already promised to the serving budget
+// (a cudaMalloc could fail or push a cohort out), or one with cohorts in
+// flight, where cudaFree would wait for the whole device.  Layout of the
+// scratch: rho[MAX] | sigma[MAX] | out[3 * MAX] (e, v_rho, v_sigma
+// interleaved per point).  Nothing in it needs to start at zero: every
+// element a call reads was written earlier in that call.
+static __device__ __align__(256) double g_xc_scratch[5 * RKS_XC_NOALLOC_MAX];
+
+static std::mutex g_xc_scratch_mu;           // one scratch per device: calls are serialised
+static double *g_xc_scratch_ptr[64] = {};    // device address per ordinal, looked up on first use
+
+extern "C" int rks_eval_xc_noalloc(rks_ctx *ctx, int32_t n, const double *rho, const double *sigma, double *e,
+                                   double *vr, double *vs, int32_t precision) {
+    if (!ctx || n <= 0 || !rho || !sigma || !e || !vr || !vs) return fail(RKS_EINVAL, "null argument or n <= 0");
+    if (n > RKS_XC_NOALLOC_MAX)
+        return fail(RKS_EINVAL, "n = " + std::to_string(n) + " exceeds the static scratch (RKS_XC_NOALLOC_MAX = " +
+                                    std::to_string(RKS_XC_NOALLOC_MAX) + " points)");
+    if (precision != RKS_FP64 && precision != RKS_MIXED) return fail(RKS_EINVAL, "bad precision");
+    const int dev = ctx->opt.device;
+    if (dev < 0 || dev >= 64) return fail(RKS_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_xc_scratch_mu);
+    int prev = 0;
+    CUDA_OK(cudaGetDevice(&prev));
+    if (prev != dev) CUDA_OK(cudaSetDevice(dev));
+    int rc = RKS_OK;
+    double *base = g_xc_scratch_ptr[dev];
+    cudaError_t err = cudaSuccess;
+    if (!base) {
+        // set-up, once per device, with that device current
+        err = cudaGetSymbolAddress((void **)&base, g_xc_scratch);
+        if (err == cudaSuccess) g_xc_scratch_ptr[dev] = base;
+    }
+    if (err == cudaSuccess) {
+        double *dr = base, *ds = base + RKS_XC_NOALLOC_MAX, *dO = base + 2 * RKS_XC_NOALLOC_MAX;
+        cudaStream_t st = ctx->stream;
+        err = cudaMemcpyAsync(dr, rho, n * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(ds, sigma, n * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) {
+            launch_eval_xc(n, dr, ds, dO, precision == RKS_MIXED, st);
+            err = cudaGetLastError();
+        }
+        double *outs[3] = {e, vr, vs};
+        for (int k = 0; k < 3 && err == cudaSuccess; k++)
+            err = cudaMemcpy2DAsync(outs[k], sizeof(double), dO + k, 3 * sizeof(double), sizeof(double), n,
+                                    cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    }
+    if (err != cudaSuccess) rc = rks_cuda_fail(err, "rks_eval_xc_noalloc", __FILE__, __LINE__);
+    if (prev != dev) cudaSetDevice(prev);
+    return rc;
+}
+
 // ----------------------------------------------------- serving worker
 // Continuous batching.  The worker keeps up to max_cohorts batches in flight,
 // each on its own stream, so a request that arrives while others are
