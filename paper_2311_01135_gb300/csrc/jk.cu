@@ -95,10 +95,23 @@ __device__ __forceinline__ void jk_block(const TS *__restrict__ v, TA scale, int
         for (int l = 0; l < nd; l++) sh_add(&Ks[(b0 + j) * n + d0 + l], kqs[j][l]);
 }
 
+// Elements of the store staged per warp and window (coalesced loads).
+template <typename TS> struct JkStage { static constexpr int CH = sizeof(TS) == 4 ? 1024 : 512; };
+#define JK_WARPS 8
+
 // grid (nchunk, nmol); mode 0: only molecules still iterating, 1: all.
+//
+// A warp walks one row pq; lane L takes ket rs = s0 + L of a 32-ket chunk.
+// The row's kept blocks are contiguous in the store, so the warp first copies
+// a window of them into its shared-memory stage with coalesced loads (lane e
+// reads element e, e + 32, ...), then every lane reads its own block from
+// shared memory (block sizes 1, 3, 9, 27, 81 are odd: no bank conflicts).  A
+// chunk whose blocks exceed one window is done in several windows, each
+// holding whole blocks.
 template <typename TS, typename TA>
-__global__ void __launch_bounds__(256) jk_kernel(DevBatch b, int nchunk, int mode) {
-    extern __shared__ unsigned char smem_raw[];
+__global__ void __launch_bounds__(JK_WARPS * 32) jk_kernel(DevBatch b, int nchunk, int mode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int CH = JkStage<TS>::CH;
     const int m = blockIdx.y, c = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
@@ -106,6 +119,8 @@ __global__ void __launch_bounds__(256) jk_kernel(DevBatch b, int nchunk, int mod
     TA *Ds = (TA *)smem_raw;
     TA *Js = Ds + nn;
     TA *Ks = Js + nn;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    TS *stg = (TS *)(smem_raw + (((size_t)3 * nn * sizeof(TA) + 15) & ~(size_t)15)) + (size_t)warp * CH;
     const double *D = b.mat + md.mat0 + (long long)M_D * nn;
     for (int i = threadIdx.x; i < nn; i += blockDim.x) {
         Ds[i] = (TA)D[i];
@@ -113,7 +128,6 @@ __global__ void __launch_bounds__(256) jk_kernel(DevBatch b, int nchunk, int mod
         Ks[i] = (TA)0;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int npair = b.npair[m];
     const TS *store = (const TS *)b.store + md.eri0;
     for (int r = c + nchunk * warp; r < npair; r += nchunk * nwarp) {
@@ -136,29 +150,43 @@ __global__ void __launch_bounds__(256) jk_kernel(DevBatch b, int nchunk, int mod
                 keep = true;
                 nel = npq * (b.sh_l[R] ? 3 : 1) * (b.sh_l[S] ? 3 : 1);
             }
-            int x = nel;
+            int x = nel;  // inclusive prefix sum of block sizes over the chunk
             for (int o = 1; o < 32; o <<= 1) {
                 int y = __shfl_up_sync(0xffffffffu, x, o);
                 if (lane >= o) x += y;
             }
             const int tot = __shfl_sync(0xffffffffu, x, 31);
-            if (keep) {
-                const TS *v = store + base + x - nel;
-                TA scale = (TA)1;
-                if (P == Q) scale *= (TA)0.5;
-                if (R == S) scale *= (TA)0.5;
-                if (s == r) scale *= (TA)0.5;
-                const int c0 = b.sh_ao0[R], d0 = b.sh_ao0[S];
-                const int cls = (lP << 3) | (lQ << 2) | (b.sh_l[R] << 1) | b.sh_l[S];
-                switch (cls) {
-                case 0x0: jk_block<TS, TA, 0, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0x8: jk_block<TS, TA, 1, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xA: jk_block<TS, TA, 1, 0, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xC: jk_block<TS, TA, 1, 1, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xE: jk_block<TS, TA, 1, 1, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xF: jk_block<TS, TA, 1, 1, 1, 1>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                default: break;
+            const int start = x - nel;  // this lane's block, relative to the chunk
+            int first = 0;              // lanes below it are done
+            while (first < 32) {
+                const int w0 = __shfl_sync(0xffffffffu, start, first);
+                const bool mine = lane >= first && x <= w0 + CH;
+                int wend = mine ? x : w0;
+                for (int o = 16; o > 0; o >>= 1) wend = max(wend, __shfl_xor_sync(0xffffffffu, wend, o));
+                const TS *src = store + base + w0;
+                for (int e = lane; e < wend - w0; e += 32) stg[e] = src[e];
+                __syncwarp();
+                if (mine && keep) {
+                    const TS *v = stg + (start - w0);
+                    TA scale = (TA)1;
+                    if (P == Q) scale *= (TA)0.5;
+                    if (R == S) scale *= (TA)0.5;
+                    if (s == r) scale *= (TA)0.5;
+                    const int c0 = b.sh_ao0[R], d0 = b.sh_ao0[S];
+                    const int cls = (lP << 3) | (lQ << 2) | (b.sh_l[R] << 1) | b.sh_l[S];
+                    switch (cls) {
+                    case 0x0: jk_block<TS, TA, 0, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0x8: jk_block<TS, TA, 1, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0xA: jk_block<TS, TA, 1, 0, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0xC: jk_block<TS, TA, 1, 1, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0xE: jk_block<TS, TA, 1, 1, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0xF: jk_block<TS, TA, 1, 1, 1, 1>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    default: break;
+                    }
                 }
+                __syncwarp();
+                const unsigned pend = __ballot_sync(0xffffffffu, lane >= first && !mine);
+                first = pend ? __ffs(pend) - 1 : 32;
             }
             base += tot;
         }
@@ -193,21 +221,25 @@ __global__ void __launch_bounds__(256) jk_kernel(DevBatch b, int nchunk, int mod
     }
 }
 
+template <typename TS, typename TA> static size_t jk_smem(int n) {
+    return ((3ull * n * n * sizeof(TA) + 15) & ~15ull) + (size_t)JK_WARPS * JkStage<TS>::CH * sizeof(TS);
+}
+
 void launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, cudaStream_t s) {
     dim3 grid(nchunk, b.nmol);
-    int n = max_nbf;
+    const int n = max_nbf;
     if (b.precision == 0) {  // FP64 store
-        size_t sm = 3ull * n * n * sizeof(double);
+        const size_t sm = jk_smem<double, double>(n);
         cudaFuncSetAttribute(jk_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        jk_kernel<double, double><<<grid, 256, sm, s>>>(b, nchunk, mode);
+        jk_kernel<double, double><<<grid, JK_WARPS * 32, sm, s>>>(b, nchunk, mode);
     } else if (acc_fp64) {
-        size_t sm = 3ull * n * n * sizeof(double);
+        const size_t sm = jk_smem<float, double>(n);
         cudaFuncSetAttribute(jk_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        jk_kernel<float, double><<<grid, 256, sm, s>>>(b, nchunk, mode);
+        jk_kernel<float, double><<<grid, JK_WARPS * 32, sm, s>>>(b, nchunk, mode);
     } else {
-        size_t sm = 3ull * n * n * sizeof(float);
+        const size_t sm = jk_smem<float, float>(n);
         cudaFuncSetAttribute(jk_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        jk_kernel<float, float><<<grid, 256, sm, s>>>(b, nchunk, mode);
+        jk_kernel<float, float><<<grid, JK_WARPS * 32, sm, s>>>(b, nchunk, mode);
     }
 }
 
