@@ -105,11 +105,19 @@ __device__ __forceinline__ uint32_t coff(int row, int k, uint32_t sg) {
     return (uint32_t)(row >> 3) * sg + (uint32_t)(k >> 2) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 3) * 4u;
 }
 
+// Named barriers (ids 1, 2) between the operand builders and the MMA warp.
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 }  // namespace tc
 
 struct TcSmem {
     // byte offsets inside the dynamic shared buffer
-    uint32_t D_hi, D_lo, R_g, R_gp, work, set1, pts, coef, part, shx, shf, shi;
+    uint32_t D_hi, D_lo, R_g, R_gp, work, set1, pts, part, xcp, grd, shx, shf, aoc, rset;
     uint32_t total;
 };
 
@@ -119,6 +127,7 @@ struct TcSmem {
 #define TC_SLICE 32
 #define TC_LBO2 144u
 #define TC_SBO2 (8u * TC_LBO2)
+#define TC_SHX 12  // floats per shell in shx: a[3], c[3], -2ac[3], l, ao0, pad
 
 __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
     TcSmem s;
@@ -128,28 +137,31 @@ __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
     s.D_lo = o; o += dsz;
     s.R_g = o; o += (uint32_t)nsh * TC_BP * 4;
     s.R_gp = o; o += (uint32_t)nsh * TC_BP * 4;
-    o = (o + 1023) & ~1023u;
+    o = (o + 127) & ~127u;
     s.work = o;
     // GEMM1: Phi hi, lo (128 points x np AOs, K-major, 128-byte core stride).
-    // GEMM2: two sets of {Phi^T hi, Phi^T lo, X hi, X lo}, each np/8 row groups of
-    // 32-point slices, plus room for the 128-row A reads past the last A buffer.
+    // GEMM2: two sets of {Phi^T hi, Phi^T lo, X hi, X lo}, each np/8 row groups
+    // of 32-point slices.  The M = 128 reads of an A operand run past its np
+    // rows into the next buffer of the same set (rows >= np are never read back).
     const uint32_t w1 = 2u * TC_BP * np * 4;
     const uint32_t opsz = (uint32_t)(np / 8) * TC_SBO2;
-    const uint32_t w2 = 8u * opsz + (uint32_t)((128 - np) / 8) * TC_SBO2;
+    const uint32_t w2 = 8u * opsz;
     s.set1 = 4u * opsz;
     o += (w1 > w2 ? w1 : w2);
-    s.pts = o; o += 4 * TC_BP * 4;
-    s.coef = o; o += 4 * TC_BP * 4;
-    s.part = o; o += 4 * 4 * TC_BP * 4;
-    s.shx = o; o += (uint32_t)nsh * 8 * 4;  // per shell: 3 exponents, 3 coefficients, l, ao0
+    s.pts = o; o += 4 * TC_BP * 4;          // point offsets x, y, z and weight
+    s.part = o; o += 4 * 4 * TC_BP * 4;     // rho, grad rho partials per AO quarter
+    s.xcp = o; o += 3 * 2 * TC_BP * 4;      // v_rho, v_sigma per XC part
+    s.grd = o; o += 3 * TC_BP * 4;          // grad rho
+    s.shx = o; o += (uint32_t)nsh * TC_SHX * 4;
     s.shf = o; o += (uint32_t)nsh * 8 * 4;  // per shell: R_owner0 - C (3), R_owner1 - C (3), pad
-    s.shi = o; o += (uint32_t)np * 2 * 4;   // per AO: shell, component
+    s.aoc = o; o += (uint32_t)np * 4;       // per AO: shell * 4 + component + 1, -1 if zero in this block
+    s.rset = o; o += (uint32_t)nsh * 4;     // radial sets: lead shell | partner << 8 (255: none)
     s.total = o;
     return s;
 }
 
 #define TC_THREADS 512
-#define TC_SCREEN 1e-9f  // per-block AO screening threshold on |phi| and |grad phi| (iterations only)
+#define TC_SCREEN 1e-9f  // per-block AO screening threshold (iterations only)
 
 __device__ __forceinline__ void ld4(uint32_t taddr, float *v) {
     uint32_t r[4];
@@ -161,31 +173,40 @@ __device__ __forceinline__ void ld4(uint32_t taddr, float *v) {
     for (int j = 0; j < 4; j++) v[j] = __uint_as_float(r[j]);
 }
 
+// Lower bound on the distance from a shell centre to any point of a block:
+// the points of owner h lie on atom-centred spheres with radii in [lo, hi],
+// and the centre sits at distance d from that atom.
+__device__ __forceinline__ float shell_rmin(float d, float lo, float hi) {
+    return d > hi ? d - hi : (d < lo ? lo - d : 0.f);
+}
+
 template <typename TA>
 __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar1, bar2[2];
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_nsig, s_nset;
     __shared__ int owner_h[TC_BP];
-    __shared__ int sig[TC_NSHMAX];  // shell significant somewhere in this block
+    __shared__ int sig[TC_NSHMAX];        // shell significant somewhere in this block
+    __shared__ unsigned blk_r[4];         // radius range of the block per owner (float bits)
     const int m = blockIdx.y, chunk = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
     const int n = md.nbf, nsh = md.nsh;
     const int np = (n + 15) & ~15;
-    const int nq = np / 4;  // AO columns per thread group (multiple of 4)
+    const int nq = np / 4;  // AO columns per thread quarter (multiple of 4)
     const TcSmem L = tc_layout(np, nsh);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     unsigned char *sm = smem;
     float *Rg = (float *)(sm + L.R_g), *Rgp = (float *)(sm + L.R_gp);
-    float *pt = (float *)(sm + L.pts), *cf = (float *)(sm + L.coef), *part = (float *)(sm + L.part);
+    float *pt = (float *)(sm + L.pts), *part = (float *)(sm + L.part);
+    float *xcp = (float *)(sm + L.xcp), *grd = (float *)(sm + L.grd);
     float *shx = (float *)(sm + L.shx), *shf = (float *)(sm + L.shf);
     int *shxi = (int *)shx;
-    int *shi = (int *)(sm + L.shi);
+    int *aoc = (int *)(sm + L.aoc), *rset = (int *)(sm + L.rset);
     const uint32_t sg1 = (uint32_t)(np / 4) * 128u;  // row-group stride, K = np (GEMM1 A and B)
 
-    // ---- per-CTA constants: D (hi, lo) as GEMM1's B (rows nu, K = mu), shells, AO map
+    // ---- per-CTA constants: D (hi, lo) as GEMM1's B (rows nu, K = mu), shells, radial sets
     const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
     for (int i = t; i < np * np / 4; i += blockDim.x) {
         const int row = i / (np / 4), kc = i % (np / 4);
@@ -204,19 +225,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
         const int g = md.sh0 + s;
         const int l = b.sh_l[g], a0 = b.sh_ao0[g];
         for (int k = 0; k < 3; k++) {
-            shx[s * 8 + k] = (float)b.sh_ex[g * 3 + k];
-            shx[s * 8 + 3 + k] = (float)b.sh_co[g * 3 + k];
+            const double a = b.sh_ex[g * 3 + k], c = b.sh_co[g * 3 + k];
+            shx[s * TC_SHX + k] = (float)a;
+            shx[s * TC_SHX + 3 + k] = (float)c;
+            shx[s * TC_SHX + 6 + k] = (float)(-2.0 * a * c);
         }
-        shxi[s * 8 + 6] = l;
-        shxi[s * 8 + 7] = a0;
-        for (int c = 0; c < (l ? 3 : 1); c++) {
-            shi[(a0 + c) * 2] = s;
-            shi[(a0 + c) * 2 + 1] = l ? c : -1;  // -1: s function
-        }
+        shxi[s * TC_SHX + 9] = l;
+        shxi[s * TC_SHX + 10] = a0;
     }
-    for (int mu = n + t; mu < np; mu += blockDim.x) {
-        shi[mu * 2] = -1;
-        shi[mu * 2 + 1] = -1;
+    if (t == 0) s_nset = 0;
+    __syncthreads();
+    if (t < nsh) {
+        // radial sets: a p shell shares the exponents of its atom's 2s shell
+        // (STO-3G 2sp), so one set of exponentials serves both
+        const int g = md.sh0 + t;
+        const int l = b.sh_l[g], at = b.sh_atom[g];
+        const double e0 = b.sh_ex[g * 3], e1 = b.sh_ex[g * 3 + 1], e2 = b.sh_ex[g * 3 + 2];
+        int partner = 255;
+        for (int q2 = 0; q2 < nsh; q2++) {
+            const int h = md.sh0 + q2;
+            if (b.sh_l[h] != l && b.sh_atom[h] == at && b.sh_ex[h * 3] == e0 && b.sh_ex[h * 3 + 1] == e1 &&
+                b.sh_ex[h * 3 + 2] == e2)
+                partner = q2;
+        }
+        if (l == 0) rset[atomicAdd(&s_nset, 1)] = t | (partner << 8);      // s shell leads its set
+        else if (partner == 255) rset[atomicAdd(&s_nset, 1)] = t | (255 << 8);  // unpaired p shell
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_slot)),
@@ -238,9 +271,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     const uint32_t tT = tmem, tV = tmem + TC_NPMAX;  // column bases of T (GEMM1) and V (GEMM2)
     const uint32_t id1 = tc::idesc(128, np), id2 = tc::idesc(128, np);
     const uint32_t su = tc::smem_u32(sm);
+    const int nset = s_nset;
     uint32_t ph1 = 0, ph2[2] = {0, 0};
     double exc = 0.0;
-    // thread group g4 (0..3) and TMEM lane quarter q: V' row q*32 + lane, columns [g4*nq, g4*nq + nq)
+    // thread quarter g4 (0..3) and TMEM lane quarter q: V' row q*32 + lane, columns [g4*nq, g4*nq + nq)
     const int q = warp & 3, g4 = warp >> 2;
     float vacc[TC_NPMAX / 4];
 #pragma unroll
@@ -251,47 +285,116 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     const float *gzp = (const float *)b.gz + md.pts0, *gwp = (const float *)b.gw + md.pts0;
     bool failed = false;
     const int npa = b.n_rad * b.n_theta * b.n_phi;
+    // point data of the next block, prefetched into registers (threads < 128)
+    float nx = 0.f, ny = 0.f, nz = 0.f, nw = 0.f;
+    if (t < TC_BP && chunk < md.nblk) {
+        const int i0 = chunk * TC_BP + t;
+        nx = gxp[i0]; ny = gyp[i0]; nz = gzp[i0]; nw = gwp[i0];
+    }
+    int shf_owner = -1;  // owner atom the shf table was built for
     for (int blk = chunk; blk < md.nblk && !failed; blk += nchunk) {
-        any_block = true;
         const int p0 = blk * TC_BP;
         const int own0 = min(p0 / npa, md.natom - 1);
-        if (t < TC_BP) {
-            owner_h[t] = min((p0 + t) / npa, md.natom - 1) - own0;
-            pt[t] = gxp[p0 + t];
-            pt[TC_BP + t] = gyp[p0 + t];
-            pt[2 * TC_BP + t] = gzp[p0 + t];
-            pt[3 * TC_BP + t] = gwp[p0 + t];
-        }
-        for (int i = t; i < 2 * nsh; i += blockDim.x) {
-            const int hh = i / nsh, s = i % nsh;
-            const int A = min(own0 + hh, md.natom - 1);
-            const double *ra = b.axyz + (md.atom0 + A) * 3, *rc = b.sh_xyz + (md.sh0 + s) * 3;
-            shf[s * 8 + hh * 3 + 0] = (float)(ra[0] - rc[0]);
-            shf[s * 8 + hh * 3 + 1] = (float)(ra[1] - rc[1]);
-            shf[s * 8 + hh * 3 + 2] = (float)(ra[2] - rc[2]);
-        }
-        for (int s = t; s < nsh; s += blockDim.x) sig[s] = 0;
+        if (t < 4) blk_r[t] = (t & 1) ? 0u : 0x7f800000u;  // lo = +inf, hi = 0 per owner
+        if (t == 0) s_nsig = 0;
         __syncthreads();
-        // ---- A: radial parts per (shell, point) and per-block shell significance
-        for (int i = t; i < nsh * TC_BP; i += blockDim.x) {
-            const int s = i >> 7, p = i & (TC_BP - 1);
-            const float *dl = shf + s * 8 + owner_h[p] * 3;
+        if (t < TC_BP) {
+            const int h = min((p0 + t) / npa, md.natom - 1) - own0;
+            owner_h[t] = h;
+            pt[t] = nx;
+            pt[TC_BP + t] = ny;
+            pt[2 * TC_BP + t] = nz;
+            pt[3 * TC_BP + t] = nw;
+            const unsigned rb = __float_as_uint(sqrtf(nx * nx + ny * ny + nz * nz));  // r >= 0: bits order as floats
+            const unsigned lo0 = __reduce_min_sync(0xffffffffu, h == 0 ? rb : 0x7f800000u);
+            const unsigned hi0 = __reduce_max_sync(0xffffffffu, h == 0 ? rb : 0u);
+            const unsigned lo1 = __reduce_min_sync(0xffffffffu, h == 1 ? rb : 0x7f800000u);
+            const unsigned hi1 = __reduce_max_sync(0xffffffffu, h == 1 ? rb : 0u);
+            if (lane == 0) {
+                atomicMin(&blk_r[0], lo0);
+                atomicMax(&blk_r[1], hi0);
+                atomicMin(&blk_r[2], lo1);
+                atomicMax(&blk_r[3], hi1);
+            }
+            const int i1 = p0 + nchunk * TC_BP + t;  // next block of this CTA
+            if (blk + nchunk < md.nblk) {
+                nx = gxp[i1]; ny = gyp[i1]; nz = gzp[i1]; nw = gwp[i1];
+            }
+        }
+        if (own0 != shf_owner) {  // R_owner - C for the block's (at most two) owners
+            for (int i = t; i < 2 * nsh; i += blockDim.x) {
+                const int hh = i / nsh, s = i % nsh;
+                const int A = min(own0 + hh, md.natom - 1);
+                const double *ra = b.axyz + (md.atom0 + A) * 3, *rc = b.sh_xyz + (md.sh0 + s) * 3;
+                shf[s * 8 + hh * 3 + 0] = (float)(ra[0] - rc[0]);
+                shf[s * 8 + hh * 3 + 1] = (float)(ra[1] - rc[1]);
+                shf[s * 8 + hh * 3 + 2] = (float)(ra[2] - rc[2]);
+            }
+            shf_owner = own0;
+        }
+        __syncthreads();
+        // ---- shell significance from the block's radius range (one thread per shell)
+        if (t < nsh) {
+            const int s = t;
+            float rmin = 3.4e38f;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const float lo = __uint_as_float(blk_r[2 * h]), hi = __uint_as_float(blk_r[2 * h + 1]);
+                if (lo > hi) continue;  // no point of this owner in the block
+                const float *dl = shf + s * 8 + h * 3;
+                const float d = sqrtf(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
+                rmin = fminf(rmin, shell_rmin(d, lo, hi));
+            }
+            // |phi|, |grad phi| <= sum_k |c_k| e^(-a_k r^2) (1 + r + 2 a_k r^3), decreasing in r
+            // beyond r = 4 bohr for every STO-3G exponent
+            bool on = rmin < 4.f;
+            if (!on) {
+                float bound = 0.f;
+                for (int k = 0; k < 3; k++) {
+                    const float a = shx[s * TC_SHX + k];
+                    bound += fabsf(shx[s * TC_SHX + 3 + k]) * __expf(-a * rmin * rmin) *
+                             (1.f + rmin + 2.f * a * rmin * rmin * rmin);
+                }
+                on = bound > TC_SCREEN;
+            }
+            sig[s] = on;
+            if (on) atomicAdd(&s_nsig, 1);
+        }
+        __syncthreads();
+        const int nsig = s_nsig;
+        __syncthreads();  // s_nsig is reset at the top of the next block
+        if (nsig == 0) continue;  // every AO below the screen: rho under the XC cutoff everywhere
+        any_block = true;
+        for (int mu = t; mu < np; mu += blockDim.x) aoc[mu] = -1;
+        __syncthreads();
+        for (int s = t; s < nsh; s += blockDim.x) {
+            if (!sig[s]) continue;
+            const int l = shxi[s * TC_SHX + 9], a0 = shxi[s * TC_SHX + 10];
+            if (l == 0) aoc[a0] = s * 4;
+            else for (int c = 0; c < 3; c++) aoc[a0 + c] = s * 4 + c + 1;
+        }
+        // ---- A: radial parts g = sum c e^(-a r^2), g' = sum -2ac e^(-a r^2) per (shell, point),
+        // one set of exponentials per radial set
+#pragma unroll 2
+        for (int i = t; i < nset * TC_BP; i += blockDim.x) {
+            const int k = i >> 7, p = i & (TC_BP - 1);
+            const int s1 = rset[k] & 255, s2 = rset[k] >> 8;
+            const bool on1 = sig[s1], on2 = s2 != 255 && sig[s2];
+            if (!on1 && !on2) continue;
+            const float *dl = shf + s1 * 8 + owner_h[p] * 3;
             const float dx = dl[0] + pt[p], dy = dl[1] + pt[TC_BP + p], dz = dl[2] + pt[2 * TC_BP + p];
             const float r2 = dx * dx + dy * dy + dz * dz;
-            float gg = 0.f, gp = 0.f;
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                const float a = shx[s * 8 + k];
-                const float e = shx[s * 8 + 3 + k] * __expf(-a * r2);
-                gg += e;
-                gp -= 2.f * a * e;
+            const float *x1 = shx + s1 * TC_SHX;
+            const float e0 = __expf(-x1[0] * r2), e1 = __expf(-x1[1] * r2), e2 = __expf(-x1[2] * r2);
+            if (on1) {
+                Rg[s1 * TC_BP + p] = x1[3] * e0 + x1[4] * e1 + x1[5] * e2;
+                Rgp[s1 * TC_BP + p] = x1[6] * e0 + x1[7] * e1 + x1[8] * e2;
             }
-            Rg[s * TC_BP + p] = gg;
-            Rgp[s * TC_BP + p] = gp;
-            // |phi| and |grad phi| bounds for s and p functions
-            const float r = sqrtf(r2);
-            const float bound = fabsf(gg) * fmaxf(1.f, r) + fabsf(gp) * fmaxf(r, r2);
-            if (bound > TC_SCREEN && !sig[s]) sig[s] = 1;  // benign race: every writer stores 1
+            if (on2) {
+                const float *x2 = shx + s2 * TC_SHX;
+                Rg[s2 * TC_BP + p] = x2[3] * e0 + x2[4] * e1 + x2[5] * e2;
+                Rgp[s2 * TC_BP + p] = x2[6] * e0 + x2[7] * e1 + x2[8] * e2;
+            }
         }
         __syncthreads();
         // ---- B: Phi (points x AOs) for GEMM1; thread = (point, AO quarter)
@@ -304,10 +407,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                 float v[4];
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
-                    const int mu = kc * 4 + j;
-                    const int s = shi[mu * 2], c = shi[mu * 2 + 1];
+                    const int code = aoc[kc * 4 + j];
                     float val = 0.f;
-                    if (s >= 0 && sig[s]) {
+                    if (code >= 0) {
+                        const int s = code >> 2, c = (code & 3) - 1;
                         const float gg = Rg[s * TC_BP + p];
                         val = (c < 0) ? gg : (shf[s * 8 + hp * 3 + c] + pt[c * TC_BP + p]) * gg;
                     }
@@ -333,7 +436,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                 tc::commit(&bar1);
             }
         }
-        // ---- D: density from the T rows (thread = point, AO quarter)
+        // ---- D: density from the T rows, shell by shell (thread = point, AO quarter):
+        // with u = sum_c T_c d_c (p shell; u = T for an s shell) and Tv = (T_x, T_y, T_z),
+        // rho += g u and grad rho += 2 (g' u d + g Tv)
         const bool ok1 = __syncthreads_and(tc::wait(&bar1, ph1));
         ph1 ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -343,32 +448,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
         }
         {
             float rho = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+            int cur = -1;
+            float cg = 0.f, cgp = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, u = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
             for (int cc = g4 * nq; cc < (g4 + 1) * nq; cc += 4) {
                 float tv[4];
                 ld4(tT + ((uint32_t)(q * 32) << 16) + cc, tv);
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
-                    const int nu = cc + j;
-                    const int s = shi[nu * 2], c = shi[nu * 2 + 1];
-                    if (s < 0 || !sig[s]) continue;
-                    const float gg = Rg[s * TC_BP + p], gp = Rgp[s * TC_BP + p];
-                    const float *dl = shf + s * 8 + hp * 3;
-                    const float dx = dl[0] + px, dy = dl[1] + py, dz = dl[2] + pz;
-                    float f, fx, fy, fz;
-                    if (c < 0) {
-                        f = gg; fx = gp * dx; fy = gp * dy; fz = gp * dz;
-                    } else {
-                        const float dc = c == 0 ? dx : (c == 1 ? dy : dz);
-                        f = dc * gg;
-                        fx = gp * dc * dx + (c == 0 ? gg : 0.f);
-                        fy = gp * dc * dy + (c == 1 ? gg : 0.f);
-                        fz = gp * dc * dz + (c == 2 ? gg : 0.f);
+                    const int code = aoc[cc + j];
+                    if (code < 0) continue;
+                    const int s = code >> 2, c = (code & 3) - 1;
+                    if (s != cur) {
+                        if (cur >= 0) {
+                            rho += cg * u;
+                            rx += cgp * u * dx + cg * tx;
+                            ry += cgp * u * dy + cg * ty;
+                            rz += cgp * u * dz + cg * tz;
+                        }
+                        cur = s;
+                        cg = Rg[s * TC_BP + p];
+                        cgp = Rgp[s * TC_BP + p];
+                        const float *dl = shf + s * 8 + hp * 3;
+                        dx = dl[0] + px; dy = dl[1] + py; dz = dl[2] + pz;
+                        u = tx = ty = tz = 0.f;
                     }
-                    rho += tv[j] * f;
-                    rx += tv[j] * fx;
-                    ry += tv[j] * fy;
-                    rz += tv[j] * fz;
+                    if (c < 0) {
+                        u = tv[j];
+                    } else if (c == 0) {
+                        u += tv[j] * dx; tx = tv[j];
+                    } else if (c == 1) {
+                        u += tv[j] * dy; ty = tv[j];
+                    } else {
+                        u += tv[j] * dz; tz = tv[j];
+                    }
                 }
+            }
+            if (cur >= 0) {
+                rho += cg * u;
+                rx += cgp * u * dx + cg * tx;
+                ry += cgp * u * dy + cg * ty;
+                rz += cgp * u * dz + cg * tz;
             }
             part[(g4 * 4 + 0) * TC_BP + p] = rho;
             part[(g4 * 4 + 1) * TC_BP + p] = rx;
@@ -376,102 +495,123 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
             part[(g4 * 4 + 3) * TC_BP + p] = rz;
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
-            if (t < TC_BP) {
+            // XC in three parts on three warp groups (exchange, VWN5, LYP)
+            if (t < 3 * TC_BP) {
+                const int gi = t >> 7;
                 float r = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
                 for (int gq = 0; gq < 4; gq++) {
-                    r += part[(gq * 4 + 0) * TC_BP + t];
-                    gx += part[(gq * 4 + 1) * TC_BP + t];
-                    gy += part[(gq * 4 + 2) * TC_BP + t];
-                    gz += part[(gq * 4 + 3) * TC_BP + t];
+                    r += part[(gq * 4 + 0) * TC_BP + p];
+                    gx += part[(gq * 4 + 1) * TC_BP + p];
+                    gy += part[(gq * 4 + 2) * TC_BP + p];
+                    gz += part[(gq * 4 + 3) * TC_BP + p];
                 }
                 gx *= 2.f; gy *= 2.f; gz *= 2.f;
-                const float w = pt[3 * TC_BP + t];
+                const float w = pt[3 * TC_BP + p];
                 float e = 0.f, vr = 0.f, vs = 0.f;
-                if (w != 0.f) xc::b3lyp<float>(r, gx * gx + gy * gy + gz * gz, e, vr, vs);
+                if (w != 0.f) xc::b3lyp_part<float>(gi, r, gx * gx + gy * gy + gz * gz, e, vr, vs);
                 exc += (double)w * (double)e;
-                cf[t] = 0.5f * w * vr;
-                cf[TC_BP + t] = 2.f * w * vs * gx;
-                cf[2 * TC_BP + t] = 2.f * w * vs * gy;
-                cf[3 * TC_BP + t] = 2.f * w * vs * gz;
+                xcp[(gi * 2 + 0) * TC_BP + p] = vr;
+                xcp[(gi * 2 + 1) * TC_BP + p] = vs;
+                if (gi == 0) {
+                    grd[p] = gx;
+                    grd[TC_BP + p] = gy;
+                    grd[2 * TC_BP + p] = gz;
+                }
             }
             __syncthreads();
         }
-        // ---- F: GEMM2 in 32-point slices, ping-pong operand sets; the MMAs of
-        // slice k run while slice k + 1 is built.  Thread = (point in slice, shell group of 16).
-        for (int k = 0; k < TC_BP / TC_SLICE; k++) {
-            const int set = k & 1;
-            if (k >= 2) {
-                const bool ok = __syncthreads_and(tc::wait(&bar2[set], ph2[set]));
-                ph2[set] ^= 1;
-                if (!ok) {
-                    failed = true;
-                    break;
-                }
-            }
-            const uint32_t base = L.work + (set ? L.set1 : 0u);
+        // ---- F: GEMM2 in 32-point slices, ping-pong operand sets.  Warps 0-14
+        // build a slice's operands (lane = point, warp = every 15th shell) and
+        // arrive on the set's named barrier; warp 15 waits there and issues the
+        // slice's MMAs, so the next slice is built while the tensor core runs.
+        {
+            const int nb = TC_THREADS / 32 - 1;  // builder warps
+            const bool issuer = warp == nb;
             const uint32_t opsz = (uint32_t)(np / 8) * TC_SBO2;
-            const uint32_t at_hi = base, at_lo = base + opsz, x_hi = base + 2 * opsz, x_lo = base + 3 * opsz;
-            const int pl = lane, pp = k * TC_SLICE + pl;
-            const float *dlb = shf + owner_h[pp] * 3;
-            const float ox = pt[pp], oy = pt[TC_BP + pp], oz = pt[2 * TC_BP + pp];
-            const float a = cf[pp], bx = cf[TC_BP + pp], by = cf[2 * TC_BP + pp], bz = cf[3 * TC_BP + pp];
-            const uint32_t pofs = (uint32_t)(pl >> 2) * TC_LBO2 + (uint32_t)(pl & 3) * 4u;
-            for (int s = warp; s < nsh; s += TC_THREADS / 32) {
-                const int l = shxi[s * 8 + 6], a0 = shxi[s * 8 + 7];
-                const int ncomp = l ? 3 : 1;
-                if (!sig[s]) {
-                    for (int c = 0; c < ncomp; c++) {
-                        const int mu = a0 + c;
-                        const uint32_t off = (uint32_t)(mu >> 3) * TC_SBO2 + (uint32_t)(mu & 7) * 16u + pofs;
-                        *(float *)(sm + at_hi + off) = 0.f;
-                        *(float *)(sm + at_lo + off) = 0.f;
-                        *(float *)(sm + x_hi + off) = 0.f;
-                        *(float *)(sm + x_lo + off) = 0.f;
+            for (int k = 0; k < TC_BP / TC_SLICE; k++) {
+                const int set = k & 1;
+                const uint32_t base = L.work + (set ? L.set1 : 0u);
+                const uint32_t at_hi = base, at_lo = base + opsz, x_hi = base + 2 * opsz, x_lo = base + 3 * opsz;
+                if (!issuer) {
+                    // the set's previous MMAs (slice k - 2) must be done before it is rewritten
+                    bool ok = true;
+                    if (k >= 2) ok = tc::wait(&bar2[set], ph2[set]);
+                    if (!ok) s_fail = 1;  // benign race: every writer stores 1
+                    const int pl = lane, pp = k * TC_SLICE + pl;
+                    const float *dlb = shf + owner_h[pp] * 3;
+                    const float ox = pt[pp], oy = pt[TC_BP + pp], oz = pt[2 * TC_BP + pp];
+                    const float w = pt[3 * TC_BP + pp];
+                    const float vr = xcp[pp] + xcp[2 * TC_BP + pp] + xcp[4 * TC_BP + pp];
+                    const float vs2 = 2.f * w * (xcp[TC_BP + pp] + xcp[5 * TC_BP + pp]);
+                    const float a = 0.5f * w * vr;
+                    const float bx = vs2 * grd[pp], by = vs2 * grd[TC_BP + pp], bz = vs2 * grd[2 * TC_BP + pp];
+                    const uint32_t pofs = (uint32_t)(pl >> 2) * TC_LBO2 + (uint32_t)(pl & 3) * 4u;
+#pragma unroll
+                    for (int j = 0; j < (TC_NSHMAX + 14) / 15; j++) {
+                        const int s = warp + nb * j;
+                        if (s >= nsh) break;
+                        const int l = shxi[s * TC_SHX + 9], a0 = shxi[s * TC_SHX + 10];
+                        const int ncomp = l ? 3 : 1;
+                        const uint32_t off0 = pofs + (uint32_t)(a0 >> 3) * TC_SBO2 + (uint32_t)(a0 & 7) * 16u;
+                        if (!sig[s]) {
+                            for (int c = 0; c < ncomp; c++) {
+                                const int mu = a0 + c;
+                                const uint32_t off = pofs + (uint32_t)(mu >> 3) * TC_SBO2 + (uint32_t)(mu & 7) * 16u;
+                                *(float *)(sm + at_hi + off) = 0.f;
+                                *(float *)(sm + at_lo + off) = 0.f;
+                                *(float *)(sm + x_hi + off) = 0.f;
+                                *(float *)(sm + x_lo + off) = 0.f;
+                            }
+                            continue;
+                        }
+                        const float gg = Rg[s * TC_BP + pp], gp = Rgp[s * TC_BP + pp];
+                        const float *dl = dlb + s * 8;
+                        const float dx = dl[0] + ox, dy = dl[1] + oy, dz = dl[2] + oz;
+                        const float basev = a * gg + gp * (bx * dx + by * dy + bz * dz);
+                        if (!l) {
+                            const float fh = tc::tf32_hi(gg), xh = tc::tf32_hi(basev);
+                            *(float *)(sm + at_hi + off0) = fh;
+                            *(float *)(sm + at_lo + off0) = gg - fh;
+                            *(float *)(sm + x_hi + off0) = xh;
+                            *(float *)(sm + x_lo + off0) = basev - xh;
+                        } else {
+                            const float dd[3] = {dx, dy, dz}, bb[3] = {bx, by, bz};
+#pragma unroll
+                            for (int c = 0; c < 3; c++) {
+                                const int mu = a0 + c;
+                                const uint32_t off = pofs + (uint32_t)(mu >> 3) * TC_SBO2 + (uint32_t)(mu & 7) * 16u;
+                                const float f = dd[c] * gg, x = dd[c] * basev + bb[c] * gg;
+                                const float fh = tc::tf32_hi(f), xh = tc::tf32_hi(x);
+                                *(float *)(sm + at_hi + off) = fh;
+                                *(float *)(sm + at_lo + off) = f - fh;
+                                *(float *)(sm + x_hi + off) = xh;
+                                *(float *)(sm + x_lo + off) = x - xh;
+                            }
+                        }
                     }
-                    continue;
-                }
-                const float gg = Rg[s * TC_BP + pp], gp = Rgp[s * TC_BP + pp];
-                const float *dl = dlb + s * 8;
-                const float dx = dl[0] + ox, dy = dl[1] + oy, dz = dl[2] + oz;
-                const float bd = bx * dx + by * dy + bz * dz;
-                const float basev = a * gg + gp * bd;
-                for (int c = 0; c < ncomp; c++) {
-                    float f, x;
-                    if (!l) {
-                        f = gg;
-                        x = basev;
-                    } else {
-                        const float dc = c == 0 ? dx : (c == 1 ? dy : dz);
-                        const float bc = c == 0 ? bx : (c == 1 ? by : bz);
-                        f = dc * gg;
-                        x = dc * basev + bc * gg;
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    tc::bar_arrive(1 + set, TC_THREADS);
+                } else {
+                    tc::bar_sync(1 + set, TC_THREADS);
+                    if (lane == 0 && !s_fail) {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        for (int s2 = 0; s2 < TC_SLICE / 8; s2++) {
+                            const uint32_t ka = 2u * s2 * TC_LBO2;
+                            const uint64_t ah = tc::sdesc(su + at_hi + ka, TC_LBO2, TC_SBO2);
+                            const uint64_t al = tc::sdesc(su + at_lo + ka, TC_LBO2, TC_SBO2);
+                            const uint64_t bh = tc::sdesc(su + x_hi + ka, TC_LBO2, TC_SBO2);
+                            const uint64_t bl = tc::sdesc(su + x_lo + ka, TC_LBO2, TC_SBO2);
+                            tc::mma(tV, ah, bh, id2, (k > 0 || s2 > 0) ? 1u : 0u);
+                            tc::mma(tV, ah, bl, id2, 1);
+                            tc::mma(tV, al, bh, id2, 1);
+                        }
                     }
-                    const int mu = a0 + c;
-                    const uint32_t off = (uint32_t)(mu >> 3) * TC_SBO2 + (uint32_t)(mu & 7) * 16u + pofs;
-                    const float fh = tc::tf32_hi(f), xh = tc::tf32_hi(x);
-                    *(float *)(sm + at_hi + off) = fh;
-                    *(float *)(sm + at_lo + off) = f - fh;
-                    *(float *)(sm + x_hi + off) = xh;
-                    *(float *)(sm + x_lo + off) = x - xh;
+                    if (lane == 0) tc::commit(&bar2[set]);  // arrives even when nothing was issued
                 }
+                if (k >= 2) ph2[set] ^= 1;
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (t == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                for (int s = 0; s < TC_SLICE / 8; s++) {
-                    const uint32_t ka = 2u * s * TC_LBO2;
-                    const uint64_t ah = tc::sdesc(su + at_hi + ka, TC_LBO2, TC_SBO2);
-                    const uint64_t al = tc::sdesc(su + at_lo + ka, TC_LBO2, TC_SBO2);
-                    const uint64_t bh = tc::sdesc(su + x_hi + ka, TC_LBO2, TC_SBO2);
-                    const uint64_t bl = tc::sdesc(su + x_lo + ka, TC_LBO2, TC_SBO2);
-                    tc::mma(tV, ah, bh, id2, (k > 0 || s > 0) ? 1u : 0u);
-                    tc::mma(tV, ah, bl, id2, 1);
-                    tc::mma(tV, al, bh, id2, 1);
-                }
-                tc::commit(&bar2[set]);
-            }
+            failed = __syncthreads_or(s_fail != 0);
         }
         if (failed) break;
         // drain the last two slices, then fold this block's V' into registers
@@ -537,7 +677,7 @@ bool grid_xc_tc_supported(int max_nbf, int max_nsh) {
 void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
                        cudaStream_t s) {
     const int np = (max_nbf + 15) & ~15;
-    const size_t sm = tc_layout(np, max_nsh).total + 1024;
+    const size_t sm = tc_layout(np, max_nsh).total + 128;
     if (acc_fp64) {
         cudaFuncSetAttribute(grid_xc_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         grid_xc_tc_kernel<double><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);

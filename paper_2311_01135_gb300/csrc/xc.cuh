@@ -114,4 +114,66 @@ __host__ __device__ __forceinline__ void b3lyp(T rho, T sigma, T &e, T &vr, T &v
     vs = (T)0.72 * vs_b + (T)0.81 * vs_l;
 }
 
+// The same functional in three independent weighted parts (0: 0.80 Slater +
+// 0.72 B88, 1: 0.19 VWN5, 2: 0.81 LYP) whose sum is b3lyp(); lets three warp
+// groups evaluate one block of points in parallel.  Same formulas, same
+// cutoffs; only the order of the final sum differs.
+template <typename T>
+__host__ __device__ __forceinline__ void b3lyp_part(int part, T rho, T sigma, T &e, T &vr, T &vs) {
+    e = vr = vs = (T)0;
+    if (!(rho >= (T)RHO_CUT)) return;
+    if (sigma < (T)SIGMA_FLOOR) sigma = (T)SIGMA_FLOOR;
+    const T r13 = cbrt_(rho);
+    const T rm13 = (T)1 / r13;
+    const T rm43 = rm13 / rho;
+    if (part == 0) {
+        const T r43 = rho * r13;
+        const T Cx = (T)0.73855876638202240588;
+        const T beta = (T)0.0042;
+        const T K = (T)1.2599210498948731648 * beta;
+        const T sq = sqrt_(sigma);
+        const T x = (T)1.2599210498948731648 * sq * rm43;
+        const T ash = asinh_(x);
+        const T g = (T)1 + (T)6 * beta * x * ash;
+        const T gp = (T)6 * beta * (ash + x / sqrt_((T)1 + x * x));
+        const T ig = (T)1 / g;
+        e = (T)0.80 * (-Cx * r43) + (T)0.72 * (-K * sigma * rm43 * ig);
+        vr = (T)0.80 * (-(T)(4.0 / 3.0) * Cx * r13) +
+             (T)0.72 * ((T)(4.0 / 3.0) * K * sigma * rm43 / rho * (ig - x * gp * ig * ig));
+        vs = (T)0.72 * (-K * rm43 * (ig - (T)0.5 * x * gp * ig * ig));
+    } else if (part == 1) {
+        const T A = (T)0.0310907, x0 = (T)-0.10498, bv = (T)3.72744, cv = (T)12.9352;
+        const T Qv = (T)6.15199081975908;
+        const T X0 = x0 * x0 + bv * x0 + cv;
+        const T rs = (T)0.62035049089940001667 * rm13;
+        const T xs = sqrt_(rs);
+        const T Xx = xs * xs + bv * xs + cv;
+        const T at = atan_(Qv / ((T)2 * xs + bv));
+        const T l1 = log_(xs * xs / Xx);
+        const T l2 = log_((xs - x0) * (xs - x0) / Xx);
+        const T eps_c = A * (l1 + (T)2 * bv / Qv * at - bv * x0 / X0 * (l2 + (T)2 * (bv + (T)2 * x0) / Qv * at));
+        const T dXx = (T)2 * xs + bv;
+        const T deps_dx = A * ((T)2 / xs - dXx / Xx - bv / Xx
+                               - bv * x0 / X0 * ((T)2 / (xs - x0) - dXx / Xx - (bv + (T)2 * x0) / Xx));
+        e = (T)0.19 * (rho * eps_c);
+        vr = (T)0.19 * (eps_c - deps_dx * xs / (T)6);
+    } else {
+        const T la = (T)0.04918, lb = (T)0.132, lc = (T)0.2533, ld = (T)0.349;
+        const T CF = (T)2.8712340001881918;
+        const T den = (T)1 / ((T)1 + ld * rm13);
+        const T Ec = exp_(-lc * rm13);
+        const T delta = lc * rm13 + ld * rm13 * den;
+        const T h = (T)(1.0 / 24.0) + (T)(7.0 / 72.0) * delta;
+        const T rm53 = rm43 * rm13;
+        const T rm83 = rm53 / rho;
+        e = (T)0.81 * (-la * rho * den - la * lb * Ec * den * (CF * rho - rm53 * sigma * h));
+        vs = (T)0.81 * (la * lb * Ec * den * rm53 * h);
+        vr = (T)0.81 * (-la * den - la * ld * rm13 * den * den / (T)3
+                        - la * lb * CF * Ec * den * ((T)1 + lc * rm13 / (T)3 + ld * rm13 * den / (T)3)
+                        + la * lb * sigma * Ec * den * rm83 *
+                              (h * (lc * rm13 / (T)3 + ld * rm13 * den / (T)3 - (T)(5.0 / 3.0))
+                               - (T)(7.0 / 216.0) * rm13 * (lc + ld * den - ld * ld * rm13 * den * den)));
+    }
+}
+
 }  // namespace xc
