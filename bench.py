@@ -215,6 +215,76 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- serving leg
+SERVE_TOL = {"fp64": (1e-7, 1e-5), "mixed": (1e-5, 1e-5)}
+
+
+def serve_run(g, precision, rate, n, seed=3):
+    """Poisson serving trace (1-11 heavy atoms) through rks_submit / rks_wait /
+    rks_result with the serving protocol: converge (|dE| < e_tol, max|e| <
+    err_tol, at most 40 iterations), then the final step.  The mixed path's
+    iteration energies carry ~1e-6 Ha of FP32 product rounding, so its dE test
+    sits at 1e-5 (the reported energy comes from the FP64-accumulated final
+    step).  Latency is submit -> result published, from the library;
+    sustained throughput is molecules / (last completion - first submission)."""
+    t_arr, mols = molgen.serving_trace(seed, n, rate)
+    pname = "mixed" if precision == g.RKS_MIXED else "fp64"
+    e_tol, err_tol = SERVE_TOL[pname]
+    opts = dict(precision=precision, fixed_iters=0, e_tol=e_tol, err_tol=err_tol, max_iters=40, admit_wait_us=2000)
+    with g.Context(**opts) as ctx:
+        warm = ctx.submit_many(mols[:8])  # module load and first launches, not measured
+        for tk in warm:
+            ctx.wait(tk, 600)
+            ctx.result(tk)
+        tickets, t_sub = [None] * n, [0.0] * n
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i in range(n):
+                dt = t_arr[i] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                t_sub[i] = time.perf_counter() - t0
+                tickets[i] = ctx.submit(*mols[i])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        lat, done, bad, energies = [], [], 0, []
+        for i, tk in enumerate(tickets):
+            ctx.wait(tk, 3600)
+            r = ctx.result(tk)
+            lat.append(r["latency_s"])
+            done.append(t_sub[i] + r["latency_s"])
+            bad += r["status"] != "ok"
+            energies.append((r["E"], r["gap"]))
+    span = max(done) - t_sub[0]
+    return {"mode": "serve", "precision": pname, "rate_per_s": rate,
+            "n": n, "sustained_mol_per_s": n / span, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "not_converged": bad, "e_tol": e_tol, "err_tol": err_tol,
+            "workload": "Poisson arrivals, 1-11 heavy atoms (seed 3), converge then final step, cap 40"}, energies
+
+
+def serve_main(args):
+    """Rate sweep, mixed then FP64 (fewer molecules: ~20x slower); the
+    molecules of the FP64 runs are the first ones of the mixed runs, so the
+    mixed-vs-FP64 energy and gap differences are reported on them."""
+    import paper_2311_01135_gb300 as g
+    g.build()
+    plan = [(g.RKS_MIXED, r, args.serve_n) for r in (100, 300, 1000, 5000)]
+    plan += [(g.RKS_FP64, r, max(40, args.serve_n // 10)) for r in (5, 20)]
+    first_mixed = None
+    for prec, rate, n in plan:
+        line, en = serve_run(g, prec, rate, n)
+        if prec == g.RKS_MIXED and first_mixed is None:
+            first_mixed = en
+        if prec == g.RKS_FP64 and first_mixed is not None:
+            k = min(len(en), len(first_mixed))
+            line["mixed_vs_fp64_max_abs_dE"] = max(abs(a[0] - b[0]) for a, b in zip(first_mixed[:k], en[:k]))
+            line["mixed_vs_fp64_max_abs_dgap"] = max(abs(a[1] - b[1]) for a, b in zip(first_mixed[:k], en[:k]))
+        print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------- GPU leg
 def main():
     ap = argparse.ArgumentParser()
@@ -227,10 +297,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="one step with per-stage times")
+    ap.add_argument("--serve", action="store_true", help="Poisson serving sweep instead of the batch step")
+    ap.add_argument("--serve-n", type=int, default=1500)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 1)
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return serve_main(args)
 
     import torch
     import paper_2311_01135_gb300 as g

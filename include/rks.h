@@ -123,6 +123,8 @@ typedef struct rks_result_t {
     double latency_s; /* submit -> done (serving API); batch wall time per molecule (batch API) */
     int32_t paper_converged; /* std of the last 5 energies < 0.01 Ha (the paper's flag) */
     int32_t pad;
+    double err_max;   /* max |X^T (F D S - S D F) X| of the last SCF iteration */
+    double de_last;   /* |E_k - E_(k-1)| of the last SCF iteration */
 } rks_result_t;
 
 /* Fill *o with the defaults listed above. */

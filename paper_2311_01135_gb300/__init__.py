@@ -21,6 +21,7 @@ RKS_PENDING, RKS_RUNNING, RKS_DONE, RKS_FAILED = 0, 1, 2, 3
 RKS_FP64, RKS_MIXED = 0, 1
 RKS_GUESS_SAD, RKS_GUESS_CORE = 0, 1
 RKS_XC_NOALLOC_MAX = 65536
+RKS_MAX_NBF = 96
 RKS_STATUS = {0: "ok", 1: "not_converged", 2: "nonfinite", 3: "s_ill", 4: "eigh"}
 (RKS_DUMP_PAIRS, RKS_DUMP_PAIR_Q, RKS_DUMP_ROW_OFF, RKS_DUMP_STORE, RKS_DUMP_S, RKS_DUMP_T, RKS_DUMP_V,
  RKS_DUMP_GRID, RKS_DUMP_J, RKS_DUMP_K, RKS_DUMP_VXC, RKS_DUMP_D, RKS_DUMP_F, RKS_DUMP_EPS, RKS_DUMP_X,
@@ -44,7 +45,8 @@ class rks_result_t(ctypes.Structure):
                 ("iters", ctypes.c_int32), ("e_total", ctypes.c_double), ("e_homo", ctypes.c_double),
                 ("e_lumo", ctypes.c_double), ("gap", ctypes.c_double), ("e_xc", ctypes.c_double),
                 ("e_nuc", ctypes.c_double), ("latency_s", ctypes.c_double),
-                ("paper_converged", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("paper_converged", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("err_max", ctypes.c_double), ("de_last", ctypes.c_double)]
 
 
 class rks_stage_time(ctypes.Structure):
@@ -230,7 +232,8 @@ class Context:
 def _res_dict(r, eps, D):
     return dict(status=RKS_STATUS.get(r.status, r.status), nbf=r.nbf, nocc=r.n_occ, iters=r.iters,
                 E=r.e_total, homo=r.e_homo, lumo=r.e_lumo, gap=r.gap, Exc=r.e_xc, Enuc=r.e_nuc,
-                latency_s=r.latency_s, paper_converged=bool(r.paper_converged), eps=eps, D=D)
+                latency_s=r.latency_s, paper_converged=bool(r.paper_converged), err_max=r.err_max,
+                de_last=r.de_last, eps=eps, D=D)
 
 
 class Batch:

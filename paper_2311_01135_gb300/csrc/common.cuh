@@ -6,6 +6,7 @@
 // every molecule of the batch (uneven basis sizes included).
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #define RKS_NBF_CAP 96      // largest nbf the kernels are compiled for
@@ -44,6 +45,7 @@ enum MatSlot {
 // Per-molecule FP64 scalars and small state (one struct per slot, device).
 struct MolState {
     double E, E_prev, Exc, Enuc, max_err, smin;
+    long long exc_fx;       // E_xc accumulator of the current grid pass, fixed point (RKS_FX_EXC)
     double eps_homo, eps_lumo;
     double B[RKS_DIIS_MAX * RKS_DIIS_MAX]; // DIIS Gram matrix of the stored error vectors
     double Ehist[RKS_NHIST];
@@ -60,6 +62,48 @@ struct MolState {
     long long n_elem;       // store elements written
     double eps[RKS_NBF_CAP];
 };
+
+// Fixed-point accumulator: the value times 2^40 in a 64-bit integer.  Integer
+// atomic adds are associative, so a sum does not depend on the order in which
+// threads, warps or blocks arrive: the mixed-precision iterations of a
+// molecule give the same bits alone or in any batch.  Range +-8.4e6, step
+// 9.1e-13; each FP32 contribution is rounded once to the step.
+struct Fx {
+    long long v;
+};
+#define RKS_FX_SCALE 1099511627776.0         // 2^40
+#define RKS_FX_EXC 17592186044416.0          // 2^44: E_xc partial sums (|E_xc| < 5e5 Ha)
+__device__ __forceinline__ void acc_add(float *p, float x) { atomicAdd(p, x); }
+__device__ __forceinline__ void acc_add(double *p, double x) { atomicAdd(p, x); }
+__device__ __forceinline__ void acc_add(Fx *p, float x) {
+    atomicAdd((unsigned long long *)&p->v, (unsigned long long)__float2ll_rn(x * (float)RKS_FX_SCALE));
+}
+__device__ __forceinline__ void acc_add(Fx *p, double x) {
+    atomicAdd((unsigned long long *)&p->v, (unsigned long long)__double2ll_rn(x * RKS_FX_SCALE));
+}
+__host__ __device__ __forceinline__ double acc_value(float x) { return (double)x; }
+__host__ __device__ __forceinline__ double acc_value(double x) { return x; }
+__host__ __device__ __forceinline__ double acc_value(Fx x) { return (double)x.v * (1.0 / RKS_FX_SCALE); }
+// merging a block's shared-memory partial sums into the global accumulators
+__device__ __forceinline__ bool acc_nonzero(double x) { return x != 0.0; }
+__device__ __forceinline__ bool acc_nonzero(Fx x) { return x.v != 0; }
+__device__ __forceinline__ void acc_merge(double *p, double x) { atomicAdd(p, x); }
+__device__ __forceinline__ void acc_merge(Fx *p, Fx x) {
+    atomicAdd((unsigned long long *)&p->v, (unsigned long long)x.v);
+}
+// E_xc partials (one per warp) into the molecule's fixed-point E_xc
+__device__ __forceinline__ void exc_add(long long *p, double x) {
+    atomicAdd((unsigned long long *)p, (unsigned long long)__double2ll_rn(x * RKS_FX_EXC));
+}
+
+// Molecules the tensor-core grid kernel takes (padded basis and shell count
+// of its shared-memory layout).  The choice is made per molecule, so a
+// molecule runs the same arithmetic whatever else is in its batch.
+#define RKS_TC_NPMAX 80
+#define RKS_TC_NSHMAX 60
+__host__ __device__ inline bool grid_tc_fits(int nbf, int nsh) {
+    return ((nbf + 15) & ~15) <= RKS_TC_NPMAX && nsh <= RKS_TC_NSHMAX;
+}
 
 // Device view of a batch (passed by value to kernels).
 struct DevBatch {
@@ -97,9 +141,10 @@ struct DevBatch {
     void *gx, *gy, *gz, *gw;
     // FP64 matrices
     double *mat;
-    // accumulators J', K', V' (3 * nbf^2 per molecule at acc0): FP32 for the
-    // mixed iterations, FP64 for the FP64 path and the final step
-    float *accf;
+    // accumulators J', K', V' (3 * nbf^2 per molecule at acc0): 64-bit fixed
+    // point for the mixed iterations (accx), FP64 for the FP64 path and the
+    // final step (accd); both views share one buffer, zeroed before each pass
+    struct Fx *accx;
     double *accd;
     // Boys tables
     const double *boys64;

@@ -278,7 +278,7 @@ struct rks_batch {
     size_t bytes = 0;               // device memory held
     int nmol = 0;
     int precision = 0;
-    int max_nbf = 0, max_nsh = 0, max_atoms = 0;
+    int max_nbf = 0, max_nsh = 0, max_atoms = 0, max_pair = 0;
     long long ncand = 0, nblk_total = 0;
     std::vector<HostMol> hm;
     std::vector<MolDesc> md;
@@ -373,7 +373,7 @@ static size_t mol_bytes(const rks_options &o, int na, const int32_t *Z) {
     if (o.precision == RKS_MIXED && o.fix_theta > 0) b += (size_t)npair * 45 * 8 + 6 * (RKS_FIX_CAP * 16 + 4);
     b += (size_t)((store_cap(ns, np) + 3) & ~3LL) * esz;
     b += (size_t)nblk * RKS_PTS_BLOCK * 4 * esz + (size_t)nblk * 4;
-    b += (size_t)nbf * nbf * (M_COUNT * 8 + 3 * 12);
+    b += (size_t)nbf * nbf * (M_COUNT * 8 + 3 * 8);
     return b;
 }
 
@@ -479,6 +479,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
         b->hm[m] = {na, nbf, nel / 2, nsh, npair_all, cap, npts};
         b->max_nbf = std::max(b->max_nbf, nbf);
         b->max_nsh = std::max(b->max_nsh, nsh);
+        b->max_pair = std::max(b->max_pair, npair_all);
         b->max_atoms = std::max(b->max_atoms, na);
         atom_off += na;
         sh_off += nsh;
@@ -508,7 +509,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     const size_t esz = o.precision ? sizeof(float) : sizeof(double);
     int rc = 0;
     MolDesc *dmol; MolState *dst; int *dZ, *dsa, *dsl, *dsao, *dcm, *dnp, *drnq; double *dax, *dsx, *dse, *dsc, *dcq, *dkq;
-    int2 *dcand, *dkp; long long *droff; void *store; void *gx, *gy, *gz, *gw; double *mat, *accd; float *accf;
+    int2 *dcand, *dkp; long long *droff; void *store; void *gx, *gy, *gz, *gw; double *mat, *accd;
     void *pairprim, *pairprim64 = nullptr;
     int4 *fixlist = nullptr;
     int *fixcount = nullptr;
@@ -525,7 +526,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
           (rc = dalloc(b, &fixlist, (size_t)nmol * 6 * RKS_FIX_CAP)) || (rc = dalloc(b, &fixcount, (size_t)nmol * 6)))) ||
         (rc = dalloc(b, (unsigned char **)&gx, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gy, pts_off * esz)) ||
         (rc = dalloc(b, (unsigned char **)&gz, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gw, pts_off * esz)) ||
-        (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) || (rc = dalloc(b, &accf, acc_off)) ||
+        (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) ||
         (rc = dalloc(b, &b->blk_mol, b->nblk_total)) || (rc = dalloc(b, &b->active_d, 1))) {
         rks_batch_destroy(b);
         return rc;
@@ -538,7 +539,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     d.fixlist = fixlist;
     d.fixcount = fixcount;
     d.fix_theta = o.fix_theta;
-    d.gx = gx; d.gy = gy; d.gz = gz; d.gw = gw; d.mat = mat; d.accd = accd; d.accf = accf;
+    d.gx = gx; d.gy = gy; d.gz = gz; d.gw = gw; d.mat = mat; d.accd = accd; d.accx = (Fx *)accd;  // one buffer, two views
     cudaStream_t s = b->stream;
 #define UP(dst_, src_)                                                                                      \
     if (!(src_).empty()) {                                                                                  \
@@ -615,11 +616,14 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
     const DevBatch &d = b->d;
     long long acc_elems = 0;
     for (auto &m : b->md) acc_elems += 3LL * m.nbf * m.nbf;
-    if (acc_fp64 || b->precision == 0) CUDA_OK(cudaMemsetAsync(d.accd, 0, sizeof(double) * acc_elems, s));
-    else CUDA_OK(cudaMemsetAsync(d.accf, 0, sizeof(float) * acc_elems, s));
+    CUDA_OK(cudaMemsetAsync(d.accd, 0, sizeof(double) * acc_elems, s));  // zero in both views
     launch_reset_exc(d, s);
     const int nchunk_jk = 8;
-    { StageScope sc(c, s, acc_fp64 ? "jk_final" : "jk", 0); launch_jk(d, nchunk_jk, acc_fp64, mode, b->max_nbf, s); }
+    {
+        StageScope sc(c, s, acc_fp64 ? "jk_final" : "jk", 0);
+        if (launch_jk(d, nchunk_jk, acc_fp64, mode, b->max_nbf, b->max_pair, s))
+            return fail(RKS_EINVAL, "basis too large for the J/K kernel's shared memory");
+    }
     if (acc_fp64 && b->precision == RKS_MIXED && d.fixlist) {
         StageScope sc(c, s, "jk_fp64_fix", 0);
         launch_jk_fix(d, s);
@@ -627,16 +631,26 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
     if (d.xc) {
         // Tensor-core accumulation truncates (round toward zero): fine for the
         // iterations, but the final step's energy uses the CUDA-core kernel,
-        // whose FP32 sums round to nearest and carry no bias.
-        if (!acc_fp64 && b->precision == RKS_MIXED && c->opt.grid_tc &&
-            grid_xc_tc_supported(b->max_nbf, b->max_nsh)) {
-            const int nchunk_tc = 4;
-            StageScope sc(c, s, acc_fp64 ? "grid_xc_tc_final" : "grid_xc_tc", 0);
-            launch_grid_xc_tc(d, nchunk_tc, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
-        } else {
+        // whose FP32 sums round to nearest and carry no bias.  The kernel is
+        // chosen per molecule (grid_tc_fits), never per batch.
+        const bool tc = !acc_fp64 && b->precision == RKS_MIXED && c->opt.grid_tc;
+        bool need_cc = !tc;
+        if (tc) {
+            bool any_tc = false;
+            for (auto &m : b->md) {
+                if (grid_tc_fits(m.nbf, m.nsh)) any_tc = true;
+                else need_cc = true;
+            }
+            if (any_tc) {
+                const int nchunk_tc = 4;
+                StageScope sc(c, s, "grid_xc_tc", 0);
+                launch_grid_xc_tc(d, nchunk_tc, 0, mode, b->max_nbf, b->max_nsh, s);
+            }
+        }
+        if (need_cc) {
             const int nchunk_gx = 16;
             StageScope sc(c, s, acc_fp64 ? "grid_xc_final" : "grid_xc", 0);
-            launch_grid_xc(d, nchunk_gx, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
+            launch_grid_xc(d, nchunk_gx, acc_fp64, mode, tc ? 1 : 0, b->max_nbf, b->max_nsh, s);
         }
     }
     return check_launch("fock pass");
@@ -797,6 +811,8 @@ extern "C" int rks_batch_result(rks_batch *b, int32_t m, rks_result_t *out, doub
     out->e_nuc = st.Enuc;
     out->latency_s = b->wall_s;
     out->paper_converged = paper_std(st) < 0.01;
+    out->err_max = st.max_err;
+    out->de_last = st.iter >= 2 ? fabs(st.Ehist[(st.iter - 1) % RKS_NHIST] - st.Ehist[(st.iter - 2) % RKS_NHIST]) : 0.0;
     if (eps_out) memcpy(eps_out, st.eps, sizeof(double) * md.nbf);
     if (D_out) {
         long long nn = (long long)md.nbf * md.nbf;

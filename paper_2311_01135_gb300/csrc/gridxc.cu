@@ -19,11 +19,12 @@
 #include "boys.cuh"
 
 template <typename T, typename TA, int BP, int TILE>
-__global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk, int mode) {
+__global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk, int mode, int skip_tc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = blockIdx.y, chunk = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
+    if (skip_tc && grid_tc_fits(b.mol[m].nbf, b.mol[m].nsh)) return;  // done by the tensor-core kernel
     const int n = md.nbf, nsh = md.nsh;
     const int XS = n | 1;  // odd row stride of X (bank-conflict free both ways)
     T *Ds = (T *)smem_raw;                 // [n][n]
@@ -182,34 +183,36 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
         __syncthreads();
     }
     // ---- flush V' and E_xc
-    TA *gV;
-    if constexpr (sizeof(TA) == 8) gV = (TA *)(b.accd + md.acc0) + 2 * n * n;
-    else gV = (TA *)(b.accf + md.acc0) + 2 * n * n;
+    // FP64 accumulators for the FP64 path and the final step, fixed point for the mixed iterations
+    using TG = std::conditional_t<sizeof(TA) == 8, double, Fx>;
+    TG *gV;
+    if constexpr (sizeof(TA) == 8) gV = b.accd + md.acc0 + 2 * n * n;
+    else gV = b.accx + md.acc0 + 2 * n * n;
 #pragma unroll
     for (int a = 0; a < TILE; a++)
 #pragma unroll
         for (int c = 0; c < TILE; c++) {
             const int mu = ti + 16 * a, nu = tj + 16 * c;
-            if (mu < n && nu < n && acc[a][c] != (TA)0) atomicAdd(&gV[mu * n + nu], acc[a][c]);
+            if (mu < n && nu < n && acc[a][c] != (TA)0) acc_add(&gV[mu * n + nu], acc[a][c]);
         }
     for (int o = 16; o > 0; o >>= 1) exc += __shfl_xor_sync(0xffffffffu, exc, o);
-    if ((t & 31) == 0 && exc != 0.0) atomicAdd(&b.st[m].Exc, exc);
+    if ((t & 31) == 0 && exc != 0.0) exc_add(&b.st[m].exc_fx, exc);
 }
 
 template <typename T, typename TA, int BP, int TILE>
-static void launch_gx(const DevBatch &b, int nchunk, int mode, int max_nbf, int max_nsh, cudaStream_t s) {
+static void launch_gx(const DevBatch &b, int nchunk, int mode, int skip_tc, int max_nbf, int max_nsh, cudaStream_t s) {
     const int n = max_nbf, XS = n | 1;
     size_t sm = sizeof(T) * ((size_t)n * n + 4ull * n * BP + (size_t)BP * XS + 8ull * BP + 18ull * max_nsh) +
                 sizeof(int) * 2ull * max_nsh + 64;
     cudaFuncSetAttribute(grid_xc_kernel<T, TA, BP, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    grid_xc_kernel<T, TA, BP, TILE><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode);
+    grid_xc_kernel<T, TA, BP, TILE><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode, skip_tc);
 }
 
-void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
+void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int skip_tc, int max_nbf, int max_nsh,
                     cudaStream_t s) {
-    if (b.precision == 0) launch_gx<double, double, 32, 6>(b, nchunk, mode, max_nbf, max_nsh, s);
-    else if (acc_fp64) launch_gx<float, double, 64, 6>(b, nchunk, mode, max_nbf, max_nsh, s);
-    else launch_gx<float, float, 64, 6>(b, nchunk, mode, max_nbf, max_nsh, s);
+    if (b.precision == 0) launch_gx<double, double, 32, 6>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
+    else if (acc_fp64) launch_gx<float, double, 64, 6>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
+    else launch_gx<float, float, 64, 6>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
 }
 
 // --------------------------------------------------------- unit entry

@@ -30,8 +30,8 @@
 #include "xc.cuh"
 
 #define TC_BP 128
-#define TC_NPMAX 80     // padded basis size this kernel handles
-#define TC_NSHMAX 60    // shells this kernel handles
+#define TC_NPMAX RKS_TC_NPMAX   // padded basis size this kernel handles
+#define TC_NSHMAX RKS_TC_NSHMAX // shells this kernel handles
 #define TC_TMEM_COLS 256
 #define TC_SPIN_LIMIT 50000000
 
@@ -148,12 +148,12 @@ __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
     const uint32_t w2 = 8u * opsz;
     s.set1 = 4u * opsz;
     o += (w1 > w2 ? w1 : w2);
-    s.pts = o; o += 4 * TC_BP * 4;          // point offsets x, y, z and weight
+    s.pts = o; o += 4 * TC_BP * 4;          // per point: offset x, y, z and weight (float4)
     s.part = o; o += 4 * 4 * TC_BP * 4;     // rho, grad rho partials per AO quarter
     s.xcp = o; o += 3 * 2 * TC_BP * 4;      // v_rho, v_sigma per XC part
     s.grd = o; o += 3 * TC_BP * 4;          // grad rho
     s.shx = o; o += (uint32_t)nsh * TC_SHX * 4;
-    s.shf = o; o += (uint32_t)nsh * 8 * 4;  // per shell: R_owner0 - C (3), R_owner1 - C (3), pad
+    s.shf = o; o += (uint32_t)nsh * 8 * 4;  // per shell: R_owner0 - C (3), pad, R_owner1 - C (3), pad
     s.aoc = o; o += (uint32_t)np * 4;       // per AO: shell * 4 + component + 1, -1 if zero in this block
     s.rset = o; o += (uint32_t)nsh * 4;     // radial sets: lead shell | partner << 8 (255: none)
     s.total = o;
@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     const int m = blockIdx.y, chunk = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
+    if (!grid_tc_fits(md.nbf, md.nsh)) return;  // the CUDA-core kernel takes this molecule
     const int n = md.nbf, nsh = md.nsh;
     const int np = (n + 15) & ~15;
     const int nq = np / 4;  // AO columns per thread quarter (multiple of 4)
@@ -199,7 +200,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     unsigned char *sm = smem;
     float *Rg = (float *)(sm + L.R_g), *Rgp = (float *)(sm + L.R_gp);
-    float *pt = (float *)(sm + L.pts), *part = (float *)(sm + L.part);
+    float4 *pt4 = (float4 *)(sm + L.pts);
+    float *part = (float *)(sm + L.part);
     float *xcp = (float *)(sm + L.xcp), *grd = (float *)(sm + L.grd);
     float *shx = (float *)(sm + L.shx), *shf = (float *)(sm + L.shf);
     int *shxi = (int *)shx;
@@ -301,10 +303,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
         if (t < TC_BP) {
             const int h = min((p0 + t) / npa, md.natom - 1) - own0;
             owner_h[t] = h;
-            pt[t] = nx;
-            pt[TC_BP + t] = ny;
-            pt[2 * TC_BP + t] = nz;
-            pt[3 * TC_BP + t] = nw;
+            pt4[t] = make_float4(nx, ny, nz, nw);
             const unsigned rb = __float_as_uint(sqrtf(nx * nx + ny * ny + nz * nz));  // r >= 0: bits order as floats
             const unsigned lo0 = __reduce_min_sync(0xffffffffu, h == 0 ? rb : 0x7f800000u);
             const unsigned hi0 = __reduce_max_sync(0xffffffffu, h == 0 ? rb : 0u);
@@ -326,9 +325,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                 const int hh = i / nsh, s = i % nsh;
                 const int A = min(own0 + hh, md.natom - 1);
                 const double *ra = b.axyz + (md.atom0 + A) * 3, *rc = b.sh_xyz + (md.sh0 + s) * 3;
-                shf[s * 8 + hh * 3 + 0] = (float)(ra[0] - rc[0]);
-                shf[s * 8 + hh * 3 + 1] = (float)(ra[1] - rc[1]);
-                shf[s * 8 + hh * 3 + 2] = (float)(ra[2] - rc[2]);
+                *(float4 *)(shf + s * 8 + hh * 4) =
+                    make_float4((float)(ra[0] - rc[0]), (float)(ra[1] - rc[1]), (float)(ra[2] - rc[2]), 0.f);
             }
             shf_owner = own0;
         }
@@ -341,7 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
             for (int h = 0; h < 2; h++) {
                 const float lo = __uint_as_float(blk_r[2 * h]), hi = __uint_as_float(blk_r[2 * h + 1]);
                 if (lo > hi) continue;  // no point of this owner in the block
-                const float *dl = shf + s * 8 + h * 3;
+                const float *dl = shf + s * 8 + h * 4;
                 const float d = sqrtf(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
                 rmin = fminf(rmin, shell_rmin(d, lo, hi));
             }
@@ -381,38 +379,45 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
             const int s1 = rset[k] & 255, s2 = rset[k] >> 8;
             const bool on1 = sig[s1], on2 = s2 != 255 && sig[s2];
             if (!on1 && !on2) continue;
-            const float *dl = shf + s1 * 8 + owner_h[p] * 3;
-            const float dx = dl[0] + pt[p], dy = dl[1] + pt[TC_BP + p], dz = dl[2] + pt[2 * TC_BP + p];
+            const float4 dl = *(const float4 *)(shf + s1 * 8 + owner_h[p] * 4);
+            const float4 q4 = pt4[p];
+            const float dx = dl.x + q4.x, dy = dl.y + q4.y, dz = dl.z + q4.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
-            const float *x1 = shx + s1 * TC_SHX;
-            const float e0 = __expf(-x1[0] * r2), e1 = __expf(-x1[1] * r2), e2 = __expf(-x1[2] * r2);
+            const float4 xa = *(const float4 *)(shx + s1 * TC_SHX), xb = *(const float4 *)(shx + s1 * TC_SHX + 4);
+            const float xc9 = shx[s1 * TC_SHX + 8];
+            const float e0 = __expf(-xa.x * r2), e1 = __expf(-xa.y * r2), e2 = __expf(-xa.z * r2);
             if (on1) {
-                Rg[s1 * TC_BP + p] = x1[3] * e0 + x1[4] * e1 + x1[5] * e2;
-                Rgp[s1 * TC_BP + p] = x1[6] * e0 + x1[7] * e1 + x1[8] * e2;
+                Rg[s1 * TC_BP + p] = xa.w * e0 + xb.x * e1 + xb.y * e2;
+                Rgp[s1 * TC_BP + p] = xb.z * e0 + xb.w * e1 + xc9 * e2;
             }
             if (on2) {
-                const float *x2 = shx + s2 * TC_SHX;
-                Rg[s2 * TC_BP + p] = x2[3] * e0 + x2[4] * e1 + x2[5] * e2;
-                Rgp[s2 * TC_BP + p] = x2[6] * e0 + x2[7] * e1 + x2[8] * e2;
+                const float4 ya = *(const float4 *)(shx + s2 * TC_SHX), yb = *(const float4 *)(shx + s2 * TC_SHX + 4);
+                const float yc9 = shx[s2 * TC_SHX + 8];
+                Rg[s2 * TC_BP + p] = ya.w * e0 + yb.x * e1 + yb.y * e2;
+                Rgp[s2 * TC_BP + p] = yb.z * e0 + yb.w * e1 + yc9 * e2;
             }
         }
         __syncthreads();
         // ---- B: Phi (points x AOs) for GEMM1; thread = (point, AO quarter)
         const int p = t & (TC_BP - 1);
-        const float px = pt[p], py = pt[TC_BP + p], pz = pt[2 * TC_BP + p];
+        const float4 pq4 = pt4[p];
+        const float px = pq4.x, py = pq4.y, pz = pq4.z;
         const int hp = owner_h[p];
         {
             const uint32_t phi_hi = L.work, phi_lo = L.work + (uint32_t)TC_BP * np * 4;
             for (int kc = g4 * (nq / 4); kc < (g4 + 1) * (nq / 4); kc++) {
                 float v[4];
+                const int4 code4 = *(const int4 *)(aoc + kc * 4);
+                const int codes[4] = {code4.x, code4.y, code4.z, code4.w};
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
-                    const int code = aoc[kc * 4 + j];
+                    const int code = codes[j];
                     float val = 0.f;
                     if (code >= 0) {
                         const int s = code >> 2, c = (code & 3) - 1;
                         const float gg = Rg[s * TC_BP + p];
-                        val = (c < 0) ? gg : (shf[s * 8 + hp * 3 + c] + pt[c * TC_BP + p]) * gg;
+                        const float pc = c == 0 ? px : (c == 1 ? py : pz);
+                        val = (c < 0) ? gg : (shf[s * 8 + hp * 4 + c] + pc) * gg;
                     }
                     v[j] = val;
                 }
@@ -453,9 +458,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
             for (int cc = g4 * nq; cc < (g4 + 1) * nq; cc += 4) {
                 float tv[4];
                 ld4(tT + ((uint32_t)(q * 32) << 16) + cc, tv);
+                const int4 code4 = *(const int4 *)(aoc + cc);
+                const int codes[4] = {code4.x, code4.y, code4.z, code4.w};
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
-                    const int code = aoc[cc + j];
+                    const int code = codes[j];
                     if (code < 0) continue;
                     const int s = code >> 2, c = (code & 3) - 1;
                     if (s != cur) {
@@ -468,8 +475,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                         cur = s;
                         cg = Rg[s * TC_BP + p];
                         cgp = Rgp[s * TC_BP + p];
-                        const float *dl = shf + s * 8 + hp * 3;
-                        dx = dl[0] + px; dy = dl[1] + py; dz = dl[2] + pz;
+                        const float4 dl = *(const float4 *)(shf + s * 8 + hp * 4);
+                        dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
                         u = tx = ty = tz = 0.f;
                     }
                     if (c < 0) {
@@ -507,7 +514,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                     gz += part[(gq * 4 + 3) * TC_BP + p];
                 }
                 gx *= 2.f; gy *= 2.f; gz *= 2.f;
-                const float w = pt[3 * TC_BP + p];
+                const float w = pq4.w;
                 float e = 0.f, vr = 0.f, vs = 0.f;
                 if (w != 0.f) xc::b3lyp_part<float>(gi, r, gx * gx + gy * gy + gz * gz, e, vr, vs);
                 exc += (double)w * (double)e;
@@ -539,9 +546,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                     if (k >= 2) ok = tc::wait(&bar2[set], ph2[set]);
                     if (!ok) s_fail = 1;  // benign race: every writer stores 1
                     const int pl = lane, pp = k * TC_SLICE + pl;
-                    const float *dlb = shf + owner_h[pp] * 3;
-                    const float ox = pt[pp], oy = pt[TC_BP + pp], oz = pt[2 * TC_BP + pp];
-                    const float w = pt[3 * TC_BP + pp];
+                    const float *dlb = shf + owner_h[pp] * 4;
+                    const float4 o4 = pt4[pp];
+                    const float ox = o4.x, oy = o4.y, oz = o4.z, w = o4.w;
                     const float vr = xcp[pp] + xcp[2 * TC_BP + pp] + xcp[4 * TC_BP + pp];
                     const float vs2 = 2.f * w * (xcp[TC_BP + pp] + xcp[5 * TC_BP + pp]);
                     const float a = 0.5f * w * vr;
@@ -566,8 +573,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                             continue;
                         }
                         const float gg = Rg[s * TC_BP + pp], gp = Rgp[s * TC_BP + pp];
-                        const float *dl = dlb + s * 8;
-                        const float dx = dl[0] + ox, dy = dl[1] + oy, dz = dl[2] + oz;
+                        const float4 dl = *(const float4 *)(dlb + s * 8);
+                        const float dx = dl.x + ox, dy = dl.y + oy, dz = dl.z + oz;
                         const float basev = a * gg + gp * (bx * dx + by * dy + bz * dz);
                         if (!l) {
                             const float fh = tc::tf32_hi(gg), xh = tc::tf32_hi(basev);
@@ -646,17 +653,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     // ---- flush V' (row mu = this thread's lane row, columns of its quarter) and E_xc
     if (!s_fail && any_block) {
         const int mu = q * 32 + lane;
-        TA *gV;
-        if constexpr (sizeof(TA) == 8) gV = (TA *)(b.accd + md.acc0) + 2 * n * n;
-        else gV = (TA *)(b.accf + md.acc0) + 2 * n * n;
+        using TG = std::conditional_t<sizeof(TA) == 8, double, Fx>;
+        TG *gV;
+        if constexpr (sizeof(TA) == 8) gV = b.accd + md.acc0 + 2 * n * n;
+        else gV = b.accx + md.acc0 + 2 * n * n;
 #pragma unroll
         for (int j = 0; j < TC_NPMAX / 4; j++) {
             const int nu = g4 * nq + j;
-            if (j < nq && mu < n && nu < n && vacc[j] != 0.f) atomicAdd(&gV[mu * n + nu], (TA)vacc[j]);
+            if (j < nq && mu < n && nu < n && vacc[j] != 0.f) acc_add(&gV[mu * n + nu], (TA)vacc[j]);
         }
     }
     for (int o = 16; o > 0; o >>= 1) exc += __shfl_xor_sync(0xffffffffu, exc, o);
-    if (lane == 0 && exc != 0.0) atomicAdd(&b.st[m].Exc, exc);
+    if (lane == 0 && exc != 0.0) exc_add(&b.st[m].exc_fx, exc);
     if (s_fail && t == 0) {
         atomicOr(&b.st[m].err_flag, 4);
         // give in-flight MMAs a bounded chance to drain before freeing tensor memory
@@ -670,14 +678,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
 }
 
-bool grid_xc_tc_supported(int max_nbf, int max_nsh) {
-    return ((max_nbf + 15) & ~15) <= TC_NPMAX && max_nsh <= TC_NSHMAX;
-}
 
 void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
                        cudaStream_t s) {
-    const int np = (max_nbf + 15) & ~15;
-    const size_t sm = tc_layout(np, max_nsh).total + 128;
+    const int np = min((max_nbf + 15) & ~15, TC_NPMAX);  // larger molecules return at once
+    const size_t sm = tc_layout(np, min(max_nsh, TC_NSHMAX)).total + 128;
     if (acc_fp64) {
         cudaFuncSetAttribute(grid_xc_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         grid_xc_tc_kernel<double><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);

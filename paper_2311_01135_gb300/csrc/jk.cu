@@ -24,11 +24,12 @@
 
 #define TAU_SCHWARZ 1e-12
 
-template <typename TA> __device__ __forceinline__ void sh_add(TA *p, TA v) { atomicAdd(p, v); }
-
-template <typename TS, typename TA, int LA, int LB, int LC, int LD>
+// TA: arithmetic type of the contributions; TACC: accumulator (double, or
+// the fixed-point Fx of the mixed iterations, whose sums do not depend on the
+// order of the atomic adds).
+template <typename TS, typename TA, typename TACC, int LA, int LB, int LC, int LD>
 __device__ __forceinline__ void jk_block(const TS *__restrict__ v, TA scale, int a0, int b0, int c0, int d0,
-                                         const TA *Ds, TA *Js, TA *Ks, int n, TA *jpq) {
+                                         const TA *Ds, TACC *Js, TACC *Ks, int n, TA *jpq) {
     constexpr int na = LA ? 3 : 1, nb = LB ? 3 : 1, nc = LC ? 3 : 1, nd = LD ? 3 : 1;
     TA Drs[nc][nd], Dpq[na][nb], Dqs[nb][nd], Dps[na][nd], Dqr[nb][nc], Dpr[na][nc];
 #pragma unroll
@@ -76,84 +77,143 @@ __device__ __forceinline__ void jk_block(const TS *__restrict__ v, TA scale, int
 #pragma unroll
     for (int k = 0; k < nc; k++)
 #pragma unroll
-        for (int l = 0; l < nd; l++) sh_add(&Js[(c0 + k) * n + d0 + l], (TA)2 * jrs[k][l]);
+        for (int l = 0; l < nd; l++) acc_add(&Js[(c0 + k) * n + d0 + l], (TA)2 * jrs[k][l]);
 #pragma unroll
     for (int i = 0; i < na; i++)
 #pragma unroll
-        for (int k = 0; k < nc; k++) sh_add(&Ks[(a0 + i) * n + c0 + k], kpr[i][k]);
+        for (int k = 0; k < nc; k++) acc_add(&Ks[(a0 + i) * n + c0 + k], kpr[i][k]);
 #pragma unroll
     for (int j = 0; j < nb; j++)
 #pragma unroll
-        for (int k = 0; k < nc; k++) sh_add(&Ks[(b0 + j) * n + c0 + k], kqr[j][k]);
+        for (int k = 0; k < nc; k++) acc_add(&Ks[(b0 + j) * n + c0 + k], kqr[j][k]);
 #pragma unroll
     for (int i = 0; i < na; i++)
 #pragma unroll
-        for (int l = 0; l < nd; l++) sh_add(&Ks[(a0 + i) * n + d0 + l], kps[i][l]);
+        for (int l = 0; l < nd; l++) acc_add(&Ks[(a0 + i) * n + d0 + l], kps[i][l]);
 #pragma unroll
     for (int j = 0; j < nb; j++)
 #pragma unroll
-        for (int l = 0; l < nd; l++) sh_add(&Ks[(b0 + j) * n + d0 + l], kqs[j][l]);
+        for (int l = 0; l < nd; l++) acc_add(&Ks[(b0 + j) * n + d0 + l], kqs[j][l]);
 }
 
-// Elements of the store staged per warp and window (coalesced loads).
-template <typename TS> struct JkStage { static constexpr int CH = sizeof(TS) == 4 ? 1024 : 512; };
-#define JK_WARPS 8
+// Elements of the store staged per warp and window (coalesced loads): up to
+// 512 (FP32 store) or 256 (FP64), fewer when the molecule's D/J/K leave less
+// room; a window must hold the largest block (81 elements).  16 warps for
+// FP32 arithmetic, 8 for FP64 (whose blocks need twice the registers).
+#define JK_WARPS_MAX 16
+#define JK_SMEM_LIMIT 232448
+
+// Per kept pair s of the molecule, in shared memory: its Schwarz factor and
+// a packed descriptor: AO start of R (bits 0-6), of S (7-13), l_R (14),
+// l_S (15), R == S (16).
+__device__ __forceinline__ uint32_t jk_pinfo(int c0, int d0, int lR, int lS, int same) {
+    return (uint32_t)c0 | ((uint32_t)d0 << 7) | ((uint32_t)lR << 14) | ((uint32_t)lS << 15) | ((uint32_t)same << 16);
+}
+
+// Shared-memory plan: D (n^2 TA), J' and K' (n^2 TACC each), the pair table
+// (when it fits) and the per-warp stages; 16 warps, or 8 when D/J/K are large.
+struct JkPlan {
+    int warps, ch, pairs_in_smem;
+    size_t bytes;
+};
+template <typename TS, typename TA, typename TACC> static JkPlan jk_plan(int n, int npair) {
+    const size_t mats = (((size_t)n * n * sizeof(TA) + 15) & ~(size_t)15) + 2 * (size_t)n * n * sizeof(TACC);
+    const size_t table = (size_t)npair * sizeof(double) + (((size_t)npair * sizeof(uint32_t) + 15) & ~(size_t)15);
+    const int ch_max = sizeof(TS) == 4 ? 512 : 256;
+    JkPlan p;
+    for (p.warps = sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS_MAX; p.warps >= 8; p.warps /= 2)
+        for (p.pairs_in_smem = 1; p.pairs_in_smem >= 0; p.pairs_in_smem--) {
+            const size_t fixed = mats + (p.pairs_in_smem ? table : 0);
+            if (fixed >= JK_SMEM_LIMIT) continue;
+            const long long ch = (long long)((JK_SMEM_LIMIT - fixed) / ((size_t)p.warps * sizeof(TS)));
+            if (ch < 96) continue;
+            p.ch = (int)(ch < ch_max ? ch : ch_max);
+            p.bytes = fixed + (size_t)p.warps * p.ch * sizeof(TS);
+            return p;
+        }
+    p.warps = 0;  // does not fit: the caller reports it
+    p.ch = 0;
+    p.pairs_in_smem = 0;
+    p.bytes = 0;
+    return p;
+}
 
 // grid (nchunk, nmol); mode 0: only molecules still iterating, 1: all.
 //
 // A warp walks one row pq; lane L takes ket rs = s0 + L of a 32-ket chunk.
-// The row's kept blocks are contiguous in the store, so the warp first copies
-// a window of them into its shared-memory stage with coalesced loads (lane e
-// reads element e, e + 32, ...), then every lane reads its own block from
-// shared memory (block sizes 1, 3, 9, 27, 81 are odd: no bank conflicts).  A
-// chunk whose blocks exceed one window is done in several windows, each
-// holding whole blocks.
-template <typename TS, typename TA>
-__global__ void __launch_bounds__(JK_WARPS * 32) jk_kernel(DevBatch b, int nchunk, int mode) {
+// The pair table (Schwarz factors, AO starts, angular momenta) is copied to
+// shared memory once per block.  The row's kept blocks are contiguous in the
+// store, so the warp copies a window of them into its shared-memory stage
+// with coalesced loads (lane e reads element e, e + 32, ...), then every lane
+// reads its own block from shared memory (block sizes 1, 3, 9, 27, 81 are
+// odd: no bank conflicts).  A chunk whose blocks exceed one window is done in
+// several windows, each holding whole blocks.
+template <typename TS, typename TA, typename TACC>
+__global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS_MAX) * 32)
+    jk_kernel(DevBatch b, int nchunk, int mode, int max_pair, int CH, int pairs_in_smem) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int CH = JkStage<TS>::CH;
     const int m = blockIdx.y, c = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
     const int n = md.nbf, nn = n * n;
+    const int npair = b.npair[m];
     TA *Ds = (TA *)smem_raw;
-    TA *Js = Ds + nn;
-    TA *Ks = Js + nn;
+    size_t o = ((size_t)nn * sizeof(TA) + 15) & ~(size_t)15;
+    TACC *Js = (TACC *)(smem_raw + o);
+    TACC *Ks = Js + nn;
+    o += 2 * (size_t)nn * sizeof(TACC);
+    double *kq = (double *)(smem_raw + o);
+    uint32_t *pinfo = nullptr;
+    if (pairs_in_smem) {
+        o += (size_t)max_pair * sizeof(double);
+        pinfo = (uint32_t *)(smem_raw + o);
+        o += ((size_t)max_pair * sizeof(uint32_t) + 15) & ~(size_t)15;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    TS *stg = (TS *)(smem_raw + (((size_t)3 * nn * sizeof(TA) + 15) & ~(size_t)15)) + (size_t)warp * CH;
+    TS *stg = (TS *)(smem_raw + o) + (size_t)warp * CH;
     const double *D = b.mat + md.mat0 + (long long)M_D * nn;
     for (int i = threadIdx.x; i < nn; i += blockDim.x) {
         Ds[i] = (TA)D[i];
-        Js[i] = (TA)0;
-        Ks[i] = (TA)0;
+        Js[i] = TACC{};
+        Ks[i] = TACC{};
+    }
+    auto pair_of = [&](int i) -> uint32_t {
+        const int2 rs = b.kpair[md.pair0 + i];
+        const int R = md.sh0 + rs.x, S = md.sh0 + rs.y;
+        return jk_pinfo(b.sh_ao0[R], b.sh_ao0[S], b.sh_l[R], b.sh_l[S], R == S);
+    };
+    if (pairs_in_smem) {
+        for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+            kq[i] = b.kq[md.pair0 + i];
+            pinfo[i] = pair_of(i);
+        }
+    } else {
+        kq = b.kq + md.pair0;  // tables stay in global memory
     }
     __syncthreads();
-    const int npair = b.npair[m];
     const TS *store = (const TS *)b.store + md.eri0;
     for (int r = c + nchunk * warp; r < npair; r += nchunk * nwarp) {
-        const int2 pq = b.kpair[md.pair0 + r];
-        const double qpq = b.kq[md.pair0 + r];
-        const int P = md.sh0 + pq.x, Q = md.sh0 + pq.y;
-        const int lP = b.sh_l[P], lQ = b.sh_l[Q];
-        const int a0 = b.sh_ao0[P], b0 = b.sh_ao0[Q];
+        const uint32_t bi = pairs_in_smem ? pinfo[r] : pair_of(r);
+        const double qpq = kq[r];
+        const int a0 = bi & 127, b0 = (bi >> 7) & 127, lP = (bi >> 14) & 1, lQ = (bi >> 15) & 1;
+        const TA bra_scale = (bi >> 16) & 1 ? (TA)0.5 : (TA)1;
         const int npq = (lP ? 3 : 1) * (lQ ? 3 : 1);
         long long base = b.row_off[md.pair0 + m + r];
         TA jpq[9] = {};
         for (int s0 = 0; s0 <= r; s0 += 32) {
             const int s = s0 + lane;
             bool keep = false;
-            int R = 0, S = 0, nel = 0;
-            if (s <= r && qpq * b.kq[md.pair0 + s] >= TAU_SCHWARZ) {
-                const int2 rs = b.kpair[md.pair0 + s];
-                R = md.sh0 + rs.x;
-                S = md.sh0 + rs.y;
+            uint32_t ki = 0;
+            int nel = 0;
+            if (s <= r && qpq * kq[s] >= TAU_SCHWARZ) {
+                ki = pairs_in_smem ? pinfo[s] : pair_of(s);
                 keep = true;
-                nel = npq * (b.sh_l[R] ? 3 : 1) * (b.sh_l[S] ? 3 : 1);
+                nel = npq * ((ki >> 14) & 1 ? 3 : 1) * ((ki >> 15) & 1 ? 3 : 1);
             }
             int x = nel;  // inclusive prefix sum of block sizes over the chunk
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o2);
+                if (lane >= o2) x += y;
             }
             const int tot = __shfl_sync(0xffffffffu, x, 31);
             const int start = x - nel;  // this lane's block, relative to the chunk
@@ -162,25 +222,24 @@ __global__ void __launch_bounds__(JK_WARPS * 32) jk_kernel(DevBatch b, int nchun
                 const int w0 = __shfl_sync(0xffffffffu, start, first);
                 const bool mine = lane >= first && x <= w0 + CH;
                 int wend = mine ? x : w0;
-                for (int o = 16; o > 0; o >>= 1) wend = max(wend, __shfl_xor_sync(0xffffffffu, wend, o));
+                for (int o2 = 16; o2 > 0; o2 >>= 1) wend = max(wend, __shfl_xor_sync(0xffffffffu, wend, o2));
                 const TS *src = store + base + w0;
                 for (int e = lane; e < wend - w0; e += 32) stg[e] = src[e];
                 __syncwarp();
                 if (mine && keep) {
                     const TS *v = stg + (start - w0);
-                    TA scale = (TA)1;
-                    if (P == Q) scale *= (TA)0.5;
-                    if (R == S) scale *= (TA)0.5;
+                    TA scale = bra_scale;
+                    if ((ki >> 16) & 1) scale *= (TA)0.5;
                     if (s == r) scale *= (TA)0.5;
-                    const int c0 = b.sh_ao0[R], d0 = b.sh_ao0[S];
-                    const int cls = (lP << 3) | (lQ << 2) | (b.sh_l[R] << 1) | b.sh_l[S];
+                    const int c0 = ki & 127, d0 = (ki >> 7) & 127;
+                    const int cls = (lP << 3) | (lQ << 2) | (((ki >> 14) & 1) << 1) | ((ki >> 15) & 1);
                     switch (cls) {
-                    case 0x0: jk_block<TS, TA, 0, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    case 0x8: jk_block<TS, TA, 1, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    case 0xA: jk_block<TS, TA, 1, 0, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    case 0xC: jk_block<TS, TA, 1, 1, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    case 0xE: jk_block<TS, TA, 1, 1, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    case 0xF: jk_block<TS, TA, 1, 1, 1, 1>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0x0: jk_block<TS, TA, TACC, 0, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0x8: jk_block<TS, TA, TACC, 1, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0xA: jk_block<TS, TA, TACC, 1, 0, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0xC: jk_block<TS, TA, TACC, 1, 1, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0xE: jk_block<TS, TA, TACC, 1, 1, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                    case 0xF: jk_block<TS, TA, TACC, 1, 1, 1, 1>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
                     default: break;
                     }
                 }
@@ -194,7 +253,7 @@ __global__ void __launch_bounds__(JK_WARPS * 32) jk_kernel(DevBatch b, int nchun
 #pragma unroll
         for (int k = 0; k < 9; k++) {
             TA t = jpq[k];
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            for (int o2 = 16; o2 > 0; o2 >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o2);
             jpq[k] = t;
         }
         if (lane < npq) {
@@ -203,44 +262,35 @@ __global__ void __launch_bounds__(JK_WARPS * 32) jk_kernel(DevBatch b, int nchun
 #pragma unroll
             for (int k = 1; k < 9; k++)
                 if (k == lane) val = jpq[k];
-            sh_add(&Js[(a0 + i) * n + b0 + j], (TA)2 * val);
+            acc_add(&Js[(a0 + i) * n + b0 + j], (TA)2 * val);
         }
     }
     __syncthreads();
-    TA *gJ, *gK;
-    if constexpr (sizeof(TA) == 8) {
-        gJ = (TA *)(b.accd + md.acc0);
-    } else {
-        gJ = (TA *)(b.accf + md.acc0);
-    }
-    gK = gJ + nn;
+    TACC *gJ;
+    if constexpr (std::is_same<TACC, double>::value) gJ = b.accd + md.acc0;
+    else gJ = b.accx + md.acc0;
+    TACC *gK = gJ + nn;
     for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-        TA j = Js[i], k = Ks[i];
-        if (j != (TA)0) atomicAdd(&gJ[i], j);
-        if (k != (TA)0) atomicAdd(&gK[i], k);
+        const TACC j = Js[i], k = Ks[i];
+        if (acc_nonzero(j)) acc_merge(&gJ[i], j);
+        if (acc_nonzero(k)) acc_merge(&gK[i], k);
     }
 }
 
-template <typename TS, typename TA> static size_t jk_smem(int n) {
-    return ((3ull * n * n * sizeof(TA) + 15) & ~15ull) + (size_t)JK_WARPS * JkStage<TS>::CH * sizeof(TS);
+template <typename TS, typename TA, typename TACC>
+static int launch_jk_t(const DevBatch &b, int nchunk, int mode, int n, int max_pair, cudaStream_t s) {
+    const JkPlan p = jk_plan<TS, TA, TACC>(n, max_pair);
+    if (!p.warps) return -1;
+    cudaFuncSetAttribute(jk_kernel<TS, TA, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.bytes);
+    jk_kernel<TS, TA, TACC><<<dim3(nchunk, b.nmol), p.warps * 32, p.bytes, s>>>(b, nchunk, mode, max_pair, p.ch,
+                                                                                p.pairs_in_smem);
+    return 0;
 }
 
-void launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, cudaStream_t s) {
-    dim3 grid(nchunk, b.nmol);
-    const int n = max_nbf;
-    if (b.precision == 0) {  // FP64 store
-        const size_t sm = jk_smem<double, double>(n);
-        cudaFuncSetAttribute(jk_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        jk_kernel<double, double><<<grid, JK_WARPS * 32, sm, s>>>(b, nchunk, mode);
-    } else if (acc_fp64) {
-        const size_t sm = jk_smem<float, double>(n);
-        cudaFuncSetAttribute(jk_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        jk_kernel<float, double><<<grid, JK_WARPS * 32, sm, s>>>(b, nchunk, mode);
-    } else {
-        const size_t sm = jk_smem<float, float>(n);
-        cudaFuncSetAttribute(jk_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        jk_kernel<float, float><<<grid, JK_WARPS * 32, sm, s>>>(b, nchunk, mode);
-    }
+int launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_pair, cudaStream_t s) {
+    if (b.precision == 0) return launch_jk_t<double, double, double>(b, nchunk, mode, max_nbf, max_pair, s);
+    if (acc_fp64) return launch_jk_t<float, double, double>(b, nchunk, mode, max_nbf, max_pair, s);
+    return launch_jk_t<float, float, Fx>(b, nchunk, mode, max_nbf, max_pair, s);
 }
 
 // ------------------------------------------------ final-step correction
@@ -268,7 +318,7 @@ __device__ __forceinline__ void correct_block(const DevBatch &b, const MolDesc &
                                             AB, CD, AC, b.boys64, out);
 #pragma unroll
     for (int x = 0; x < N; x++) out[x] -= (double)v32[x];
-    jk_block<double, double, LA, LB, LC, LD>(out, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq);
+    jk_block<double, double, double, LA, LB, LC, LD>(out, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq);
 }
 
 __global__ void __launch_bounds__(256) jk_correct_kernel(DevBatch b, int nchunk, double theta) {

@@ -17,7 +17,9 @@ int launch_grid_build(const DevBatch &b, long long nblk_total, const int *blk_mo
                       const double *ang, int max_atoms, cudaStream_t s);
 // J/K from the packed store.  acc_fp64: accumulate in FP64 (accd) instead of
 // FP32 (accf); mode 0: molecules still iterating, 1: every molecule.
-void launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, cudaStream_t s);
+// max_pair: largest candidate-pair count of a molecule (sizes the shared pair table).
+// Returns -1 when a molecule of max_nbf does not fit the kernel's shared memory.
+int launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_pair, cudaStream_t s);
 // Final-step correction of the FP32 store: quartets with Q_pq Q_rs >= theta
 // recomputed in FP64, (I64 - I32) contracted with D into the FP64 accumulators.
 void launch_jk_correct(const DevBatch &b, int nchunk, double theta, int max_nbf, cudaStream_t s);
@@ -26,11 +28,11 @@ void launch_jk_correct(const DevBatch &b, int nchunk, double theta, int max_nbf,
 void launch_fix_list(const DevBatch &b, cudaStream_t s);
 void launch_jk_fix(const DevBatch &b, cudaStream_t s);
 // AO + density + B3LYP + V_xc on the grid; acc_fp64 and mode as above.
-void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
+// skip_tc: leave out the molecules the tensor-core kernel takes (grid_tc_fits).
+void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int skip_tc, int max_nbf, int max_nsh,
                     cudaStream_t s);
-// Tensor-core (tcgen05, 3xTF32) version for the mixed path; supported when
-// the padded basis is <= 80 and a molecule has <= 60 shells.
-bool grid_xc_tc_supported(int max_nbf, int max_nsh);
+// Tensor-core (tcgen05, 3xTF32) version for the mixed iterations; takes the
+// molecules with grid_tc_fits() and skips the others.
 void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
                        cudaStream_t s);
 // Per-molecule FP64 SCF stages.

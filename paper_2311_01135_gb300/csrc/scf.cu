@@ -212,9 +212,9 @@ __device__ double assemble_fock(const DevBatch &b, int m, const MolDesc &md, con
     double e = 0.0;
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
         int i = idx / n, j = idx % n, tr = j * n + i;
-        double jj = (double)aJ[idx] + (double)aJ[tr];
-        double kk = (double)aK[idx] + (double)aK[tr];
-        double vv = b.xc ? (double)aV[idx] + (double)aV[tr] : 0.0;
+        double jj = acc_value(aJ[idx]) + acc_value(aJ[tr]);
+        double kk = acc_value(aK[idx]) + acc_value(aK[tr]);
+        double vv = b.xc ? acc_value(aV[idx]) + acc_value(aV[tr]) : 0.0;
         J[idx] = jj;
         K[idx] = kk;
         Vx[idx] = vv;
@@ -222,7 +222,10 @@ __device__ double assemble_fock(const DevBatch &b, int m, const MolDesc &md, con
         e += D[idx] * (H[idx] + 0.5 * jj - 0.25 * b.a0 * kk);
     }
     e = la::block_sum(e, red);
-    return e + b.st[m].Exc + b.st[m].Enuc;
+    const double exc = (double)b.st[m].exc_fx * (1.0 / RKS_FX_EXC);
+    __syncthreads();
+    if (threadIdx.x == 0) b.st[m].Exc = exc;
+    return e + exc + b.st[m].Enuc;
 }
 
 // ------------------------------------------------------------ one step
@@ -403,8 +406,8 @@ void launch_scf_step(const DevBatch &b, int acc_fp64, cudaStream_t s) {
         cudaFuncSetAttribute(scf_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
         scf_step_kernel<double><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accd);
     } else {
-        cudaFuncSetAttribute(scf_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
-        scf_step_kernel<float><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accf);
+        cudaFuncSetAttribute(scf_step_kernel<Fx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
+        scf_step_kernel<Fx><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accx);
     }
 }
 
@@ -452,8 +455,8 @@ void launch_scf_final(const DevBatch &b, int acc_fp64, cudaStream_t s) {
         cudaFuncSetAttribute(scf_final_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
         scf_final_kernel<double><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accd);
     } else {
-        cudaFuncSetAttribute(scf_final_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
-        scf_final_kernel<float><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accf);
+        cudaFuncSetAttribute(scf_final_kernel<Fx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
+        scf_final_kernel<Fx><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accx);
     }
 }
 
@@ -469,13 +472,16 @@ __global__ void fock_only_kernel(DevBatch b, const TA *accbase) {
 
 void launch_fock_only(const DevBatch &b, int acc_fp64, cudaStream_t s) {
     if (acc_fp64 || b.precision == 0) fock_only_kernel<double><<<b.nmol, 256, 0, s>>>(b, b.accd);
-    else fock_only_kernel<float><<<b.nmol, 256, 0, s>>>(b, b.accf);
+    else fock_only_kernel<Fx><<<b.nmol, 256, 0, s>>>(b, b.accx);
 }
 
 // Exc accumulators to zero before a grid pass.
 __global__ void reset_exc_kernel(DevBatch b) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < b.nmol) b.st[m].Exc = 0.0;
+    if (m < b.nmol) {
+        b.st[m].Exc = 0.0;
+        b.st[m].exc_fx = 0;
+    }
 }
 void launch_reset_exc(const DevBatch &b, cudaStream_t s) {
     reset_exc_kernel<<<(b.nmol + 127) / 128, 128, 0, s>>>(b);
