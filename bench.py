@@ -422,7 +422,8 @@ def main():
     stages = {k: v for k, v in prof.items()}
     dom = max(stages, key=lambda k: stages[k]["ms"])
     roof = roofline(dom, stages[dom], B, mols, pk)
-    others = {k: roofline(k, stages[k], B, mols, pk) for k in ("jk", "grid_xc_final") if k in stages and k != dom}
+    others = {k: roofline(k, stages[k], B, mols, pk) for k in ("jk", "grid_xc_tc_final", "grid_xc_final")
+              if k in stages and k != dom}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -456,7 +457,7 @@ def roofline(name, st, B, mols, pk):
     n = [g.rks_nbf(Z) for Z, _ in mols]
     P = [len(Z) * 50 * 12 * 24 for Z, _ in mols]
     flops = sum(4.0 * p * k * k for p, k in zip(P, n))  # rho: 2 P n^2 (Phi D), V_xc: 2 P n^2 (Phi^T X)
-    if name == "grid_xc_tc":
+    if name in ("grid_xc_tc", "grid_xc_tc_final"):
         # the two contractions run on the tensor cores (3xTF32 split: 3 MMAs per
         # product, counted once here); peak = TF32 dense, taken as the measured
         # sustained bf16 figure x the nominal TF32 : BF16 ratio (1.1 : 2.25)

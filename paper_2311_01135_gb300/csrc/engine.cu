@@ -629,11 +629,11 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
         launch_jk_fix(d, s);
     }
     if (d.xc) {
-        // Tensor-core accumulation truncates (round toward zero): fine for the
-        // iterations, but the final step's energy uses the CUDA-core kernel,
-        // whose FP32 sums round to nearest and carry no bias.  The kernel is
-        // chosen per molecule (grid_tc_fits), never per batch.
-        const bool tc = !acc_fp64 && b->precision == RKS_MIXED && c->opt.grid_tc;
+        // Molecules that fit the tensor-core kernel (grid_tc_fits, decided per
+        // molecule, never per batch) run it; in the final step it forms the
+        // density on the CUDA cores (the tensor cores' truncating accumulation
+        // would bias E_xc).  The others run the CUDA-core kernel.
+        const bool tc = b->precision == RKS_MIXED && c->opt.grid_tc;
         bool need_cc = !tc;
         if (tc) {
             bool any_tc = false;
@@ -643,8 +643,8 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
             }
             if (any_tc) {
                 const int nchunk_tc = 4;
-                StageScope sc(c, s, "grid_xc_tc", 0);
-                launch_grid_xc_tc(d, nchunk_tc, 0, mode, b->max_nbf, b->max_nsh, s);
+                StageScope sc(c, s, acc_fp64 ? "grid_xc_tc_final" : "grid_xc_tc", 0);
+                launch_grid_xc_tc(d, nchunk_tc, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
             }
         }
         if (need_cc) {

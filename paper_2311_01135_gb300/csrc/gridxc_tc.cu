@@ -161,7 +161,8 @@ __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
 }
 
 #define TC_THREADS 512
-#define TC_SCREEN 1e-9f  // per-block AO screening threshold (iterations only)
+#define TC_SCREEN 1e-9f         // per-block AO screening threshold, iterations
+#define TC_SCREEN_FINAL 1e-14f  // and final step
 
 __device__ __forceinline__ void ld4(uint32_t taddr, float *v) {
     uint32_t r[4];
@@ -180,7 +181,12 @@ __device__ __forceinline__ float shell_rmin(float d, float lo, float hi) {
     return d > hi ? d - hi : (d < lo ? lo - d : 0.f);
 }
 
-template <typename TA>
+// FINAL (the mixed path's final step, TA = double): the density contraction
+// T = Phi D runs on the CUDA cores in FP32 with round-to-nearest sums (the
+// tensor cores' truncating accumulation would bias rho and E_xc), V_xc stays
+// on the tensor cores (it only moves the final eigenvalues, at ~1e-7), and
+// V_xc is accumulated in FP64.
+template <typename TA, bool FINAL>
 __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar1, bar2[2];
@@ -208,20 +214,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     int *aoc = (int *)(sm + L.aoc), *rset = (int *)(sm + L.rset);
     const uint32_t sg1 = (uint32_t)(np / 4) * 128u;  // row-group stride, K = np (GEMM1 A and B)
 
-    // ---- per-CTA constants: D (hi, lo) as GEMM1's B (rows nu, K = mu), shells, radial sets
+    // ---- per-CTA constants: D (hi, lo) as GEMM1's B (rows nu, K = mu), or plain
+    // FP32 D[mu][nu] for the CUDA-core contraction of the final step; shells, radial sets
     const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
-    for (int i = t; i < np * np / 4; i += blockDim.x) {
-        const int row = i / (np / 4), kc = i % (np / 4);
-        float v[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int k = kc * 4 + j;
-            v[j] = (row < n && k < n) ? (float)D[row * n + k] : 0.f;
+    if constexpr (FINAL) {
+        float *Dp = (float *)(sm + L.D_hi);
+        for (int i = t; i < np * np; i += blockDim.x) {
+            const int row = i / np, col = i % np;
+            Dp[i] = (row < n && col < n) ? (float)D[row * n + col] : 0.f;
         }
-        float4 hi, lo;
-        tc::split4(v, hi, lo);
-        *(float4 *)(sm + L.D_hi + tc::coff(row, kc * 4, sg1)) = hi;
-        *(float4 *)(sm + L.D_lo + tc::coff(row, kc * 4, sg1)) = lo;
+    } else {
+        for (int i = t; i < np * np / 4; i += blockDim.x) {
+            const int row = i / (np / 4), kc = i % (np / 4);
+            float v[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int k = kc * 4 + j;
+                v[j] = (row < n && k < n) ? (float)D[row * n + k] : 0.f;
+            }
+            float4 hi, lo;
+            tc::split4(v, hi, lo);
+            *(float4 *)(sm + L.D_hi + tc::coff(row, kc * 4, sg1)) = hi;
+            *(float4 *)(sm + L.D_lo + tc::coff(row, kc * 4, sg1)) = lo;
+        }
     }
     for (int s = t; s < nsh; s += blockDim.x) {
         const int g = md.sh0 + s;
@@ -353,7 +368,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                     bound += fabsf(shx[s * TC_SHX + 3 + k]) * __expf(-a * rmin * rmin) *
                              (1.f + rmin + 2.f * a * rmin * rmin * rmin);
                 }
-                on = bound > TC_SCREEN;
+                on = bound > (FINAL ? TC_SCREEN_FINAL : TC_SCREEN);
             }
             sig[s] = on;
             if (on) atomicAdd(&s_nsig, 1);
@@ -403,7 +418,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
         const float4 pq4 = pt4[p];
         const float px = pq4.x, py = pq4.y, pz = pq4.z;
         const int hp = owner_h[p];
-        {
+        if constexpr (FINAL) {
+            // plain FP32 Phi[mu][point] for the CUDA-core contraction
+            float *phi = (float *)(sm + L.work);
+            for (int kc = g4 * (nq / 4); kc < (g4 + 1) * (nq / 4); kc++) {
+                const int4 code4 = *(const int4 *)(aoc + kc * 4);
+                const int codes[4] = {code4.x, code4.y, code4.z, code4.w};
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int code = codes[j];
+                    float val = 0.f;
+                    if (code >= 0) {
+                        const int s = code >> 2, c = (code & 3) - 1;
+                        const float gg = Rg[s * TC_BP + p];
+                        const float pc = c == 0 ? px : (c == 1 ? py : pz);
+                        val = (c < 0) ? gg : (shf[s * 8 + hp * 4 + c] + pc) * gg;
+                    }
+                    phi[(kc * 4 + j) * TC_BP + p] = val;
+                }
+            }
+            __syncthreads();
+        } else {
             const uint32_t phi_hi = L.work, phi_lo = L.work + (uint32_t)TC_BP * np * 4;
             for (int kc = g4 * (nq / 4); kc < (g4 + 1) * (nq / 4); kc++) {
                 float v[4];
@@ -444,20 +479,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
         // ---- D: density from the T rows, shell by shell (thread = point, AO quarter):
         // with u = sum_c T_c d_c (p shell; u = T for an s shell) and Tv = (T_x, T_y, T_z),
         // rho += g u and grad rho += 2 (g' u d + g Tv)
-        const bool ok1 = __syncthreads_and(tc::wait(&bar1, ph1));
-        ph1 ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok1) {
-            failed = true;
-            break;
+        float Tacc[TC_NPMAX / 4];  // FINAL: this thread's T columns, from the CUDA cores
+        if constexpr (FINAL) {
+#pragma unroll
+            for (int j = 0; j < TC_NPMAX / 4; j++) Tacc[j] = 0.f;
+            const float *phi = (const float *)(sm + L.work);
+            const float *Dp = (const float *)(sm + L.D_hi);
+            for (int mu = 0; mu < n; mu++) {
+                if (aoc[mu] < 0) continue;  // zero in this block (uniform)
+                const float ph = phi[mu * TC_BP + p];
+                const float4 *drow = (const float4 *)(Dp + mu * np + g4 * nq);
+#pragma unroll
+                for (int k = 0; k < TC_NPMAX / 16; k++) {
+                    if (k * 4 < nq) {
+                        const float4 d4 = drow[k];
+                        Tacc[4 * k] += ph * d4.x;
+                        Tacc[4 * k + 1] += ph * d4.y;
+                        Tacc[4 * k + 2] += ph * d4.z;
+                        Tacc[4 * k + 3] += ph * d4.w;
+                    }
+                }
+            }
+        } else {
+            const bool ok1 = __syncthreads_and(tc::wait(&bar1, ph1));
+            ph1 ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok1) {
+                failed = true;
+                break;
+            }
         }
         {
             float rho = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
             int cur = -1;
             float cg = 0.f, cgp = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, u = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
-            for (int cc = g4 * nq; cc < (g4 + 1) * nq; cc += 4) {
+#pragma unroll
+            for (int k4 = 0; k4 < TC_NPMAX / 16; k4++) {
+                if (k4 * 4 >= nq) break;
+                const int cc = g4 * nq + k4 * 4;
                 float tv[4];
-                ld4(tT + ((uint32_t)(q * 32) << 16) + cc, tv);
+                if constexpr (FINAL) {
+                    tv[0] = Tacc[4 * k4]; tv[1] = Tacc[4 * k4 + 1]; tv[2] = Tacc[4 * k4 + 2]; tv[3] = Tacc[4 * k4 + 3];
+                } else {
+                    ld4(tT + ((uint32_t)(q * 32) << 16) + cc, tv);
+                }
                 const int4 code4 = *(const int4 *)(aoc + cc);
                 const int codes[4] = {code4.x, code4.y, code4.z, code4.w};
 #pragma unroll
@@ -668,7 +733,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     if (s_fail && t == 0) {
         atomicOr(&b.st[m].err_flag, 4);
         // give in-flight MMAs a bounded chance to drain before freeing tensor memory
-        tc::wait(&bar1, ph1);
+        if (!FINAL) tc::wait(&bar1, ph1);
         tc::wait(&bar2[0], ph2[0]);
         tc::wait(&bar2[1], ph2[1]);
     }
@@ -684,10 +749,10 @@ void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, in
     const int np = min((max_nbf + 15) & ~15, TC_NPMAX);  // larger molecules return at once
     const size_t sm = tc_layout(np, min(max_nsh, TC_NSHMAX)).total + 128;
     if (acc_fp64) {
-        cudaFuncSetAttribute(grid_xc_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        grid_xc_tc_kernel<double><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);
+        cudaFuncSetAttribute(grid_xc_tc_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        grid_xc_tc_kernel<double, true><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);
     } else {
-        cudaFuncSetAttribute(grid_xc_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        grid_xc_tc_kernel<float><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);
+        cudaFuncSetAttribute(grid_xc_tc_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        grid_xc_tc_kernel<float, false><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);
     }
 }

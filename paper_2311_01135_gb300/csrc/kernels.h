@@ -31,8 +31,9 @@ void launch_jk_fix(const DevBatch &b, cudaStream_t s);
 // skip_tc: leave out the molecules the tensor-core kernel takes (grid_tc_fits).
 void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int skip_tc, int max_nbf, int max_nsh,
                     cudaStream_t s);
-// Tensor-core (tcgen05, 3xTF32) version for the mixed iterations; takes the
-// molecules with grid_tc_fits() and skips the others.
+// Tensor-core (tcgen05, 3xTF32) version for the mixed path; takes the
+// molecules with grid_tc_fits() and skips the others.  acc_fp64 = 1 is the
+// final step: density contraction on the CUDA cores, FP64 V_xc accumulation.
 void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
                        cudaStream_t s);
 // Per-molecule FP64 SCF stages.
