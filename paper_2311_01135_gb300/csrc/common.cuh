@@ -146,6 +146,7 @@ struct DevBatch {
     // final step (accd); both views share one buffer, zeroed before each pass
     struct Fx *accx;
     double *accd;
+    int *jk_next;           // [nmol] J/K row queue heads (zeroed before each J/K launch)
     // Boys tables
     const double *boys64;
     const float *boys32;

@@ -527,7 +527,8 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
         (rc = dalloc(b, (unsigned char **)&gx, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gy, pts_off * esz)) ||
         (rc = dalloc(b, (unsigned char **)&gz, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gw, pts_off * esz)) ||
         (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) ||
-        (rc = dalloc(b, &b->blk_mol, b->nblk_total)) || (rc = dalloc(b, &b->active_d, 1))) {
+        (rc = dalloc(b, &b->blk_mol, b->nblk_total)) || (rc = dalloc(b, &b->active_d, 1)) ||
+        (rc = dalloc(b, &d.jk_next, nmol))) {
         rks_batch_destroy(b);
         return rc;
     }
@@ -618,7 +619,8 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
     for (auto &m : b->md) acc_elems += 3LL * m.nbf * m.nbf;
     CUDA_OK(cudaMemsetAsync(d.accd, 0, sizeof(double) * acc_elems, s));  // zero in both views
     launch_reset_exc(d, s);
-    const int nchunk_jk = 8;
+    const int nchunk_jk = 4;  // blocks per molecule; rows are shared out dynamically
+    CUDA_OK(cudaMemsetAsync(d.jk_next, 0, sizeof(int) * b->nmol, s));
     {
         StageScope sc(c, s, acc_fp64 ? "jk_final" : "jk", 0);
         if (launch_jk(d, nchunk_jk, acc_fp64, mode, b->max_nbf, b->max_pair, s))
@@ -642,7 +644,7 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
                 else need_cc = true;
             }
             if (any_tc) {
-                const int nchunk_tc = 4;
+                const int nchunk_tc = 16;  // tuned: 1024-molecule sweep over 2, 4, 8, 16
                 StageScope sc(c, s, acc_fp64 ? "grid_xc_tc_final" : "grid_xc_tc", 0);
                 launch_grid_xc_tc(d, nchunk_tc, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
             }

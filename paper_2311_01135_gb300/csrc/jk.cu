@@ -192,7 +192,14 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
     }
     __syncthreads();
     const TS *store = (const TS *)b.store + md.eri0;
-    for (int r = c + nchunk * warp; r < npair; r += nchunk * nwarp) {
+    // rows are taken from a per-molecule queue shared by the molecule's
+    // blocks, longest first (row r holds r + 1 kets; the p-shell rows come last)
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = atomicAdd(&b.jk_next[m], 1);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= npair) break;
+        const int r = npair - 1 - q;
         const uint32_t bi = pairs_in_smem ? pinfo[r] : pair_of(r);
         const double qpq = kq[r];
         const int a0 = bi & 127, b0 = (bi >> 7) & 127, lP = (bi >> 14) & 1, lQ = (bi >> 15) & 1;
