@@ -107,6 +107,10 @@ typedef struct rks_options {
     int32_t admit_wait_us;  /* serving: while other cohorts run, a partial cohort (fewer than
                                max_slots molecules) is admitted once its oldest request has waited
                                this long (microseconds), default 20000 */
+    int32_t grid_chunks;    /* thread blocks per molecule of the grid kernels (0 = tuned default, 16);
+                               changes the grouping of the V_xc sums, so results move at ~1e-7 */
+    int32_t jk_chunks;      /* thread blocks per molecule of the J/K kernel (0 = tuned default, 8);
+                               results are bit-identical for any value */
 } rks_options;
 
 typedef struct rks_result_t {

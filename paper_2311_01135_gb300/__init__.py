@@ -37,7 +37,8 @@ class rks_options(ctypes.Structure):
                 ("hbm_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("pad0", ctypes.c_int32), ("fix_theta", ctypes.c_double),
                 ("grid_tc", ctypes.c_int32), ("guess", ctypes.c_int32),
-                ("max_cohorts", ctypes.c_int32), ("admit_wait_us", ctypes.c_int32)]
+                ("max_cohorts", ctypes.c_int32), ("admit_wait_us", ctypes.c_int32),
+                ("grid_chunks", ctypes.c_int32), ("jk_chunks", ctypes.c_int32)]
 
 
 class rks_result_t(ctypes.Structure):

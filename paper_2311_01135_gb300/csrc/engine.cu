@@ -619,7 +619,9 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
     for (auto &m : b->md) acc_elems += 3LL * m.nbf * m.nbf;
     CUDA_OK(cudaMemsetAsync(d.accd, 0, sizeof(double) * acc_elems, s));  // zero in both views
     launch_reset_exc(d, s);
-    const int nchunk_jk = 4;  // blocks per molecule; rows are shared out dynamically
+    // blocks per molecule; J/K rows are shared out dynamically.  Defaults from
+    // the autotuner (tune.py) on the 9-11-heavy-atom workload.
+    const int nchunk_jk = c->opt.jk_chunks > 0 ? c->opt.jk_chunks : 8;
     CUDA_OK(cudaMemsetAsync(d.jk_next, 0, sizeof(int) * b->nmol, s));
     {
         StageScope sc(c, s, acc_fp64 ? "jk_final" : "jk", 0);
@@ -644,13 +646,13 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
                 else need_cc = true;
             }
             if (any_tc) {
-                const int nchunk_tc = 16;  // tuned: 1024-molecule sweep over 2, 4, 8, 16
+                const int nchunk_tc = c->opt.grid_chunks > 0 ? c->opt.grid_chunks : 16;
                 StageScope sc(c, s, acc_fp64 ? "grid_xc_tc_final" : "grid_xc_tc", 0);
                 launch_grid_xc_tc(d, nchunk_tc, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
             }
         }
         if (need_cc) {
-            const int nchunk_gx = 16;
+            const int nchunk_gx = c->opt.grid_chunks > 0 ? c->opt.grid_chunks : 16;
             StageScope sc(c, s, acc_fp64 ? "grid_xc_final" : "grid_xc", 0);
             launch_grid_xc(d, nchunk_gx, acc_fp64, mode, tc ? 1 : 0, b->max_nbf, b->max_nsh, s);
         }
@@ -1231,7 +1233,7 @@ extern "C" int rks_create(const rks_options *options, rks_ctx **out) {
     if (o.basis != 0 || o.n_rad <= 0 || o.n_theta <= 0 || o.n_theta > 64 || o.n_phi <= 0 || o.becke_iters < 0 ||
         (o.precision != RKS_FP64 && o.precision != RKS_MIXED) || o.max_iters <= 0 || o.max_slots <= 0 ||
         !(o.fix_theta >= 0) || (o.guess != RKS_GUESS_SAD && o.guess != RKS_GUESS_CORE) || o.max_cohorts <= 0 ||
-        o.admit_wait_us < 0)
+        o.admit_wait_us < 0 || o.grid_chunks < 0 || o.grid_chunks > 256 || o.jk_chunks < 0 || o.jk_chunks > 256)
         return fail(RKS_EINVAL, "bad options");
     int ndev = 0;
     CUDA_OK(cudaGetDeviceCount(&ndev));
