@@ -97,11 +97,12 @@ __device__ __forceinline__ void jk_block(const TS *__restrict__ v, TA scale, int
 }
 
 // Elements of the store staged per warp and window (coalesced loads): up to
-// 512 (FP32 store) or 256 (FP64), fewer when the molecule's D/J/K leave less
-// room; a window must hold the largest block (81 elements).  16 warps for
+// 32 x 27 (a chunk of the largest staged blocks), fewer when the molecule's
+// D/J/K leave less room; a window must hold one staged block.  16 warps for
 // FP32 arithmetic, 8 for FP64 (whose blocks need twice the registers).
 #define JK_WARPS_MAX 16
 #define JK_SMEM_LIMIT 232448
+#define JK_STAGE_BLOCK 27  // largest block that goes through the stage
 
 // Per kept pair s of the molecule, in shared memory: its Schwarz factor and
 // a packed descriptor: AO start of R (bits 0-6), of S (7-13), l_R (14),
@@ -119,14 +120,14 @@ struct JkPlan {
 template <typename TS, typename TA, typename TACC> static JkPlan jk_plan(int n, int npair) {
     const size_t mats = (((size_t)n * n * sizeof(TA) + 15) & ~(size_t)15) + 2 * (size_t)n * n * sizeof(TACC);
     const size_t table = (size_t)npair * sizeof(double) + (((size_t)npair * sizeof(uint32_t) + 15) & ~(size_t)15);
-    const int ch_max = sizeof(TS) == 4 ? 512 : 256;
+    const int ch_max = 32 * JK_STAGE_BLOCK;  // a full chunk of the largest staged blocks
     JkPlan p;
     for (p.warps = sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS_MAX; p.warps >= 8; p.warps /= 2)
         for (p.pairs_in_smem = 1; p.pairs_in_smem >= 0; p.pairs_in_smem--) {
             const size_t fixed = mats + (p.pairs_in_smem ? table : 0);
             if (fixed >= JK_SMEM_LIMIT) continue;
             const long long ch = (long long)((JK_SMEM_LIMIT - fixed) / ((size_t)p.warps * sizeof(TS)));
-            if (ch < 96) continue;
+            if (ch < 2 * JK_STAGE_BLOCK) continue;
             p.ch = (int)(ch < ch_max ? ch : ch_max);
             p.bytes = fixed + (size_t)p.warps * p.ch * sizeof(TS);
             return p;
@@ -224,34 +225,39 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
             }
             const int tot = __shfl_sync(0xffffffffu, x, 31);
             const int start = x - nel;  // this lane's block, relative to the chunk
-            int first = 0;              // lanes below it are done
+            auto run_block = [&](const TS *v) {
+                TA scale = bra_scale;
+                if ((ki >> 16) & 1) scale *= (TA)0.5;
+                if (s == r) scale *= (TA)0.5;
+                const int c0 = ki & 127, d0 = (ki >> 7) & 127;
+                const int cls = (lP << 3) | (lQ << 2) | (((ki >> 14) & 1) << 1) | ((ki >> 15) & 1);
+                switch (cls) {
+                case 0x0: jk_block<TS, TA, TACC, 0, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0x8: jk_block<TS, TA, TACC, 1, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0xA: jk_block<TS, TA, TACC, 1, 0, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0xC: jk_block<TS, TA, TACC, 1, 1, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0xE: jk_block<TS, TA, TACC, 1, 1, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0xF: jk_block<TS, TA, TACC, 1, 1, 1, 1>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                default: break;
+                }
+            };
+            // (pp|pp) blocks (81 elements) are read by their lane straight from
+            // the store: a window of them would leave most lanes idle.  They
+            // are the chunk's last lanes (kets are ordered by class).
+            const bool big = nel > JK_STAGE_BLOCK;
+            if (__any_sync(0xffffffffu, big) && big) run_block(store + base + start);
+            int first = 0;  // lanes below it are done
             while (first < 32) {
                 const int w0 = __shfl_sync(0xffffffffu, start, first);
-                const bool mine = lane >= first && x <= w0 + CH;
+                const bool mine = lane >= first && !big && x <= w0 + CH;
                 int wend = mine ? x : w0;
                 for (int o2 = 16; o2 > 0; o2 >>= 1) wend = max(wend, __shfl_xor_sync(0xffffffffu, wend, o2));
                 const TS *src = store + base + w0;
                 for (int e = lane; e < wend - w0; e += 32) stg[e] = src[e];
                 __syncwarp();
-                if (mine && keep) {
-                    const TS *v = stg + (start - w0);
-                    TA scale = bra_scale;
-                    if ((ki >> 16) & 1) scale *= (TA)0.5;
-                    if (s == r) scale *= (TA)0.5;
-                    const int c0 = ki & 127, d0 = (ki >> 7) & 127;
-                    const int cls = (lP << 3) | (lQ << 2) | (((ki >> 14) & 1) << 1) | ((ki >> 15) & 1);
-                    switch (cls) {
-                    case 0x0: jk_block<TS, TA, TACC, 0, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    case 0x8: jk_block<TS, TA, TACC, 1, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    case 0xA: jk_block<TS, TA, TACC, 1, 0, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    case 0xC: jk_block<TS, TA, TACC, 1, 1, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    case 0xE: jk_block<TS, TA, TACC, 1, 1, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    case 0xF: jk_block<TS, TA, TACC, 1, 1, 1, 1>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                    default: break;
-                    }
-                }
+                if (mine && keep) run_block(stg + (start - w0));
                 __syncwarp();
-                const unsigned pend = __ballot_sync(0xffffffffu, lane >= first && !mine);
+                const unsigned pend = __ballot_sync(0xffffffffu, lane >= first && !mine && !big);
                 first = pend ? __ffs(pend) - 1 : 32;
             }
             base += tot;
