@@ -243,8 +243,9 @@ class Batch:
     def __init__(self, ctx: Context, mols):
         self.ctx = ctx
         na = np.array([len(Z) for Z, _ in mols], np.int32)
-        Z = np.ascontiguousarray(np.concatenate([np.asarray(Z, np.int32) for Z, _ in mols]))
-        xyz = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1, 3) for _, x in mols]))
+        Z = np.ascontiguousarray(np.concatenate([np.asarray(Z, np.int32) for Z, _ in mols] or [np.zeros(0, np.int32)]))
+        xyz = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1, 3) for _, x in mols]
+                                                  or [np.zeros((0, 3))]))
         h = ctypes.c_void_p()
         _chk(lib().rks_batch_create(ctx.h, len(mols), _ptr(na), _ptr(Z), _ptr(xyz), ctypes.byref(h)),
              "rks_batch_create")
