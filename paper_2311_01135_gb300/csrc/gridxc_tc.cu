@@ -174,6 +174,26 @@ __device__ __forceinline__ void ld4(uint32_t taddr, float *v) {
     for (int j = 0; j < 4; j++) v[j] = __uint_as_float(r[j]);
 }
 
+static_assert(TC_NPMAX / 4 == 20, "ld20 reads one quarter of the padded basis");
+// This thread's row of 20 TMEM columns starting at taddr (5 loads of 4
+// columns, one wait; the wait names the registers so that no use moves above it).
+__device__ __forceinline__ void ld20(uint32_t taddr, float *v) {
+    uint32_t r[20];
+#pragma unroll
+    for (int k = 0; k < 5; k++)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r[4 * k]), "=r"(r[4 * k + 1]), "=r"(r[4 * k + 2]), "=r"(r[4 * k + 3])
+                     : "r"(taddr + 4 * k));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                   "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 20; j++) v[j] = __uint_as_float(r[j]);
+}
+
 // Lower bound on the distance from a shell centre to any point of a block:
 // the points of owner h lie on atom-centred spheres with radii in [lo, hi],
 // and the centre sits at distance d from that atom.
@@ -192,7 +212,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     __shared__ __align__(8) uint64_t bar1, bar2[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail, s_nsig, s_nset;
-    __shared__ int owner_h[TC_BP];
+    __shared__ __align__(16) int owner_h[TC_BP];
     __shared__ int sig[TC_NSHMAX];        // shell significant somewhere in this block
     __shared__ unsigned blk_r[4];         // radius range of the block per owner (float bits)
     const int m = blockIdx.y, chunk = blockIdx.x;
@@ -508,6 +528,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                 failed = true;
                 break;
             }
+            // the thread's T row segment (columns g4*nq .. +20 lie inside the
+            // 256-column allocation; those past nq are not used)
+            ld20(tT + ((uint32_t)(q * 32) << 16) + g4 * nq, Tacc);
         }
         {
             float rho = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
@@ -517,12 +540,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
             for (int k4 = 0; k4 < TC_NPMAX / 16; k4++) {
                 if (k4 * 4 >= nq) break;
                 const int cc = g4 * nq + k4 * 4;
-                float tv[4];
-                if constexpr (FINAL) {
-                    tv[0] = Tacc[4 * k4]; tv[1] = Tacc[4 * k4 + 1]; tv[2] = Tacc[4 * k4 + 2]; tv[3] = Tacc[4 * k4 + 3];
-                } else {
-                    ld4(tT + ((uint32_t)(q * 32) << 16) + cc, tv);
-                }
+                const float tv[4] = {Tacc[4 * k4], Tacc[4 * k4 + 1], Tacc[4 * k4 + 2], Tacc[4 * k4 + 3]};
                 const int4 code4 = *(const int4 *)(aoc + cc);
                 const int codes[4] = {code4.x, code4.y, code4.z, code4.w};
 #pragma unroll
@@ -700,15 +718,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                 failed = true;
                 break;
             }
+            float v[TC_NPMAX / 4];
+            ld20(tV + ((uint32_t)(q * 32) << 16) + g4 * nq, v);
 #pragma unroll
-            for (int cc = 0; cc < TC_NPMAX / 4; cc += 4) {
-                if (cc < nq) {
-                    float v[4];
-                    ld4(tV + ((uint32_t)(q * 32) << 16) + g4 * nq + cc, v);
-#pragma unroll
-                    for (int j = 0; j < 4; j++) vacc[cc + j] += v[j];
-                }
-            }
+            for (int j = 0; j < TC_NPMAX / 4; j++)
+                if (j < nq) vacc[j] += v[j];
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
         __syncthreads();
