@@ -38,9 +38,9 @@ sys.path.insert(0, ROOT)
 import molgen  # noqa: E402
 
 # dram__bytes_read.sum + dram__bytes_write.sum of grid_xc_tc_kernel<float, 0>
-# per grid point (221.95 MB over the 13,363,200 points of the 38-molecule
+# per grid point (221.30 MB over the 13,363,200 points of the 38-molecule
 # capture); kept in step with the kernel: set to None when it changes
-GRID_TC_DRAM_BYTES_PER_POINT = 16.61
+GRID_TC_DRAM_BYTES_PER_POINT = 16.56
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
@@ -469,7 +469,7 @@ def roofline(name, st, B, mols, pk):
         peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * 1.1 / 2.25
         ach = flops / (ms / 1e3) / 1e12
         # DRAM bytes per launch: ncu capture of the iteration kernel on the
-        # first 38 molecules (profiles/grid_xc_tc_38mol_mixed.md), 16.61 B per
+        # first 38 molecules (profiles/grid_xc_tc_38mol_mixed.md), 16.56 B per
         # grid point, scaled by the points of this launch
         traffic = GRID_TC_DRAM_BYTES_PER_POINT * sum(P) / 1e9 if name == "grid_xc_tc" else None
         return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",

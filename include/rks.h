@@ -262,6 +262,14 @@ int rks_eval_boys(rks_ctx *ctx, int32_t mmax, int32_t n, const double *T, double
 int rks_eval_xc(rks_ctx *ctx, int32_t n, const double *rho, const double *sigma, double *e,
                 double *v_rho, double *v_sigma, int32_t precision);
 
+/* ------------------------------------------------------ diagnostics */
+/* Exercise the device-side failure path without a fault: one block waits on
+ * an mbarrier that nothing ever arrives at, polling at most `spins` times
+ * (1 .. 2^24), the same bounded wait the tensor-core kernels use.  Returns
+ * RKS_EDEVICE when the wait gave up (the expected outcome), after which the
+ * context stays usable.  RKS_EINVAL for spins out of range. */
+int rks_selftest_bounded_wait(rks_ctx *ctx, int32_t spins);
+
 /* ------------------------------------------- allocation-free XC entry */
 /* The paper has no counterpart: this is a deployment variant of rks_eval_xc.
  * Same arguments, same kernel, same results (bit-identical), but it allocates

@@ -84,6 +84,7 @@ _SIGS = {
     "rks_eval_boys": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32]),
     "rks_eval_xc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32]),
     "rks_eval_xc_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32]),
+    "rks_selftest_bounded_wait": (ctypes.c_int, [_P, ctypes.c_int32]),
 }
 
 _lib = None
@@ -219,6 +220,10 @@ class Context:
         _chk(lib().rks_eval_xc(self.h, len(rho), _ptr(rho), _ptr(sigma), _ptr(e), _ptr(vr), _ptr(vs),
                                precision), "rks_eval_xc")
         return e, vr, vs
+
+    def selftest_bounded_wait(self, spins=100000):
+        """rks_selftest_bounded_wait: the return code (RKS_EDEVICE expected)."""
+        return lib().rks_selftest_bounded_wait(self.h, spins)
 
     def eval_xc_noalloc(self, rho, sigma, precision=RKS_FP64):
         """rks_eval_xc_noalloc: as eval_xc, staged through the library's static scratch."""

@@ -968,6 +968,19 @@ extern "C" int rks_eval_xc(rks_ctx *ctx, int32_t n, const double *rho, const dou
     return RKS_OK;
 }
 
+extern "C" int rks_selftest_bounded_wait(rks_ctx *ctx, int32_t spins) {
+    if (!ctx || spins <= 0 || spins > (1 << 24)) return fail(RKS_EINVAL, "spins out of range");
+    int *d = nullptr, h = 0;
+    CUDA_OK(cudaMalloc(&d, sizeof(int)));
+    launch_wait_selftest(d, spins, ctx->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return rks_cuda_fail(e, "bounded-wait self test", __FILE__, __LINE__);
+    return h ? fail(RKS_EDEVICE, "bounded wait gave up (expected: nothing arrives)") : RKS_OK;
+}
+
 // ------------------------------------------- allocation-free XC entry
 // The same B3LYP kernel as rks_eval_xc, staged through one file-scope device
 // array instead of cudaMalloc'd buffers.  For callers that must not allocate:

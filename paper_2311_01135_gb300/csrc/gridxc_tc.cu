@@ -33,7 +33,7 @@
 #define TC_NPMAX RKS_TC_NPMAX   // padded basis size this kernel handles
 #define TC_NSHMAX RKS_TC_NSHMAX // shells this kernel handles
 #define TC_TMEM_COLS 256
-#define TC_SPIN_LIMIT 50000000
+#define TC_SPIN_LIMIT 4000000  // polls before a wait gives up: >= ~40 ms, far above any MMA here
 
 namespace tc {
 
@@ -770,3 +770,31 @@ void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, in
         grid_xc_tc_kernel<float, false><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);
     }
 }
+
+// ------------------------------------------------ bounded-wait self test
+// The tensor-core kernels wait on mbarriers with an iteration limit; on
+// expiry they set an error flag, drain, free tensor memory and return, and
+// the host reports RKS_EDEVICE.  This kernel exercises that path without
+// any fault: it waits on an mbarrier nothing will ever arrive at, with the
+// given limit, and records whether the wait gave up.
+__global__ void wait_selftest_kernel(int *gave_up, int spins) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t done = 0;
+    for (int it = 0; it < spins && !done; it++) {
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(tc::smem_u32(&bar)), "r"(0u)
+                     : "memory");
+    }
+    const bool ok = __syncthreads_and(done != 0);
+    if (threadIdx.x == 0) *gave_up = ok ? 0 : 1;
+}
+
+void launch_wait_selftest(int *gave_up, int spins, cudaStream_t s) { wait_selftest_kernel<<<1, 32, 0, s>>>(gave_up, spins); }
+

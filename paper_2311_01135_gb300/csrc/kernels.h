@@ -45,3 +45,5 @@ void launch_fock_only(const DevBatch &b, int acc_fp64, cudaStream_t s);
 void launch_reset_exc(const DevBatch &b, cudaStream_t s);
 void launch_count_active(const DevBatch &b, int *out, cudaStream_t s);
 void launch_eval_xc(int n, const double *rho, const double *sigma, double *out, int fp32, cudaStream_t s);
+// Waits on an mbarrier that is never arrived at, `spins` bounded polls; *gave_up = 1 on expiry.
+void launch_wait_selftest(int *gave_up, int spins, cudaStream_t s);

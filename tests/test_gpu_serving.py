@@ -156,3 +156,15 @@ def test_submit_validation_and_destroy_with_work_in_flight(mols):
     t0 = time.time()
     c.close()  # in-flight and queued tickets are failed, not waited for
     assert time.time() - t0 < 120
+
+
+def test_bounded_wait_gives_up_and_context_survives():
+    """The device-side failure path, without a fault: a bounded wait on an
+    mbarrier nothing arrives at returns RKS_EDEVICE, and the same context
+    then runs a molecule normally."""
+    Z, x = molgen.h2o()
+    with g.Context(precision=g.RKS_MIXED, fixed_iters=20) as c:
+        assert c.selftest_bounded_wait(100000) == g.RKS_EDEVICE
+        assert c.selftest_bounded_wait(0) == g.RKS_EINVAL
+        r = _serve(c, [(Z, x)])[0]
+        assert r["status"] == "ok"
