@@ -4,7 +4,7 @@ Only tests, the smoke check and the CPU-baseline leg of the benchmark import
 anything under oracle/.
 
 The paper evaluates V_xc by quadrature on a small atom-centred grid ("small
-grid size (10-30k)", Section 6) but does not define it.  The definition used
+grid size (10-30k)", Section 5) but does not define it.  The definition used
 here, per atom:
 
 * radial: Treutler-Ahlrichs M4 mapping r(x) = (xi/ln 2) (1+x)^0.6 ln(2/(1-x)) of

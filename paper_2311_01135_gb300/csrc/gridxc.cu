@@ -2,7 +2,7 @@
 // gradients, density and its gradient, the B3LYP kernel, and the V_xc matrix.
 //
 // Paper: V_xc(rho) in Eq. 1 (Section 3.1), B3LYP only (Section 3.2), AO values
-// recomputed on the grid instead of stored (Section 6, "Recomputation").
+// recomputed on the grid instead of stored (Section 5, "Recomputation").
 //   rho_p = sum_mn phi_pm D_mn phi_pn,  grad rho_p = 2 sum_mn grad phi_pm D_mn phi_pn,
 //   E_xc = sum_p w_p e(rho_p, sigma_p),
 //   V_xc = V' + V'^T,  V'_mn = sum_p phi_pm X_pn,

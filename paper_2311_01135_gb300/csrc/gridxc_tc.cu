@@ -1,7 +1,7 @@
 // Exchange-correlation quadrature with the two grid contractions on the
 // tensor cores (tcgen05, kind::tf32, 3xTF32 split products, FP32 accumulators
 // in tensor memory).  Same quantities as gridxc.cu (paper Section 3.1 V_xc,
-// Section 3.2 B3LYP, Section 6 AO recomputation):
+// Section 3.2 B3LYP, AOs recomputed per block as in Section 5):
 //   GEMM1  T = Phi D            (M = 128 points, N = K = nbf padded to 16)
 //   rho_p = sum_n T_pn phi_pn,  grad rho_p = 2 sum_n T_pn grad phi_pn
 //   GEMM2  V' += Phi^T X        (M = 128 AO rows, N = nbf padded, K = points)
@@ -10,17 +10,24 @@
 //
 // All tcgen05 operands are K-major in the no-swizzle core-matrix layout: a
 // core is 8 rows x 16 bytes (4 FP32 values along K), 128 contiguous bytes;
-// core (row group g, K chunk c) sits at g * SBO + c * 128.  GEMM1 contracts
+// core (row group g, K chunk c) sits at g * SBO + c * LBO.  GEMM1 contracts
 // over AOs (Phi stored point-row / AO-column), GEMM2 over points (Phi^T and X
-// stored AO-row / point-column), so Phi is written in both arrangements.
+// stored AO-row / point-column), so Phi is written in both arrangements
+// (TF32 operands must be K-major).
 //
-// One thread block (256 threads) owns a molecule's share of 128-point grid
-// blocks and keeps V' in tensor memory across all of them.  Per block:
-//   A  radial parts g = sum c e^(-a r^2), g' = sum -2ac e^(-a r^2) per (shell, point) -> smem
-//   B  Phi (hi, lo) in GEMM1 layout;  one thread issues GEMM1 (3 MMAs per K step)
-//   D  after the commit barrier: each thread reads its point's T row from TMEM,
-//      forms rho, grad rho; B3LYP per point; coefficients to smem
-//   F  per half block (64 points): Phi^T and X (hi, lo) in GEMM2 layout; GEMM2
+// One thread block (512 threads, one per SM) owns 1/nchunk of a molecule's
+// 128-point grid blocks and keeps V' in registers across them.  Per block:
+//   top  point data (prefetched), R_owner - C table, per-shell significance
+//        from the block's radius range
+//   A    radial parts g = sum c e^(-a r^2), g' = sum -2ac e^(-a r^2) per
+//        (shell, point), one set of exponentials per radial set (2s/2p)
+//   B    Phi (hi, lo) in GEMM1 layout; thread 0 issues GEMM1 (3 MMAs per K step)
+//   D    each thread reads its point's T row segment from TMEM and forms rho,
+//        grad rho shell by shell; B3LYP in three parts on three warp groups
+//   F    32-point slices: warps 0-14 build Phi^T and X (hi, lo) in GEMM2
+//        layout, warp 15 issues each slice's MMAs behind named barriers
+//   drain  the block's V' from TMEM into registers (FP32 round-to-nearest)
+// FINAL (the mixed final step) forms T on the CUDA cores instead of GEMM1.
 // Waits on the MMA barriers are bounded: on expiry the block records an error
 // flag, waits (bounded) once more, frees its tensor memory and returns.
 #include <cstdint>
@@ -77,16 +84,6 @@ __device__ __forceinline__ bool wait(uint64_t *bar, uint32_t phase) {
                      : "memory");
     }
     return done != 0;
-}
-
-__device__ __forceinline__ void ld8(uint32_t taddr, float *v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 8; j++) v[j] = __uint_as_float(r[j]);
 }
 
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -163,16 +160,6 @@ __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
 #define TC_THREADS 512
 #define TC_SCREEN 1e-9f         // per-block AO screening threshold, iterations
 #define TC_SCREEN_FINAL 1e-14f  // and final step
-
-__device__ __forceinline__ void ld4(uint32_t taddr, float *v) {
-    uint32_t r[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 4; j++) v[j] = __uint_as_float(r[j]);
-}
 
 static_assert(TC_NPMAX / 4 == 20, "ld20 reads one quarter of the padded basis");
 // This thread's row of 20 TMEM columns starting at taddr (5 loads of 4

@@ -12,7 +12,7 @@
 // and J = J' + J'^T, K_std = K' + K'^T.
 //
 // The paper's IPU version replicated the density per thread and summed N^2
-// partial vectors at the end (Section 6, "Current (Naive) Bottleneck").  Here
+// partial vectors at the end (Section 5, "Current (Naive) Bottleneck").  Here
 // one thread block owns one slice of one molecule's rows: D sits once in shared
 // memory, a warp walks one row pq (lanes take consecutive rs), the row-local
 // J'_PQ terms are reduced across the warp by shuffles, the scattered terms go
@@ -306,136 +306,13 @@ int launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf
     return launch_jk_t<float, float, Fx>(b, nchunk, mode, max_nbf, max_pair, s);
 }
 
-// ------------------------------------------------ final-step correction
-// The mixed path keeps an FP32 store.  For the final Fock build, every kept
-// quartet whose Schwarz bound Q_pq Q_rs is at least theta is recomputed in FP64
-// and the difference (I_64 - I_32) is contracted with D into the FP64 J'/K'
-// accumulators (on top of the FP32-store contraction accumulated in FP64).
-// Quartets below theta keep their FP32 values: their rounding error is bounded
-// by ~1e-7 Q_pq Q_rs.
-template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void correct_block(const DevBatch &b, const MolDesc &md, int r, int s, int P, int Q, int R,
-                                              int S, const float *v32, double scale, int a0, int b0, int c0, int d0,
-                                              const double *Ds, double *Js, double *Ks, int n, double *jpq) {
-    double AB[3], CD[3], AC[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        AB[k] = b.sh_xyz[P * 3 + k] - b.sh_xyz[Q * 3 + k];
-        CD[k] = b.sh_xyz[R * 3 + k] - b.sh_xyz[S * 3 + k];
-        AC[k] = b.sh_xyz[P * 3 + k] - b.sh_xyz[R * 3 + k];
-    }
-    const eri::PrimPair<double> *pp = (const eri::PrimPair<double> *)b.pairprim64;
-    constexpr int N = (LA ? 3 : 1) * (LB ? 3 : 1) * (LC ? 3 : 1) * (LD ? 3 : 1);
-    double out[N];
-    eri::quartet_pd<double, LA, LB, LC, LD>(pp + (long long)(md.pair0 + r) * 9, pp + (long long)(md.pair0 + s) * 9,
-                                            AB, CD, AC, b.boys64, out);
-#pragma unroll
-    for (int x = 0; x < N; x++) out[x] -= (double)v32[x];
-    jk_block<double, double, double, LA, LB, LC, LD>(out, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq);
-}
-
-__global__ void __launch_bounds__(256) jk_correct_kernel(DevBatch b, int nchunk, double theta) {
-    extern __shared__ unsigned char smem_raw[];
-    const int m = blockIdx.y, c = blockIdx.x;
-    const MolDesc md = b.mol[m];
-    const int n = md.nbf, nn = n * n;
-    double *Ds = (double *)smem_raw;
-    double *Js = Ds + nn;
-    double *Ks = Js + nn;
-    const double *Dg = b.mat + md.mat0 + (long long)M_D * nn;
-    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-        Ds[i] = Dg[i];
-        Js[i] = 0.0;
-        Ks[i] = 0.0;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int npair = b.npair[m];
-    const float *store = (const float *)b.store + md.eri0;
-    double qmax = 0.0;
-    for (int i = lane; i < npair; i += 32) qmax = fmax(qmax, b.kq[md.pair0 + i]);
-    for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
-    for (int r = c + nchunk * warp; r < npair; r += nchunk * nwarp) {
-        const double qpq = b.kq[md.pair0 + r];
-        if (qpq * qmax < theta) continue;  // nothing in this row reaches theta
-        const int2 pq = b.kpair[md.pair0 + r];
-        const int P = md.sh0 + pq.x, Q = md.sh0 + pq.y;
-        const int lP = b.sh_l[P], lQ = b.sh_l[Q];
-        const int a0 = b.sh_ao0[P], b0 = b.sh_ao0[Q];
-        const int npq = (lP ? 3 : 1) * (lQ ? 3 : 1);
-        long long base = b.row_off[md.pair0 + m + r];
-        double jpq[9] = {};
-        for (int s0 = 0; s0 <= r; s0 += 32) {
-            const int s = s0 + lane;
-            bool keep = false, fix = false;
-            int R = 0, S = 0, nel = 0;
-            if (s <= r) {
-                const double prod = qpq * b.kq[md.pair0 + s];
-                if (prod >= TAU_SCHWARZ) {
-                    const int2 rs = b.kpair[md.pair0 + s];
-                    R = md.sh0 + rs.x;
-                    S = md.sh0 + rs.y;
-                    keep = true;
-                    fix = prod >= theta;
-                    nel = npq * (b.sh_l[R] ? 3 : 1) * (b.sh_l[S] ? 3 : 1);
-                }
-            }
-            int x = nel;
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            const int tot = __shfl_sync(0xffffffffu, x, 31);
-            if (keep && fix) {
-                const float *v = store + base + x - nel;
-                double scale = 1.0;
-                if (P == Q) scale *= 0.5;
-                if (R == S) scale *= 0.5;
-                if (s == r) scale *= 0.5;
-                const int c0 = b.sh_ao0[R], d0 = b.sh_ao0[S];
-                const int cls = (lP << 3) | (lQ << 2) | (b.sh_l[R] << 1) | b.sh_l[S];
-                switch (cls) {
-                case 0x0: correct_block<0, 0, 0, 0>(b, md, r, s, P, Q, R, S, v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0x8: correct_block<1, 0, 0, 0>(b, md, r, s, P, Q, R, S, v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xA: correct_block<1, 0, 1, 0>(b, md, r, s, P, Q, R, S, v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xC: correct_block<1, 1, 0, 0>(b, md, r, s, P, Q, R, S, v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xE: correct_block<1, 1, 1, 0>(b, md, r, s, P, Q, R, S, v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xF: correct_block<1, 1, 1, 1>(b, md, r, s, P, Q, R, S, v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                default: break;
-                }
-            }
-            base += tot;
-        }
-#pragma unroll
-        for (int k = 0; k < 9; k++) {
-            double t = jpq[k];
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            jpq[k] = t;
-        }
-        if (lane < npq) {
-            const int i = lQ ? lane / 3 : lane, j = lQ ? lane % 3 : 0;
-            double val = jpq[0];
-#pragma unroll
-            for (int k = 1; k < 9; k++)
-                if (k == lane) val = jpq[k];
-            atomicAdd(&Js[(a0 + i) * n + b0 + j], 2.0 * val);
-        }
-    }
-    __syncthreads();
-    double *gJ = b.accd + md.acc0, *gK = gJ + nn;
-    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-        if (Js[i] != 0.0) atomicAdd(&gJ[i], Js[i]);
-        if (Ks[i] != 0.0) atomicAdd(&gK[i], Ks[i]);
-    }
-}
-
-void launch_jk_correct(const DevBatch &b, int nchunk, double theta, int max_nbf, cudaStream_t s) {
-    size_t sm = 3ull * max_nbf * max_nbf * sizeof(double);
-    cudaFuncSetAttribute(jk_correct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    jk_correct_kernel<<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, theta);
-}
-
 // ------------------------------------------- dense FP64 recompute lists
+// The mixed path keeps an FP32 store.  For the final Fock build, every kept
+// quartet whose Schwarz bound Q_pq Q_rs is at least fix_theta is recomputed in
+// FP64 and the difference (I_64 - I_32) is contracted with D into the FP64
+// J'/K' accumulators (on top of the FP32-store contraction accumulated in
+// FP64).  Quartets below the threshold keep their FP32 values: their rounding
+// error is bounded by ~1e-7 Q_pq Q_rs.
 __device__ __forceinline__ int class_index(int cls) {
     // (lP lQ lR lS) bit code -> 0..5 in packing order
     return cls == 0x0 ? 0 : cls == 0x8 ? 1 : cls == 0xA ? 2 : cls == 0xC ? 3 : cls == 0xE ? 4 : 5;

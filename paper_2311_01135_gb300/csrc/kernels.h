@@ -20,11 +20,10 @@ int launch_grid_build(const DevBatch &b, long long nblk_total, const int *blk_mo
 // max_pair: largest candidate-pair count of a molecule (sizes the shared pair table).
 // Returns -1 when a molecule of max_nbf does not fit the kernel's shared memory.
 int launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_pair, cudaStream_t s);
-// Final-step correction of the FP32 store: quartets with Q_pq Q_rs >= theta
-// recomputed in FP64, (I64 - I32) contracted with D into the FP64 accumulators.
-void launch_jk_correct(const DevBatch &b, int nchunk, double theta, int max_nbf, cudaStream_t s);
-// Dense version: per-molecule class lists of the quartets above fix_theta
-// (built once at setup), one thread per listed quartet in the final step.
+// Final-step correction of the FP32 store: per-molecule class lists of the
+// quartets with Q_pq Q_rs >= fix_theta (built once at setup); in the final
+// step one thread per listed quartet recomputes it in FP64 and contracts
+// (I64 - I32) with D into the FP64 accumulators.
 void launch_fix_list(const DevBatch &b, cudaStream_t s);
 void launch_jk_fix(const DevBatch &b, cudaStream_t s);
 // AO + density + B3LYP + V_xc on the grid; acc_fp64 and mode as above.
