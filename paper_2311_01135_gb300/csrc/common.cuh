@@ -142,8 +142,8 @@ struct DevBatch {
     // FP64 matrices
     double *mat;
     // accumulators J', K', V' (3 * nbf^2 per molecule at acc0): 64-bit fixed
-    // point for the mixed iterations (accx), FP64 for the FP64 path and the
-    // final step (accd); both views share one buffer, zeroed before each pass
+    // point in every pass of the mixed path (accx), FP64 for the FP64 path
+    // (accd); both views share one buffer, zeroed before each pass
     struct Fx *accx;
     double *accd;
     int *jk_next;           // [nmol] J/K row queue heads (zeroed before each J/K launch)

@@ -183,10 +183,10 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
         __syncthreads();
     }
     // ---- flush V' and E_xc
-    // FP64 accumulators for the FP64 path and the final step, fixed point for the mixed iterations
-    using TG = std::conditional_t<sizeof(TA) == 8, double, Fx>;
+    // FP64 accumulators for the FP64 path, fixed point for every pass of the mixed path
+    using TG = std::conditional_t<sizeof(T) == 8, double, Fx>;
     TG *gV;
-    if constexpr (sizeof(TA) == 8) gV = b.accd + md.acc0 + 2 * n * n;
+    if constexpr (sizeof(T) == 8) gV = b.accd + md.acc0 + 2 * n * n;
     else gV = b.accx + md.acc0 + 2 * n * n;
 #pragma unroll
     for (int a = 0; a < TILE; a++)

@@ -192,7 +192,7 @@ __device__ __forceinline__ float shell_rmin(float d, float lo, float hi) {
 // T = Phi D runs on the CUDA cores in FP32 with round-to-nearest sums (the
 // tensor cores' truncating accumulation would bias rho and E_xc), V_xc stays
 // on the tensor cores (it only moves the final eigenvalues, at ~1e-7), and
-// V_xc is accumulated in FP64.
+// V_xc is accumulated in 64-bit fixed point like every mixed pass.
 template <typename TA, bool FINAL>
 __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -719,10 +719,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     // ---- flush V' (row mu = this thread's lane row, columns of its quarter) and E_xc
     if (!s_fail && any_block) {
         const int mu = q * 32 + lane;
-        using TG = std::conditional_t<sizeof(TA) == 8, double, Fx>;
-        TG *gV;
-        if constexpr (sizeof(TA) == 8) gV = b.accd + md.acc0 + 2 * n * n;
-        else gV = b.accx + md.acc0 + 2 * n * n;
+        Fx *gV = b.accx + md.acc0 + 2 * n * n;  // mixed path: fixed point in every pass
 #pragma unroll
         for (int j = 0; j < TC_NPMAX / 4; j++) {
             const int nu = g4 * nq + j;

@@ -302,7 +302,10 @@ static int launch_jk_t(const DevBatch &b, int nchunk, int mode, int n, int max_p
 
 int launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_pair, cudaStream_t s) {
     if (b.precision == 0) return launch_jk_t<double, double, double>(b, nchunk, mode, max_nbf, max_pair, s);
-    if (acc_fp64) return launch_jk_t<float, double, double>(b, nchunk, mode, max_nbf, max_pair, s);
+    // mixed path: fixed-point sums in every pass; the final step forms the
+    // products in FP64 (FP64 D): with FP32 D and products its energy moved by
+    // ~1e-5 Ha, which the iterations tolerate but the reported energy does not
+    if (acc_fp64) return launch_jk_t<float, double, Fx>(b, nchunk, mode, max_nbf, max_pair, s);
     return launch_jk_t<float, float, Fx>(b, nchunk, mode, max_nbf, max_pair, s);
 }
 
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(128) jk_fix_kernel(DevBatch b, int ci) {
     for (int x = 0; x < N; x++) v[x] = scale * (v[x] - (double)v32[x]);
     const int n = md.nbf;
     const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
-    double *gJ = b.accd + md.acc0, *gK = gJ + (long long)n * n;
+    Fx *gJ = b.accx + md.acc0, *gK = gJ + (long long)n * n;  // the mixed path's fixed-point accumulators
     const int a0 = b.sh_ao0[P], b0 = b.sh_ao0[Q], c0 = b.sh_ao0[R], d0 = b.sh_ao0[S];
     double jpq[na][nb] = {}, jrs[nc][nd] = {}, kpr[na][nc] = {}, kqr[nb][nc] = {}, kps[na][nd] = {}, kqs[nb][nd] = {};
 #pragma unroll
@@ -437,27 +440,27 @@ __global__ void __launch_bounds__(128) jk_fix_kernel(DevBatch b, int ci) {
 #pragma unroll
     for (int i = 0; i < na; i++)
 #pragma unroll
-        for (int j = 0; j < nb; j++) atomicAdd(&gJ[(a0 + i) * n + b0 + j], 2.0 * jpq[i][j]);
+        for (int j = 0; j < nb; j++) acc_add(&gJ[(a0 + i) * n + b0 + j], 2.0 * jpq[i][j]);
 #pragma unroll
     for (int kk = 0; kk < nc; kk++)
 #pragma unroll
-        for (int l = 0; l < nd; l++) atomicAdd(&gJ[(c0 + kk) * n + d0 + l], 2.0 * jrs[kk][l]);
+        for (int l = 0; l < nd; l++) acc_add(&gJ[(c0 + kk) * n + d0 + l], 2.0 * jrs[kk][l]);
 #pragma unroll
     for (int i = 0; i < na; i++)
 #pragma unroll
-        for (int kk = 0; kk < nc; kk++) atomicAdd(&gK[(a0 + i) * n + c0 + kk], kpr[i][kk]);
+        for (int kk = 0; kk < nc; kk++) acc_add(&gK[(a0 + i) * n + c0 + kk], kpr[i][kk]);
 #pragma unroll
     for (int j = 0; j < nb; j++)
 #pragma unroll
-        for (int kk = 0; kk < nc; kk++) atomicAdd(&gK[(b0 + j) * n + c0 + kk], kqr[j][kk]);
+        for (int kk = 0; kk < nc; kk++) acc_add(&gK[(b0 + j) * n + c0 + kk], kqr[j][kk]);
 #pragma unroll
     for (int i = 0; i < na; i++)
 #pragma unroll
-        for (int l = 0; l < nd; l++) atomicAdd(&gK[(a0 + i) * n + d0 + l], kps[i][l]);
+        for (int l = 0; l < nd; l++) acc_add(&gK[(a0 + i) * n + d0 + l], kps[i][l]);
 #pragma unroll
     for (int j = 0; j < nb; j++)
 #pragma unroll
-        for (int l = 0; l < nd; l++) atomicAdd(&gK[(b0 + j) * n + d0 + l], kqs[j][l]);
+        for (int l = 0; l < nd; l++) acc_add(&gK[(b0 + j) * n + d0 + l], kqs[j][l]);
     }
 }
 

@@ -32,7 +32,7 @@ void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int s
                     cudaStream_t s);
 // Tensor-core (tcgen05, 3xTF32) version for the mixed path; takes the
 // molecules with grid_tc_fits() and skips the others.  acc_fp64 = 1 is the
-// final step: density contraction on the CUDA cores, FP64 V_xc accumulation.
+// final step: density contraction on the CUDA cores (round-to-nearest sums).
 void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
                        cudaStream_t s);
 // Per-molecule FP64 SCF stages.

@@ -402,7 +402,8 @@ __global__ void scf_step_kernel(DevBatch b, const TA *accbase) {
 }
 
 void launch_scf_step(const DevBatch &b, int acc_fp64, cudaStream_t s) {
-    if (acc_fp64 || b.precision == 0) {
+    (void)acc_fp64;
+    if (b.precision == 0) {
         cudaFuncSetAttribute(scf_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
         scf_step_kernel<double><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accd);
     } else {
@@ -451,7 +452,8 @@ __global__ void scf_final_kernel(DevBatch b, const TA *accbase) {
 }
 
 void launch_scf_final(const DevBatch &b, int acc_fp64, cudaStream_t s) {
-    if (acc_fp64 || b.precision == 0) {
+    (void)acc_fp64;  // the accumulator type follows the precision: FP64 path double, mixed fixed point
+    if (b.precision == 0) {
         cudaFuncSetAttribute(scf_final_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
         scf_final_kernel<double><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accd);
     } else {
@@ -471,7 +473,8 @@ __global__ void fock_only_kernel(DevBatch b, const TA *accbase) {
 }
 
 void launch_fock_only(const DevBatch &b, int acc_fp64, cudaStream_t s) {
-    if (acc_fp64 || b.precision == 0) fock_only_kernel<double><<<b.nmol, 256, 0, s>>>(b, b.accd);
+    (void)acc_fp64;
+    if (b.precision == 0) fock_only_kernel<double><<<b.nmol, 256, 0, s>>>(b, b.accd);
     else fock_only_kernel<Fx><<<b.nmol, 256, 0, s>>>(b, b.accx);
 }
 
