@@ -114,6 +114,14 @@ def workload(nmol, seed=2):
     return molgen.batch(seed, nmol, 9, 11)
 
 
+def workload_config(nmol, world):
+    """The `config` of the JSON line (both arms)."""
+    return {"workload": f"{nmol} molecules/GPU, 9-11 heavy atoms (C/N/O/F+H), B3LYP(VWN5)/STO-3G, "
+                        "mixed precision, 20 SCF iterations + final correction step",
+            "nmol_per_gpu": nmol, "seed": 2, "l2": "inputs larger than L2 (packed ERIs ~10 MB x nmol)",
+            "parallelism": f"replicas x{world}"}
+
+
 def shard_indices(nmol_per_rank, rank, world):
     """Molecules of rank `rank`: r, r + N, ... of an N * nmol_per_rank set.
     Molecules are independent, so the shards need no exchange (weak scaling)."""
@@ -214,8 +222,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "molecules/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_it * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "qm1b-like 9-11 heavy atoms, B3LYP/STO-3G, 20+1 Fock builds",
-                                            "nmol": 1},
+            "data": "synthetic", "config": workload_config(args.nmol, args.gpus),
             "cpu_baseline": {"value": value, "unit": "molecules/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "molecules/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -511,10 +518,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "molecules/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": f"{nmol} molecules/GPU, 9-11 heavy atoms (C/N/O/F+H), B3LYP(VWN5)/STO-3G, "
-                                       "mixed precision, 20 SCF iterations + final correction step",
-                           "nmol_per_gpu": nmol, "seed": 2, "l2": "inputs larger than L2 (packed ERIs ~10 MB x nmol)",
-                           "parallelism": f"replicas x{world}"},
+                "config": workload_config(nmol, world),
                 "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roof, "roofline_other": others,
                 "cpu_baseline": cpu,
                 "fp64_gpu": fp64, "status_not_ok_in_first8": n_bad,

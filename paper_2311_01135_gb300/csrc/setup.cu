@@ -599,19 +599,24 @@ __global__ void grid_build_kernel(DevBatch b, const int *blk_mol, const double *
         T dz = (T)(ax[A * 3 + 2] - ax[B * 3 + 2]) + oz;
         dist[B] = dev_sqrt(dx * dx + dy * dy + dz * dz);
     }
-    T sumP = 0, PA = 0;
+    // each unordered pair once: mu_CB = -mu_BC and the iterated p is odd, so
+    // s(mu_CB) = (1 + f_BC) / 2 while s(mu_BC) = (1 - f_BC) / 2
+    T P[128];
+    for (int B = 0; B < nat; B++) P[B] = (T)1;
     for (int B = 0; B < nat; B++) {
-        T P = 1;
-        for (int C = 0; C < nat; C++) {
-            if (C == B) continue;
+        T PB = P[B];
+        for (int C = B + 1; C < nat; C++) {
             T mu = (dist[B] - dist[C]) * invR[B * nat + C];
             T f = mu;
             for (int it = 0; it < b.becke_iters; it++) f = (T)1.5 * f - (T)0.5 * f * f * f;
-            P *= (T)0.5 * ((T)1 - f);
+            PB *= (T)0.5 * ((T)1 - f);
+            P[C] *= (T)0.5 * ((T)1 + f);
         }
-        sumP += P;
-        if (B == A) PA = P;
+        P[B] = PB;
     }
+    T sumP = 0;
+    for (int B = 0; B < nat; B++) sumP += P[B];
+    const T PA = P[A];
     gx[gp] = ox; gy[gp] = oy; gz[gp] = oz;
     gw[gp] = (T)(wr * wa) * PA / sumP;
 }
