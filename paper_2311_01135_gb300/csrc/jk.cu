@@ -15,9 +15,10 @@
 // partial vectors at the end (Section 5, "Current (Naive) Bottleneck").  Here
 // one thread block owns one slice of one molecule's rows: D sits once in shared
 // memory, a warp walks one row pq (lanes take consecutive rs), the row-local
-// J'_PQ terms are reduced across the warp by shuffles, the scattered terms go
-// to shared-memory accumulators, and the block adds its J'/K' to the
-// molecule's global accumulators once at the end.
+// J'_PQ terms are reduced across the warp by shuffles, the K' terms that a run
+// of kets with the same R shares are summed across that run's lanes, the
+// remaining scattered terms go to shared-memory accumulators, and the block
+// adds its J'/K' to the molecule's global accumulators once at the end.
 #include "common.cuh"
 #include "eri.cuh"
 #include "kernels.h"
@@ -27,9 +28,12 @@
 // TA: arithmetic type of the contributions; TACC: accumulator (double, or
 // the fixed-point Fx of the mixed iterations, whose sums do not depend on the
 // order of the atomic adds).
+// The K'_PR and K'_QR blocks are handed back in kpr_o / kqr_o for the
+// caller's reduction over the run of kets that share R.
 template <typename TS, typename TA, typename TACC, int LA, int LB, int LC, int LD>
 __device__ __forceinline__ void jk_block(const TS *__restrict__ v, TA scale, int a0, int b0, int c0, int d0,
-                                         const TA *Ds, TACC *Js, TACC *Ks, int n, TA *jpq) {
+                                         const TA *Ds, TACC *Js, TACC *Ks, int n, TA *jpq, TA (&kpr_o)[3][3],
+                                         TA (&kqr_o)[3][3]) {
     constexpr int na = LA ? 3 : 1, nb = LB ? 3 : 1, nc = LC ? 3 : 1, nd = LD ? 3 : 1;
     TA Drs[nc][nd], Dpq[na][nb], Dqs[nb][nd], Dps[na][nd], Dqr[nb][nc], Dpr[na][nc];
 #pragma unroll
@@ -81,11 +85,11 @@ __device__ __forceinline__ void jk_block(const TS *__restrict__ v, TA scale, int
 #pragma unroll
     for (int i = 0; i < na; i++)
 #pragma unroll
-        for (int k = 0; k < nc; k++) acc_add(&Ks[(a0 + i) * n + c0 + k], kpr[i][k]);
+        for (int k = 0; k < nc; k++) kpr_o[i][k] = kpr[i][k];
 #pragma unroll
     for (int j = 0; j < nb; j++)
 #pragma unroll
-        for (int k = 0; k < nc; k++) acc_add(&Ks[(b0 + j) * n + c0 + k], kqr[j][k]);
+        for (int k = 0; k < nc; k++) kqr_o[j][k] = kqr[j][k];
 #pragma unroll
     for (int i = 0; i < na; i++)
 #pragma unroll
@@ -153,7 +157,7 @@ template <typename TS, typename TA, typename TACC>
 __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS_MAX) * 32)
     jk_kernel(DevBatch b, int nchunk, int mode, int max_pair, int CH, int pairs_in_smem) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int m = blockIdx.y, c = blockIdx.x;
+    const int m = blockIdx.y;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
     const int n = md.nbf, nn = n * n;
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
         pinfo = (uint32_t *)(smem_raw + o);
         o += ((size_t)max_pair * sizeof(uint32_t) + 15) & ~(size_t)15;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     TS *stg = (TS *)(smem_raw + o) + (size_t)warp * CH;
     const double *D = b.mat + md.mat0 + (long long)M_D * nn;
     for (int i = threadIdx.x; i < nn; i += blockDim.x) {
@@ -213,11 +217,14 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
             bool keep = false;
             uint32_t ki = 0;
             int nel = 0;
-            if (s <= r && qpq * kq[s] >= TAU_SCHWARZ) {
+            if (s <= r) {
                 ki = pairs_in_smem ? pinfo[s] : pair_of(s);
-                keep = true;
-                nel = npq * ((ki >> 14) & 1 ? 3 : 1) * ((ki >> 15) & 1 ? 3 : 1);
+                if (qpq * kq[s] >= TAU_SCHWARZ) {
+                    keep = true;
+                    nel = npq * ((ki >> 14) & 1 ? 3 : 1) * ((ki >> 15) & 1 ? 3 : 1);
+                }
             }
+            TA kpr_o[3][3] = {}, kqr_o[3][3] = {};
             int x = nel;  // inclusive prefix sum of block sizes over the chunk
             for (int o2 = 1; o2 < 32; o2 <<= 1) {
                 int y = __shfl_up_sync(0xffffffffu, x, o2);
@@ -232,12 +239,12 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
                 const int c0 = ki & 127, d0 = (ki >> 7) & 127;
                 const int cls = (lP << 3) | (lQ << 2) | (((ki >> 14) & 1) << 1) | ((ki >> 15) & 1);
                 switch (cls) {
-                case 0x0: jk_block<TS, TA, TACC, 0, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0x8: jk_block<TS, TA, TACC, 1, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xA: jk_block<TS, TA, TACC, 1, 0, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xC: jk_block<TS, TA, TACC, 1, 1, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xE: jk_block<TS, TA, TACC, 1, 1, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
-                case 0xF: jk_block<TS, TA, TACC, 1, 1, 1, 1>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq); break;
+                case 0x0: jk_block<TS, TA, TACC, 0, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq, kpr_o, kqr_o); break;
+                case 0x8: jk_block<TS, TA, TACC, 1, 0, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq, kpr_o, kqr_o); break;
+                case 0xA: jk_block<TS, TA, TACC, 1, 0, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq, kpr_o, kqr_o); break;
+                case 0xC: jk_block<TS, TA, TACC, 1, 1, 0, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq, kpr_o, kqr_o); break;
+                case 0xE: jk_block<TS, TA, TACC, 1, 1, 1, 0>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq, kpr_o, kqr_o); break;
+                case 0xF: jk_block<TS, TA, TACC, 1, 1, 1, 1>(v, scale, a0, b0, c0, d0, Ds, Js, Ks, n, jpq, kpr_o, kqr_o); break;
                 default: break;
                 }
             };
@@ -259,6 +266,37 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
                 __syncwarp();
                 const unsigned pend = __ballot_sync(0xffffffffu, lane >= first && !mine && !big);
                 first = pend ? __ffs(pend) - 1 : 32;
+            }
+            {
+                // K'_PR and K'_QR target shell R's columns, and kets are sorted
+                // by (class, R, S): a run of lanes shares R and would hit the
+                // same shared-memory words.  Sum each run across its lanes
+                // (segmented scan in a fixed lane order, so the sum does not
+                // depend on which warp takes the row) and let its last lane add.
+                const int key = s <= r ? (int)(ki & 127) : 128 + lane;  // AO start of R
+                const int prv = __shfl_up_sync(0xffffffffu, key, 1), nxt = __shfl_down_sync(0xffffffffu, key, 1);
+                const bool tail = lane == 31 || nxt != key;
+                const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prv != key);
+                const int lo = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+                const int ncm = __any_sync(0xffffffffu, s <= r && ((ki >> 14) & 1)) ? 3 : 1;
+                const int nc = (ki >> 14) & 1 ? 3 : 1, c0 = ki & 127;
+                const int na = lP ? 3 : 1, nbq = lQ ? 3 : 1;
+#pragma unroll
+                for (int i = 0; i < 6; i++)
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        const bool onq = i >= 3;
+                        const int ii = onq ? i - 3 : i;
+                        if (ii >= (onq ? nbq : na) || k >= ncm) continue;  // warp-uniform
+                        TA x = onq ? kqr_o[ii][k] : kpr_o[ii][k];
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const TA y = __shfl_up_sync(0xffffffffu, x, d);
+                            if (lane - d >= lo) x += y;
+                        }
+                        if (tail && s <= r && k < nc && x != (TA)0)
+                            acc_add(&Ks[((onq ? b0 : a0) + ii) * n + c0 + k], x);
+                    }
             }
             base += tot;
         }
