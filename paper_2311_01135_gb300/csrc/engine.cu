@@ -601,7 +601,7 @@ extern "C" int rks_batch_setup(rks_batch *b) {
     if (d.fixlist) { StageScope sc(c, s, "fix_list", 0); launch_fix_list(d, s); }
     { StageScope sc(c, s, "grid_build", 0); launch_grid_build(d, b->nblk_total, b->blk_mol, c->rad, c->ang, b->max_atoms, s); }
     { StageScope sc(c, s, "scf_init", 0); launch_scf_init(d, s); }
-    { StageScope sc(c, s, "scf_guess", 0); launch_scf_guess(d, s); }
+    { StageScope sc(c, s, "scf_guess", 0); launch_scf_guess(d, b->max_nbf, s); }
     int rc = check_launch("setup kernels");
     if (rc) return rc;
     b->it_enq = 0;
@@ -667,7 +667,7 @@ static int enqueue_one_iter(rks_batch *b) {
     int rc = fock_pass(b, fp64_iter, 0);
     if (rc) return rc;
     StageScope sc(b->ctx, b->stream, "scf_step", 0);
-    launch_scf_step(b->d, fp64_iter, b->stream);
+    launch_scf_step(b->d, fp64_iter, b->max_nbf, b->stream);
     return check_launch("scf step");
 }
 
@@ -719,7 +719,7 @@ static int enqueue_final(rks_batch *b) {
     int rc = fock_pass(b, 1, 1);
     if (rc) return rc;
     StageScope sc(b->ctx, b->stream, "scf_final", 0);
-    launch_scf_final(b->d, 1, b->stream);
+    launch_scf_final(b->d, 1, b->max_nbf, b->stream);
     b->st_valid = false;
     return check_launch("final");
 }

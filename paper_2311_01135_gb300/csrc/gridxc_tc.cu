@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar1, bar2[2];
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_fail, s_nsig, s_nset;
+    __shared__ int s_fail, s_nset;
     __shared__ __align__(16) int owner_h[TC_BP];
     __shared__ int sig[TC_NSHMAX];        // shell significant somewhere in this block
     __shared__ unsigned blk_r[4];         // radius range of the block per owner (float bits)
@@ -320,7 +320,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
         const int p0 = blk * TC_BP;
         const int own0 = min(p0 / npa, md.natom - 1);
         if (t < 4) blk_r[t] = (t & 1) ? 0u : 0x7f800000u;  // lo = +inf, hi = 0 per owner
-        if (t == 0) s_nsig = 0;
         __syncthreads();
         if (t < TC_BP) {
             const int h = min((p0 + t) / npa, md.natom - 1) - own0;
@@ -354,6 +353,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
         }
         __syncthreads();
         // ---- shell significance from the block's radius range (one thread per shell)
+        bool sig_t = false;
         if (t < nsh) {
             const int s = t;
             float rmin = 3.4e38f;
@@ -378,11 +378,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                 on = bound > (FINAL ? TC_SCREEN_FINAL : TC_SCREEN);
             }
             sig[s] = on;
-            if (on) atomicAdd(&s_nsig, 1);
+            sig_t = on;
         }
-        __syncthreads();
-        const int nsig = s_nsig;
-        __syncthreads();  // s_nsig is reset at the top of the next block
+        const int nsig = __syncthreads_count(sig_t);
         if (nsig == 0) continue;  // every AO below the screen: rho under the XC cutoff everywhere
         any_block = true;
         for (int mu = t; mu < np; mu += blockDim.x) aoc[mu] = -1;

@@ -37,9 +37,9 @@ void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, in
                        cudaStream_t s);
 // Per-molecule FP64 SCF stages.
 void launch_scf_init(const DevBatch &b, cudaStream_t s);
-void launch_scf_guess(const DevBatch &b, cudaStream_t s);
-void launch_scf_step(const DevBatch &b, int acc_fp64, cudaStream_t s);
-void launch_scf_final(const DevBatch &b, int acc_fp64, cudaStream_t s);
+void launch_scf_guess(const DevBatch &b, int max_nbf, cudaStream_t s);
+void launch_scf_step(const DevBatch &b, int acc_fp64, int max_nbf, cudaStream_t s);
+void launch_scf_final(const DevBatch &b, int acc_fp64, int max_nbf, cudaStream_t s);
 void launch_fock_only(const DevBatch &b, int acc_fp64, cudaStream_t s);
 void launch_reset_exc(const DevBatch &b, cudaStream_t s);
 void launch_count_active(const DevBatch &b, int *out, cudaStream_t s);

@@ -28,19 +28,24 @@ struct ScfSmem {
     int *perm;
 };
 
-__device__ inline ScfSmem scf_smem(unsigned char *raw) {
+// A and V are sized for the batch's largest basis nmax (not the compiled
+// cap), so that two or three molecules' blocks share an SM: the step is
+// latency-bound FP64 work and gains from the extra resident warps.
+__device__ inline ScfSmem scf_smem(unsigned char *raw, int nmax) {
     ScfSmem s;
     double *d = (double *)raw;
     s.A = d;
-    s.V = d + RKS_NBF_CAP * RKS_NBF_CAP;
-    s.w = s.V + RKS_NBF_CAP * RKS_NBF_CAP;
+    s.V = d + nmax * nmax;
+    s.w = s.V + nmax * nmax;
     s.red = s.w + RKS_NBF_CAP;
     s.cs = s.red + 64;
     s.perm = (int *)(s.cs + 2 * RKS_NBF_CAP + 8);
     return s;
 }
-static const size_t SCF_SMEM = sizeof(double) * (2 * RKS_NBF_CAP * RKS_NBF_CAP + RKS_NBF_CAP + 64 + 2 * RKS_NBF_CAP + 8) +
-                               sizeof(int) * (3 * RKS_NBF_CAP + 8);
+static size_t scf_smem_bytes(int nmax) {
+    return sizeof(double) * (2 * (size_t)nmax * nmax + RKS_NBF_CAP + 64 + 2 * RKS_NBF_CAP + 8) +
+           sizeof(int) * (3 * RKS_NBF_CAP + 8);
+}
 
 // Diagonalise X^T F X (F global, n x n): eigenvalues -> w (shared), C = X C' -> Cout (global).
 // Warm start: with the previous eigenvectors Cp (global, orthogonal), Jacobi
@@ -127,9 +132,9 @@ __global__ void scf_init_kernel(DevBatch b) {
 void launch_scf_init(const DevBatch &b, cudaStream_t s) { scf_init_kernel<<<b.nmol, 256, 0, s>>>(b); }
 
 // ------------------------------------------- orthogonaliser + core guess
-__global__ void scf_guess_kernel(DevBatch b) {
+__global__ void scf_guess_kernel(DevBatch b, int nmax) {
     extern __shared__ unsigned char raw[];
-    ScfSmem sm = scf_smem(raw);
+    ScfSmem sm = scf_smem(raw, nmax);
     const int m = blockIdx.x;
     const MolDesc md = b.mol[m];
     const int n = md.nbf, nn = n * n;
@@ -191,9 +196,10 @@ __global__ void scf_guess_kernel(DevBatch b) {
     }
 }
 
-void launch_scf_guess(const DevBatch &b, cudaStream_t s) {
-    cudaFuncSetAttribute(scf_guess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
-    scf_guess_kernel<<<b.nmol, 256, SCF_SMEM, s>>>(b);
+void launch_scf_guess(const DevBatch &b, int max_nbf, cudaStream_t s) {
+    const size_t sm = scf_smem_bytes(max_nbf);
+    cudaFuncSetAttribute(scf_guess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    scf_guess_kernel<<<b.nmol, 256, sm, s>>>(b, max_nbf);
 }
 
 // ----------------------------------------------------- Fock assembly
@@ -230,9 +236,9 @@ __device__ double assemble_fock(const DevBatch &b, int m, const MolDesc &md, con
 
 // ------------------------------------------------------------ one step
 template <typename TA>
-__global__ void scf_step_kernel(DevBatch b, const TA *accbase) {
+__global__ void scf_step_kernel(DevBatch b, const TA *accbase, int nmax) {
     extern __shared__ unsigned char raw[];
-    ScfSmem sm = scf_smem(raw);
+    ScfSmem sm = scf_smem(raw, nmax);
     const int m = blockIdx.x;
     const MolDesc &md = b.mol[m];
     MolState &st = b.st[m];
@@ -401,14 +407,15 @@ __global__ void scf_step_kernel(DevBatch b, const TA *accbase) {
     }
 }
 
-void launch_scf_step(const DevBatch &b, int acc_fp64, cudaStream_t s) {
+void launch_scf_step(const DevBatch &b, int acc_fp64, int max_nbf, cudaStream_t s) {
     (void)acc_fp64;
+    const size_t sm = scf_smem_bytes(max_nbf);
     if (b.precision == 0) {
-        cudaFuncSetAttribute(scf_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
-        scf_step_kernel<double><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accd);
+        cudaFuncSetAttribute(scf_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        scf_step_kernel<double><<<b.nmol, 256, sm, s>>>(b, b.accd, max_nbf);
     } else {
-        cudaFuncSetAttribute(scf_step_kernel<Fx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
-        scf_step_kernel<Fx><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accx);
+        cudaFuncSetAttribute(scf_step_kernel<Fx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        scf_step_kernel<Fx><<<b.nmol, 256, sm, s>>>(b, b.accx, max_nbf);
     }
 }
 
@@ -417,9 +424,9 @@ void launch_scf_step(const DevBatch &b, int acc_fp64, cudaStream_t s) {
 // eps, HOMO/LUMO, and the output density (written over M_D; the input
 // density is kept in M_TMP3).
 template <typename TA>
-__global__ void scf_final_kernel(DevBatch b, const TA *accbase) {
+__global__ void scf_final_kernel(DevBatch b, const TA *accbase, int nmax) {
     extern __shared__ unsigned char raw[];
-    ScfSmem sm = scf_smem(raw);
+    ScfSmem sm = scf_smem(raw, nmax);
     const int m = blockIdx.x;
     const MolDesc &md = b.mol[m];
     MolState &st = b.st[m];
@@ -451,14 +458,15 @@ __global__ void scf_final_kernel(DevBatch b, const TA *accbase) {
     }
 }
 
-void launch_scf_final(const DevBatch &b, int acc_fp64, cudaStream_t s) {
+void launch_scf_final(const DevBatch &b, int acc_fp64, int max_nbf, cudaStream_t s) {
     (void)acc_fp64;  // the accumulator type follows the precision: FP64 path double, mixed fixed point
+    const size_t sm = scf_smem_bytes(max_nbf);
     if (b.precision == 0) {
-        cudaFuncSetAttribute(scf_final_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
-        scf_final_kernel<double><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accd);
+        cudaFuncSetAttribute(scf_final_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        scf_final_kernel<double><<<b.nmol, 256, sm, s>>>(b, b.accd, max_nbf);
     } else {
-        cudaFuncSetAttribute(scf_final_kernel<Fx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCF_SMEM);
-        scf_final_kernel<Fx><<<b.nmol, 256, SCF_SMEM, s>>>(b, b.accx);
+        cudaFuncSetAttribute(scf_final_kernel<Fx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        scf_final_kernel<Fx><<<b.nmol, 256, sm, s>>>(b, b.accx, max_nbf);
     }
 }
 
