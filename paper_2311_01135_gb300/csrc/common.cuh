@@ -36,7 +36,6 @@ struct MolDesc {
 // FP64 matrices of one molecule, each nbf*nbf, at mat0 + slot * nbf*nbf.
 enum MatSlot {
     M_S = 0, M_T, M_V, M_H, M_X, M_D, M_F, M_C, M_J, M_K, M_VXC, M_FX, M_TMP1, M_TMP2, M_TMP3,
-    M_CP,     // eigenvectors of the previous X^T F X (unused when cold-started)
     M_DIIS_F, // RKS_DIIS_MAX matrices
     M_DIIS_E = M_DIIS_F + RKS_DIIS_MAX,
     M_COUNT = M_DIIS_E + RKS_DIIS_MAX
@@ -55,7 +54,7 @@ struct MolState {
     int converged;
     int status;             // RKS_STATUS_*
     int eigh_fail;
-    int cp_valid;           // M_CP holds the eigenvectors of the previous X^T F X
+    int c_valid;            // M_C holds the previous step's coefficients (warm-started diagonalisation)
     int err_flag;           // device-side bounds / consistency failures
     int n_quartets;
     int near_ties;

@@ -59,19 +59,35 @@ __device__ inline double block_max(double v, double *red) {
 
 // Symmetric eigendecomposition A = V diag(w) V^T by cyclic Jacobi with the
 // round-robin ("tournament") ordering: each step applies n/2 disjoint plane
-// rotations at once (rows, then columns), a sweep has n-1 steps.
+// rotations at once, a sweep has n-1 steps.  Position 0 stays, positions
+// 1..ne-1 rotate by one per step; pair k of a step joins positions k and
+// ne-1-k.
 // Rotation per pair (p, q) (Rutishauser's form): theta = (a_qq - a_pp)/(2 a_pq),
 // t = sgn(theta)/(|theta| + sqrt(theta^2 + 1)), c = 1/sqrt(1 + t^2), s = t c.
-// A (destroyed) and V live in shared memory; on return w (shared, n) holds the
-// eigenvalues in ascending order and V's columns the matching eigenvectors.
+// A step is one pass: the pairs split A into 2x2 blocks (rows of pair k1,
+// columns of pair k2), each transformed as J_k1^T B J_k2 by one thread; the
+// blocks with k1 < k2 also write their transpose, so A stays exactly
+// symmetric and only the upper block triangle is computed.  V <- V J in the
+// same pass.
+// A (symmetrised, then destroyed) and V live in shared memory; on return w
+// (shared, n) holds the eigenvalues in ascending order and V's columns the matching eigenvectors.
 // scratch: shared ints/doubles of size >= 3 * RKS_NBF_CAP.  Returns the sweep
 // count, or -1 when max_sweeps was exhausted before convergence.
 __device__ inline int jacobi(double *A, double *V, double *w, int n, double *red, int *perm,
                              double *cs, int max_sweeps = 40) {
     const int ne = n + (n & 1);  // even count; index n is a dummy when n is odd
     const int npair = ne / 2;
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) V[i] = (i / n == i % n) ? 1.0 : 0.0;
-    for (int i = threadIdx.x; i < ne; i += blockDim.x) perm[i] = i;
+    const int nblk = npair * (npair + 1) / 2;
+    // the block update reads one triangle: make A exactly symmetric first
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx % n;
+        V[idx] = i == j ? 1.0 : 0.0;
+        if (i < j) {
+            const double v = 0.5 * (A[idx] + A[j * n + i]);
+            A[idx] = v;
+            A[j * n + i] = v;
+        }
+    }
     __syncthreads();
     double *cc = cs, *ss = cs + RKS_NBF_CAP / 2 + 1;
     int *pp = perm + RKS_NBF_CAP + 2, *qq = pp + RKS_NBF_CAP / 2 + 1;
@@ -88,7 +104,10 @@ __device__ inline int jacobi(double *A, double *V, double *w, int n, double *red
         if (off <= 1e-30 * dia || off == 0.0) break;
         for (int step = 0; step < ne - 1; step++) {
             for (int k = threadIdx.x; k < npair; k += blockDim.x) {
-                int p = perm[k], q = perm[ne - 1 - k];
+                // index at position i after `step` rotations
+                const int ik = ne - 1 - k;
+                int p = k == 0 ? 0 : (k - 1 - step + 2 * (ne - 1)) % (ne - 1) + 1;
+                int q = (ik - 1 - step + 2 * (ne - 1)) % (ne - 1) + 1;
                 if (p > q) { int t = p; p = q; q = t; }
                 double c = 1.0, s = 0.0;
                 if (q < n) {
@@ -104,36 +123,48 @@ __device__ inline int jacobi(double *A, double *V, double *w, int n, double *red
                 cc[k] = c; ss[k] = s; pp[k] = p; qq[k] = q;
             }
             __syncthreads();
-            // rows: row_p <- c row_p - s row_q; row_q <- s row_p + c row_q
-            for (int idx = threadIdx.x; idx < npair * n; idx += blockDim.x) {
-                int k = idx / n, j = idx % n;
-                int p = pp[k], q = qq[k];
-                if (q >= n || ss[k] == 0.0) continue;
-                double c = cc[k], s = ss[k];
-                double ap = A[p * n + j], aq = A[q * n + j];
-                A[p * n + j] = c * ap - s * aq;
-                A[q * n + j] = s * ap + c * aq;
-            }
-            __syncthreads();
-            // columns of A and V
-            for (int idx = threadIdx.x; idx < npair * n; idx += blockDim.x) {
-                int k = idx / n, i = idx % n;
-                int p = pp[k], q = qq[k];
-                if (q >= n || ss[k] == 0.0) continue;
-                double c = cc[k], s = ss[k];
-                double ap = A[i * n + p], aq = A[i * n + q];
-                A[i * n + p] = c * ap - s * aq;
-                A[i * n + q] = s * ap + c * aq;
-                double vp = V[i * n + p], vq = V[i * n + q];
-                V[i * n + p] = c * vp - s * vq;
-                V[i * n + q] = s * vp + c * vq;
-            }
-            __syncthreads();
-            // rotate positions 1..ne-1
-            if (threadIdx.x == 0) {
-                int last = perm[ne - 1];
-                for (int i = ne - 1; i > 1; i--) perm[i] = perm[i - 1];
-                perm[1] = last;
+            for (int idx = threadIdx.x; idx < nblk + npair * n; idx += blockDim.x) {
+                if (idx < nblk) {
+                    // block (k1, k2), k1 <= k2, from the triangular index
+                    int k2 = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+                    while (k2 * (k2 + 1) / 2 > idx) k2--;
+                    while ((k2 + 1) * (k2 + 2) / 2 <= idx) k2++;
+                    const int k1 = idx - k2 * (k2 + 1) / 2;
+                    const double s1 = ss[k1], s2 = ss[k2];
+                    if (s1 == 0.0 && s2 == 0.0) continue;
+                    const double c1 = cc[k1], c2 = cc[k2];
+                    const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
+                    const bool r1 = q1 < n, r2 = q2 < n;  // q is the dummy index when n is odd
+                    const double bpp = A[p1 * n + p2], bpq = r2 ? A[p1 * n + q2] : 0.0;
+                    const double bqp = r1 ? A[q1 * n + p2] : 0.0, bqq = r1 && r2 ? A[q1 * n + q2] : 0.0;
+                    // rows of pair k1, then columns of pair k2
+                    const double tpp = c1 * bpp - s1 * bqp, tpq = c1 * bpq - s1 * bqq;
+                    const double tqp = s1 * bpp + c1 * bqp, tqq = s1 * bpq + c1 * bqq;
+                    const double upp = c2 * tpp - s2 * tpq, upq = s2 * tpp + c2 * tpq;
+                    const double uqp = c2 * tqp - s2 * tqq, uqq = s2 * tqp + c2 * tqq;
+                    if (k1 == k2) {  // diagonal block: p1 = p2, q1 = q2
+                        A[p1 * n + p1] = upp;
+                        if (r1) {
+                            A[p1 * n + q1] = upq;
+                            A[q1 * n + p1] = upq;
+                            A[q1 * n + q1] = uqq;
+                        }
+                    } else {
+                        A[p1 * n + p2] = upp; A[p2 * n + p1] = upp;
+                        if (r2) { A[p1 * n + q2] = upq; A[q2 * n + p1] = upq; }
+                        if (r1) { A[q1 * n + p2] = uqp; A[p2 * n + q1] = uqp; }
+                        if (r1 && r2) { A[q1 * n + q2] = uqq; A[q2 * n + q1] = uqq; }
+                    }
+                } else {
+                    // columns p, q of V
+                    const int j = idx - nblk, k = j / n, i = j % n;
+                    const int p = pp[k], q = qq[k];
+                    if (q >= n || ss[k] == 0.0) continue;
+                    const double c = cc[k], s = ss[k];
+                    const double vp = V[i * n + p], vq = V[i * n + q];
+                    V[i * n + p] = c * vp - s * vq;
+                    V[i * n + q] = s * vp + c * vq;
+                }
             }
             __syncthreads();
         }

@@ -47,46 +47,23 @@ static size_t scf_smem_bytes(int nmax) {
            sizeof(int) * (3 * RKS_NBF_CAP + 8);
 }
 
-// Diagonalise X^T F X (F global, n x n): eigenvalues -> w (shared), C = X C' -> Cout (global).
-// Warm start: with the previous eigenvectors Cp (global, orthogonal), Jacobi
-// runs on Cp^T (X^T F X) Cp, which is nearly diagonal after the first SCF
-// iterations, and C' = Cp V; the new C' is written back to Cp.
-__device__ int diag_fock(const double *F, const double *X, double *tmp, double *Cout, ScfSmem &sm, int n,
-                         double *Cp = nullptr, bool warm = false) {
-    la::gemm(tmp, F, X, n, false, false);
+// Diagonalise F in the Loewdin basis: eigenvalues -> w (shared), C = X C'
+// (global, in/out).
+// Cold start: Jacobi on X^T F X, then C = X V.
+// Warm start (C holds the previous step's coefficients, so C^T S C = I):
+// Jacobi on C^T F C, which is X^T F X in the previous eigenvector basis and
+// nearly diagonal after the first SCF iterations, then C <- C V.  This is
+// the cold form with C' = C'_prev V, for half the FP64 products.
+__device__ int diag_fock(const double *F, const double *X, double *tmp, double *C, ScfSmem &sm, int n, bool warm) {
+    const double *B = warm ? C : X;
+    la::gemm(tmp, F, B, n, false, false);
     __syncthreads();
-    la::gemm(sm.A, X, tmp, n, true, false);
-    __syncthreads();
-    if (warm) {
-        la::gemm(tmp, sm.A, Cp, n, false, false);
-        __syncthreads();
-        la::gemm(sm.A, Cp, tmp, n, true, false);
-        __syncthreads();
-    }
-    // exact symmetry before Jacobi
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        int i = idx / n, j = idx % n;
-        if (i < j) {
-            double v = 0.5 * (sm.A[i * n + j] + sm.A[j * n + i]);
-            sm.A[i * n + j] = v;
-            sm.A[j * n + i] = v;
-        }
-    }
+    la::gemm(sm.A, B, tmp, n, true, false);
     __syncthreads();
     int sw = la::jacobi(sm.A, sm.V, sm.w, n, sm.red, sm.perm, sm.cs);
-    if (warm) {
-        la::gemm(tmp, Cp, sm.V, n, false, false);  // C' = Cp V
-        __syncthreads();
-        for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-            Cp[i] = tmp[i];
-            sm.V[i] = tmp[i];
-        }
-        __syncthreads();
-    } else if (Cp) {
-        for (int i = threadIdx.x; i < n * n; i += blockDim.x) Cp[i] = sm.V[i];
-        __syncthreads();
-    }
-    la::gemm(Cout, X, sm.V, n, false, false);
+    la::gemm(tmp, B, sm.V, n, false, false);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) C[i] = tmp[i];
     __syncthreads();
     return sw;
 }
@@ -125,7 +102,7 @@ __global__ void scf_init_kernel(DevBatch b) {
         st.Enuc = e;
         st.E = 0.0; st.E_prev = 0.0; st.Exc = 0.0; st.max_err = 0.0;
         st.diis_n = 0; st.diis_head = 0; st.iter = 0; st.active = 1; st.converged = 0;
-        st.status = RKS_STATUS_OK_; st.eigh_fail = 0; st.cp_valid = 0;
+        st.status = RKS_STATUS_OK_; st.eigh_fail = 0; st.c_valid = 0;
     }
 }
 
@@ -159,7 +136,7 @@ __global__ void scf_guess_kernel(DevBatch b, int nmax) {
     int sw2 = 0;
     if (b.guess == 1) {
         // core Hamiltonian: diagonalise X^T H X, occupy the lowest n_occ
-        sw2 = diag_fock(H, X, tmp, C, sm, n, b.mat + md.mat0 + (long long)M_CP * nn, false);
+        sw2 = diag_fock(H, X, tmp, C, sm, n, false);
         density_from_C(C, D, n, md.nocc);
     } else {
         // superposed neutral atoms: per heavy atom D_ss = 2 S_ss^-1 over (1s, 2s)
@@ -192,7 +169,7 @@ __global__ void scf_guess_kernel(DevBatch b, int nmax) {
         if (smin < 1e-8) st.status = RKS_STATUS_S_ILL_;
         if (sw < 0 || sw2 < 0) st.eigh_fail++;
         for (int i = 0; i < n; i++) st.eps[i] = sm.w[i];
-        st.cp_valid = (b.guess == 1);
+        st.c_valid = (b.guess == 1);
     }
 }
 
@@ -390,12 +367,11 @@ __global__ void scf_step_kernel(DevBatch b, const TA *accbase, int nmax) {
         Fuse = FX;
     }
     // ---- diagonalise, new density
-    double *Cp = b.mat + md.mat0 + (long long)M_CP * nn;
-    int sw = diag_fock(Fuse, X, t1, C, sm, n, Cp, st.cp_valid != 0);
+    int sw = diag_fock(Fuse, X, t1, C, sm, n, st.c_valid != 0);
     density_from_C(C, D, n, md.nocc);
     if (threadIdx.x == 0) {
         if (sw < 0) st.eigh_fail++;
-        st.cp_valid = 1;
+        st.c_valid = 1;
         st.E_prev = E;
         st.iter += 1;
         for (int i = 0; i < n; i++) st.eps[i] = sm.w[i];
@@ -439,8 +415,7 @@ __global__ void scf_final_kernel(DevBatch b, const TA *accbase, int nmax) {
     double *t3 = b.mat + md.mat0 + (long long)M_TMP3 * nn;
     const double E = assemble_fock<TA>(b, m, md, accbase + md.acc0, sm.red);
     __syncthreads();
-    double *Cp = b.mat + md.mat0 + (long long)M_CP * nn;
-    int sw = diag_fock(F, X, t1, C, sm, n, Cp, st.cp_valid != 0);
+    int sw = diag_fock(F, X, t1, C, sm, n, st.c_valid != 0);
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) t3[idx] = D[idx];
     __syncthreads();
     density_from_C(C, D, n, md.nocc);
