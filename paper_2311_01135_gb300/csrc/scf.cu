@@ -5,8 +5,9 @@
 // is silent on them):
 //  * F = H + J - (a0/2) K_std + V_xc, a0 = 0.2 for B3LYP (1 in Hartree-Fock mode);
 //  * E = tr D (H + J/2 - a0 K_std/4) + E_xc + E_nuc;
-//  * X = S^-1/2 (Loewdin), X^T F X diagonalised by Jacobi, C = X C';
-//  * core-Hamiltonian guess;
+//  * X = S^-1/2 (Loewdin), X^T F X diagonalised by Jacobi, C = X C' (after the
+//    first step in the previous step's MO basis: C_prev^T F C_prev, C = C_prev V);
+//  * initial density from superposed neutral atoms (default) or the core Hamiltonian;
 //  * Pulay DIIS on e = X^T (F D S - S D F) X with the last diis_space pairs,
 //    used once two pairs exist; a singular bordered system drops the oldest pair;
 //  * convergence: |E - E_prev| < e_tol and max|e| < err_tol (converge protocol),
