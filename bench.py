@@ -7,14 +7,25 @@ sums).  One "step" = the whole method for the whole batch: integrals, Schwarz
 screening and packing, ERIs, grid, 20 iterations of J/K + XC + FP64
 DIIS/eigh, final step.
 
+The mixed path runs with the recheck: molecules whose DIIS error is still
+above 1e-4 after the 20 iterations run again from the initial guess with
+every Fock build at the final step's precision, and the unconverged ones
+(DIIS error above 1e-3) are redone on the FP64 path.
+
 Printed JSON line (rank 0):
-  value       molecules/s with inputs resident in HBM (CUDA events on the
-              library's stream around K steps)
+  value       molecules within the accuracy gate per second, inputs resident
+              in HBM (CUDA events on the library's stream around K steps)
+  gate        every molecule of the run against the plain FP64 GPU path
+              (itself pinned to the FP64 oracle by the parity tests): counts
+              over |dE| 1e-5 Ha and |d gap| 1e-4 Ha; a molecule outside the
+              gate does not count in value
   e2e         the same metric through the serving API (rks_submit / rks_wait /
               rks_result) with host buffers: H2D, every kernel and D2H inside
-  roofline    the dominant kernel's achieved rate vs the measured peak
+  latency_s   p50 / p99 of a short Poisson trace through the serving API
+  roofline    the dominant kernel's achieved rate vs the peak, measured by the
+              library's probes in the same run (peaks_probed_tflops)
   cpu_baseline  the FP64 oracle on the host cores (bounded sample)
-  fp64_gpu    the FP64 GPU path on a sample of the same molecules
+  fp64_gpu    the FP64 GPU path's molecules/s on the same molecules
 
 --impl reference times the FP64 oracle as the reference arm.
 Multi-GPU: molecules are independent, so N ranks run N independent shards
@@ -39,9 +50,9 @@ sys.path.insert(0, ROOT)
 import molgen  # noqa: E402
 
 # dram__bytes_read.sum + dram__bytes_write.sum of grid_xc_tc_kernel<float, 0>
-# per grid point (221.30 MB over the 13,363,200 points of the 38-molecule
-# capture); kept in step with the kernel: set to None when it changes
-GRID_TC_DRAM_BYTES_PER_POINT = 16.56
+# per grid point from one ncu capture of the current kernel (None until the
+# kernel as it stands has been captured); scaled by the points of a launch
+GRID_TC_DRAM_BYTES_PER_POINT = None
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
@@ -366,6 +377,109 @@ def validate_main(args):
 
 
 # ----------------------------------------------------------------- GPU leg
+# Mixed-precision options of the benchmark (and of every GPU leg below): the
+# fixed protocol, with molecules still moving after the 20 iterations run
+# again at the final step's precision (rks_options.recheck_err).
+RECHECK_ERR, RECHECK_FP64_ERR = 1e-4, 1e-3
+GATE_DE, GATE_DGAP = 1e-5, 1e-4
+
+
+def fp64_leg(g, mols, device, budget_s, chunk=512):
+    """The plain FP64 GPU path on the same molecules, in chunks, until every
+    molecule is done or the next chunk would overrun budget_s.  Returns the
+    per-molecule results (None where not run) and molecules/s."""
+    import torch
+    res = [None] * len(mols)
+    done, t_run = 0, 0.0
+    with g.Context(precision=g.RKS_FP64, fixed_iters=20, device=device) as c64:
+        s64 = torch.cuda.ExternalStream(c64.stream())
+        with g.Batch(c64, mols[:4]) as Bw:  # warm-up (module load, first launches)
+            Bw.run()
+            Bw.sync()
+        t_chunk = None
+        while done < len(mols):
+            if t_chunk is not None and t_run + t_chunk > budget_s:
+                break
+            sub = mols[done:done + chunk]
+            with g.Batch(c64, sub) as B64:
+                f0 = torch.cuda.Event(enable_timing=True)
+                f1 = torch.cuda.Event(enable_timing=True)
+                f0.record(s64)
+                B64.setup()
+                B64.run()
+                f1.record(s64)
+                B64.sync()
+                ms = f0.elapsed_time(f1)
+                for k in range(len(sub)):
+                    res[done + k] = B64.result(k)
+            t_run += ms / 1e3
+            t_chunk = ms / 1e3 * (chunk / len(sub))
+            done += len(sub)
+    return res, done / t_run if t_run > 0 else None, t_run
+
+
+def gate_report(rmx, r64):
+    """Mixed vs FP64 GPU (the FP64 path is itself pinned to the oracle at
+    ~1e-10 Ha by the parity tests) on every molecule both ran."""
+    pairs = [(a, b) for a, b in zip(rmx, r64) if b is not None]
+    dE = np.array([abs(a["E"] - b["E"]) for a, b in pairs])
+    dg = np.array([abs(a["gap"] - b["gap"]) for a, b in pairs])
+    bad_status = sum(1 for a, b in pairs if a["status"] != "ok" or b["status"] != "ok")
+    fail = (dE > GATE_DE) | (dg > GATE_DGAP)
+    return {"n_checked": len(pairs), "n_dE_over_1e-5": int((dE > GATE_DE).sum()),
+            "n_dgap_over_1e-4": int((dg > GATE_DGAP).sum()), "n_fail": int(fail.sum()),
+            "max_abs_dE": float(dE.max()) if len(dE) else None,
+            "max_abs_dgap": float(dg.max()) if len(dg) else None,
+            "p99_abs_dE": float(np.percentile(dE, 99)) if len(dE) else None,
+            "status_not_ok": bad_status, "n_rerun_precise": int(sum(1 for a in rmx if a["rechecked"] == 1)),
+            "n_redone_fp64": int(sum(1 for a in rmx if a["rechecked"] == 2)),
+            "passed": bool(len(pairs) and not fail.any() and bad_status == 0)}
+
+
+def serve_leg(g, mols, rate, device):
+    """A short Poisson trace of the workload's molecules through the serving
+    API (rks_submit / rks_wait / rks_result), the benchmark's protocol:
+    latency = submit -> result published, p50 / p99."""
+    rng = np.random.default_rng(2 + int(rate))
+    t_arr = np.cumsum(rng.exponential(1.0 / rate, size=len(mols)))
+    with g.Context(precision=g.RKS_MIXED, fixed_iters=20, recheck_err=RECHECK_ERR,
+                   recheck_fp64_err=RECHECK_FP64_ERR, device=device, admit_wait_us=2000) as ctx:
+        for tk in ctx.submit_many(mols[:8]):  # module load, not measured
+            ctx.wait(tk, 600)
+            ctx.result(tk)
+        tickets, t_sub = [None] * len(mols), [0.0] * len(mols)
+        t0 = time.perf_counter()
+        for i, m in enumerate(mols):
+            dt = t_arr[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            t_sub[i] = time.perf_counter() - t0
+            tickets[i] = ctx.submit(*m)
+        lat, done = [], []
+        for i, tk in enumerate(tickets):
+            ctx.wait(tk, 3600)
+            r = ctx.result(tk)
+            lat.append(r["latency_s"])
+            done.append(t_sub[i] + r["latency_s"])
+    return {"rate_per_s": rate, "n": len(mols), "sustained_mol_per_s": len(mols) / (max(done) - t_sub[0]),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "protocol": "fixed 20 iterations + recheck + final step, Poisson arrivals"}
+
+
+def measured_peaks(g, ctx):
+    """TF32 tensor, FP32 and FP64 FMA peaks measured now by the library's
+    probes (rks_probe_peak), TFLOP/s."""
+    out = {}
+    for name, kind in (("tf32_mma", g.RKS_PROBE_TF32_MMA), ("fp32_fma", g.RKS_PROBE_FP32_FMA),
+                       ("fp64_fma", g.RKS_PROBE_FP64_FMA)):
+        try:
+            out[name] = ctx.probe_peak(kind) / 1e12
+        except Exception as e:  # noqa: BLE001 - report, do not fail the bench
+            out[name] = None
+            out[name + "_error"] = str(e)[:200]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,7 +487,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--nmol", type=int, default=4096)
-    ap.add_argument("--fp64-sample", type=int, default=64)
+    ap.add_argument("--fp64-budget-s", type=float, default=1800.0,
+                    help="time allowed for the FP64 GPU comparison (every molecule when it fits)")
+    ap.add_argument("--serve-leg-n", type=int, default=1500)
+    ap.add_argument("--serve-leg-rate", type=float, default=200.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="one step with per-stage times")
@@ -407,7 +524,8 @@ def main():
     allm = workload(args.nmol * world)
     mols = [allm[i] for i in shard_indices(args.nmol, rank, world)]
     nmol = len(mols)
-    ctx = g.Context(precision=g.RKS_MIXED, fixed_iters=20, device=local)
+    ctx = g.Context(precision=g.RKS_MIXED, fixed_iters=20, recheck_err=RECHECK_ERR,
+                    recheck_fp64_err=RECHECK_FP64_ERR, device=local)
     stream = torch.cuda.ExternalStream(ctx.stream())
     B = g.Batch(ctx, mols)  # H2D of the inputs happens here (outside the timed region)
 
@@ -452,16 +570,10 @@ def main():
     ck = clocks.stop()
     ms_max = max_over_ranks(ms)
     ms_per_step = ms_max / args.steps
-    value = nmol * world / (ms_per_step / 1e3)
-
-    # accuracy check of this run on a few molecules is done by the tests; here
-    # report the spread of results for sanity
-    res = [B.result(m) for m in range(min(nmol, 8))]
-    n_bad = sum(1 for r in res if r["status"] != "ok")
+    rmx = [B.result(m) for m in range(nmol)]
 
     # ---- e2e through the serving API (host buffers)
     e2e = None
-    lat = []
     if not args.no_e2e:
         h2d = sum(len(Z) * (4 + 24) for Z, _ in mols)
         d2h = 0
@@ -473,41 +585,29 @@ def main():
         t1 = time.perf_counter()
         for r in out:
             d2h += 8 * (r["nbf"] + r["nbf"] ** 2) + 96
-            lat.append(r["latency_s"])
         e2e = {"value": nmol * world / (t1 - t0), "unit": "molecules/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
-    # ---- FP64 GPU path on a sample of the same molecules
-    fp64 = None
-    if args.fp64_sample > 0:
-        sub = mols[:args.fp64_sample]
-        with g.Context(precision=g.RKS_FP64, fixed_iters=20, device=local) as c64:
-            s64 = torch.cuda.ExternalStream(c64.stream())
-            with g.Batch(c64, sub[:4]) as Bw:  # warm-up (module load, first launches)
-                Bw.run()
-                Bw.sync()
-            with g.Batch(c64, sub) as B64:
-                f0 = torch.cuda.Event(enable_timing=True)
-                f1 = torch.cuda.Event(enable_timing=True)
-                f0.record(s64)
-                B64.setup()
-                B64.run()
-                f1.record(s64)
-                B64.sync()
-                fms = f0.elapsed_time(f1)
-                r64 = [B64.result(m) for m in range(len(sub))]
-        rmx = [B.result(m) for m in range(len(sub))]
-        dE = [abs(a["E"] - b["E"]) for a, b in zip(rmx, r64)]
-        dgap = [abs(a["gap"] - b["gap"]) for a, b in zip(rmx, r64)]
-        fp64 = {"value": len(sub) / (fms / 1e3), "unit": "molecules/s", "nmol": len(sub),
-                "mixed_vs_fp64_max_abs_dE": max(dE), "mixed_vs_fp64_max_abs_dgap": max(dgap)}
+    # ---- the accuracy gate: every molecule against the FP64 GPU path
+    r64, fp64_rate, fp64_s = fp64_leg(g, mols, local, args.fp64_budget_s)
+    gate = gate_report(rmx, r64)
+    fp64 = {"value": fp64_rate, "unit": "molecules/s", "nmol": gate["n_checked"], "wall_s": fp64_s}
+    n_fail = gate["n_fail"] + gate["status_not_ok"]
+    value = (nmol - n_fail) * world / (ms_per_step / 1e3)  # molecules within the gate per second
+
+    # ---- latency under Poisson arrivals (serving API)
+    serve = None
+    if args.serve_leg_n > 0:
+        serve = serve_leg(g, mols[:args.serve_leg_n], args.serve_leg_rate, local)
 
     # ---- roofline of the dominant kernel
     pk = peaks()
+    probes = measured_peaks(g, ctx)
     stages = {k: v for k, v in prof.items()}
     dom = max(stages, key=lambda k: stages[k]["ms"])
-    roof = roofline(dom, stages[dom], B, mols, pk)
-    others = {k: roofline(k, stages[k], B, mols, pk) for k in ("jk", "grid_xc_tc_final", "grid_xc_final")
+    roof = roofline(dom, stages[dom], B, mols, pk, probes)
+    others = {k: roofline(k, stages[k], B, mols, pk, probes)
+              for k in ("jk", "grid_xc_tc", "grid_xc_tc_final", "jk_final", "grid_xc_final")
               if k in stages and k != dom}
 
     cpu = None
@@ -520,10 +620,9 @@ def main():
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": workload_config(nmol, world),
                 "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roof, "roofline_other": others,
-                "cpu_baseline": cpu,
-                "fp64_gpu": fp64, "status_not_ok_in_first8": n_bad,
-                "latency_s": {"p50": float(np.percentile(lat, 50)) if lat else None,
-                              "p99": float(np.percentile(lat, 99)) if lat else None},
+                "cpu_baseline": cpu, "gate": gate, "fp64_gpu": fp64,
+                "mixed_vs_fp64_speedup": (nmol / (ms_per_step / 1e3)) / fp64_rate if fp64_rate else None,
+                "latency_s": serve, "peaks_probed_tflops": probes,
                 "stages_ms": {k: round(v["ms"], 3) for k, v in stages.items()}}
         print(json.dumps(line), flush=True)
     B.close()
@@ -532,32 +631,37 @@ def main():
         tdist.destroy_process_group()
 
 
-def roofline(name, st, B, mols, pk):
-    """Algorithmic work of the dominant stage per launch / its mean launch time."""
+def roofline(name, st, B, mols, pk, probes):
+    """Algorithmic work of a stage per launch / its mean launch time, against
+    the peak of the unit that bounds it."""
     import paper_2311_01135_gb300 as g
     ms = st["ms"] / max(st["launches"], 1)
-    n = [g.rks_nbf(Z) for Z, _ in mols]
-    P = [len(Z) * 50 * 12 * 24 for Z, _ in mols]
-    flops = sum(4.0 * p * k * k for p, k in zip(P, n))  # rho: 2 P n^2 (Phi D), V_xc: 2 P n^2 (Phi^T X)
-    if name in ("grid_xc_tc", "grid_xc_tc_final"):
-        # the two contractions run on the tensor cores (3xTF32 split: 3 MMAs per
-        # product, counted once here); peak = TF32 dense, taken as the measured
-        # sustained bf16 figure x the nominal TF32 : BF16 ratio (1.1 : 2.25)
-        peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * 1.1 / 2.25
+    if name.startswith("grid_xc_tc"):
+        # both contractions (rho: T = Phi D, V_xc: Phi^T X) over the AOs
+        # significant in each 128-point block: 2 * 128 * n_sig^2 flops each,
+        # summed over blocks (counted once; the 3xTF32 split issues 3 MMAs each)
+        k = 9 if name.endswith("final") else 8
+        flops = sum(4.0 * B.dump(m, g.RKS_DUMP_SCALARS)[k] for m in range(len(mols)))
         ach = flops / (ms / 1e3) / 1e12
-        # DRAM bytes per launch: ncu capture of the iteration kernel on the
-        # first 38 molecules (profiles/grid_xc_tc_38mol_mixed.md), 16.56 B per
-        # grid point, scaled by the points of this launch
-        traffic = GRID_TC_DRAM_BYTES_PER_POINT * sum(P) / 1e9 if name == "grid_xc_tc" else None
+        peak = probes.get("tf32_mma")
+        src = "tcgen05 kind::tf32 dense, measured by rks_probe_peak in this run"
+        if not peak:
+            peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * 1.1 / 2.25
+            src = f"{pk['_source']} sustained bf16 x 1.1/2.25 (TF32 dense)"
+        traffic = GRID_TC_DRAM_BYTES_PER_POINT * sum(len(Z) * 50 * 12 * 24 for Z, _ in mols) / 1e9 \
+            if (name == "grid_xc_tc" and GRID_TC_DRAM_BYTES_PER_POINT) else None
         return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": traffic, "traffic_unit": "GB per launch",
-                "peak_source": f"{pk['_source']} sustained bf16 x 1.1/2.25 (TF32 dense)",
-                "units": "4 * points * nbf^2 per molecule per launch (rho and V_xc contractions)"}
+                "frac": ach / peak, "traffic": traffic, "traffic_unit": "GB per launch", "peak_source": src,
+                "units": "4 * sum over 128-point blocks of 128 n_sig^2 per molecule per launch "
+                         "(two contractions over the significant AOs)"}
     if name.startswith("grid_xc"):
-        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        n = [g.rks_nbf(Z) for Z, _ in mols]
+        P = [len(Z) * 50 * 12 * 24 for Z, _ in mols]
+        flops = sum(4.0 * p * k * k for p, k in zip(P, n))
+        peak = probes.get("fp32_fma") or 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         return {"kernel": name, "bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+                "peak_source": "FP32 FMA measured by rks_probe_peak" if probes.get("fp32_fma") else "derived"}
     if name.startswith("jk"):
         nbytes = 0.0
         for m in range(len(mols)):

@@ -99,34 +99,69 @@ typedef struct rks_options {
                                are recomputed in FP64 and replace their FP32 store values in J/K;
                                0 disables; default 0.1 */
     int32_t grid_tc;        /* RKS_MIXED: 1 = grid contractions on the tensor cores (tcgen05, 3xTF32)
-                               when every molecule has nbf <= 80 and <= 60 shells (default);
-                               0 = the CUDA-core grid kernel */
+                               for each molecule with nbf <= 80 and <= 60 shells, decided per
+                               molecule (default); the others, and every molecule when 0, take
+                               the CUDA-core grid kernel */
     int32_t guess;          /* initial density: RKS_GUESS_SAD (default) or RKS_GUESS_CORE */
     int32_t max_cohorts;    /* serving: most batches ("cohorts") in flight at once, each on its own
                                stream, default 4 */
     int32_t admit_wait_us;  /* serving: while other cohorts run, a partial cohort (fewer than
                                max_slots molecules) is admitted once its oldest request has waited
                                this long (microseconds), default 20000 */
-    int32_t grid_chunks;    /* thread blocks per molecule of the grid kernels (0 = tuned default, 16);
-                               changes the grouping of the V_xc sums, so results move at ~1e-7 */
-    int32_t jk_chunks;      /* thread blocks per molecule of the J/K kernel (0 = tuned default, 8);
-                               results are bit-identical for any value */
+    int32_t grid_chunks;    /* thread blocks per molecule of the grid kernels (0 = default: 16 on the
+                               mixed path; on the FP64 path 16, or more for batches too small to
+                               fill the GPU); changes the grouping of the V_xc sums, so mixed
+                               results move at ~1e-7 */
+    int32_t jk_chunks;      /* thread blocks per molecule of the J/K kernel (0 = default: 8, or more
+                               for batches too small to fill the GPU); results are bit-identical
+                               for any value on the mixed path */
+    int32_t iter_precision; /* RKS_MIXED: precision of the Fock builds inside the SCF iterations,
+                               bit flags: RKS_ITER_JK_FINAL = J/K as in the final step (FP64
+                               products and the FP64 recompute of the largest quartets),
+                               RKS_ITER_GRID_FINAL = grid pass as in the final step (density
+                               contraction on the CUDA cores); default 0 (both at iteration
+                               precision) */
+    int32_t pad1;
+    double recheck_err;     /* RKS_MIXED, fixed protocol: a molecule whose DIIS error max|e|
+                               after the fixed iterations exceeds recheck_err is run again from
+                               the initial guess, the same number of iterations, with both Fock
+                               builds at the final step's precision, before the final step;
+                               0 disables.  A molecule's decision depends on it alone.
+                               Default 1e-4 */
+    double recheck_fp64_err; /* RKS_MIXED, fixed protocol: a molecule whose DIIS error after the
+                               fixed iterations exceeds recheck_fp64_err, or whose status is not
+                               OK, has not converged and is redone on the FP64 path (paper
+                               Section 3.2, "Numerical Error": the float32 results stand for the
+                               converged molecules, the rest are recomputed in float64); its
+                               result is the FP64 path's.  The redo runs as a batch of its own
+                               on its own stream, beside the precise reruns and the final step.
+                               0 disables.  Default 1e-3 */
 } rks_options;
 
+#define RKS_ITER_JK_FINAL 1
+#define RKS_ITER_GRID_FINAL 2
+
+/* One molecule's outputs: the labels the paper's dataset records per
+ * conformer (Section 4: energy, HOMO, LUMO, HL gap) and the SCF bookkeeping
+ * of Section 3.1's iteration. */
 typedef struct rks_result_t {
     int32_t status;   /* RKS_STATUS_* */
-    int32_t nbf;      /* basis size */
-    int32_t n_occ;    /* doubly occupied orbitals */
-    int32_t iters;    /* SCF iterations run (excluding the final step) */
-    double e_total;   /* total energy (Ha) at the last density */
-    double e_homo;    /* eps[n_occ - 1] */
+    int32_t nbf;      /* basis size N of Section 3.1 (STO-3G, Section 3.3) */
+    int32_t n_occ;    /* doubly occupied orbitals, N_electrons/2 (the D_ii = 2 entries of Eq. 1) */
+    int32_t iters;    /* SCF iterations run (Section 3.1's iteration i), excluding the final step */
+    double e_total;   /* total energy (Ha) of the density that entered the last Fock build */
+    double e_homo;    /* eps[n_occ - 1]: eps of Eq. 1, ascending */
     double e_lumo;    /* eps[n_occ] */
-    double gap;       /* e_lumo - e_homo */
-    double e_xc;      /* exchange-correlation energy (no exact-exchange part) */
+    double gap;       /* HL gap of Section 3.1, reported as e_lumo - e_homo > 0 */
+    double e_xc;      /* exchange-correlation energy of the B3LYP V_XC of Eq. 1 (Section 3.2, "Libxc"),
+                         without the exact-exchange part carried by K */
     double e_nuc;     /* nuclear repulsion */
     double latency_s; /* submit -> done (serving API); batch wall time per molecule (batch API) */
-    int32_t paper_converged; /* std of the last 5 energies < 0.01 Ha (the paper's flag) */
-    int32_t pad;
+    int32_t paper_converged; /* the paper's convergence flag (Section 3.2, "Numerical Error",
+                                footnote): std of the last 5 energies < 0.01, taken in Ha */
+    int32_t rechecked;       /* 1: the molecule was run again at the final step's precision
+                                (rks_options.recheck_err); 2: redone on the FP64 path
+                                (rks_options.recheck_fp64_err) */
     double err_max;   /* max |X^T (F D S - S D F) X| of the last SCF iteration */
     double de_last;   /* |E_k - E_(k-1)| of the last SCF iteration */
 } rks_result_t;
@@ -144,8 +179,11 @@ const char *rks_last_error(rks_ctx *ctx);
 
 /* ------------------------------------------------------------ context */
 /* Create a context on options->device: allocates streams and the constant
- * tables (Boys function table), starts the serving worker thread.
- * Errors: RKS_EINVAL (bad options), RKS_ECUDA, RKS_ENOMEM. */
+ * tables (Boys function table of the integral code, Section 3.2 "Libcint";
+ * radial and angular quadrature tables of the grid), starts the serving
+ * worker thread.  options may be NULL (defaults); *out receives the context,
+ * owned by the caller until rks_destroy.
+ * Errors: RKS_EINVAL (bad options), RKS_ECUDA (no device), RKS_ENOMEM. */
 int rks_create(const rks_options *options, rks_ctx **out);
 /* Stops the worker (queued and in-flight tickets are failed), frees device memory. */
 int rks_destroy(rks_ctx *ctx);
@@ -153,8 +191,10 @@ int rks_destroy(rks_ctx *ctx);
 void *rks_stream(rks_ctx *ctx);
 
 /* ------------------------------------------------------- serving API */
-/* Queue one molecule.  Non-blocking: copies Z[natom] and xyz[natom*3]
- * (row-major) and returns a ticket.  Continuous batching: the worker thread
+/* Queue one molecule: the inputs of a DFT computation, atomic numbers and
+ * positions (Section 3.1), to be run through the iteration of Eq. 1.
+ * Non-blocking: copies Z[natom] and xyz[natom*3] (row-major) and returns a
+ * ticket in *ticket_out.  Continuous batching: the worker thread
  * keeps up to max_cohorts batches in flight, each on its own CUDA stream, and
  * admits queued molecules as a new cohort whenever the HBM budget has room
  * (a full cohort at once, a partial one when the GPU is idle or the oldest
@@ -174,11 +214,15 @@ int rks_submit(rks_ctx *ctx, int32_t natom, const int32_t *Z, const double *xyz,
  * RKS_EAGAIN. */
 int rks_submit_batch(rks_ctx *ctx, int32_t nmol, const int32_t *natom, const int32_t *Z,
                      const double *xyz, uint64_t *tickets_out);
-/* Non-blocking state query: RKS_PENDING / RKS_RUNNING / RKS_DONE / RKS_FAILED. */
+/* Non-blocking state query of a ticket from rks_submit: *state_out gets
+ * RKS_PENDING (queued), RKS_RUNNING (its cohort is in Section 3.1's
+ * iterations), RKS_DONE or RKS_FAILED.  Errors: RKS_EINVAL, RKS_ENOTFOUND. */
 int rks_poll(rks_ctx *ctx, uint64_t ticket, int32_t *state_out);
 /* Block the calling host thread until the ticket is done or timeout_s passes. */
 int rks_wait(rks_ctx *ctx, uint64_t ticket, double timeout_s);
-/* Copy the result of a finished ticket and release it.  eps_out (nbf values,
+/* Copy the result of a finished ticket and release it: the energy, the
+ * orbital energies eps and the density rho = C D C^T of Eq. 1 (Section 3.1),
+ * HOMO, LUMO and gap (the labels of Section 4).  eps_out (nbf values,
  * ascending) and D_out (nbf*nbf, the output total density) may be NULL;
  * cap_nbf is their capacity in basis functions (RKS_EINVAL if smaller than
  * nbf).  Errors: RKS_ENOTREADY, RKS_ENOTFOUND; for a failed ticket (released
@@ -195,26 +239,33 @@ int rks_result(rks_ctx *ctx, uint64_t ticket, rks_result_t *out, double *eps_out
  * Errors: RKS_EINVAL, RKS_ENOMEM, RKS_ECUDA. */
 int rks_batch_create(rks_ctx *ctx, int32_t nmol, const int32_t *natom, const int32_t *Z,
                      const double *xyz, rks_batch **out);
-/* Enqueue the whole method (integrals, grid, SCF iterations, final step) on
- * the context stream and return without waiting (for the converge protocol the
+/* Enqueue the whole method of Section 3.1 for every molecule of the batch
+ * (iteration 0: integrals incl. I^2e under its 8-fold symmetry, Section 3.2
+ * footnote, and the grid; then the SCF iterations and the final step) on the
+ * context stream and return without waiting.  For the converge protocol the
  * call reads the count of molecules still iterating every 4 iterations and
- * stops when it reaches zero). */
+ * stops when it reaches zero; with recheck_err set it reads the count of
+ * molecules to run again once, after the fixed iterations. */
 int rks_batch_run(rks_batch *b);
 /* Wait for the batch's work to finish; RKS_EDEVICE if a kernel reported a
  * bounded-wait or bounds failure. */
 int rks_batch_sync(rks_batch *b);
-/* Results of molecule m (after sync), same buffers as rks_result. */
+/* Results of molecule m (after sync), same buffers and fields as rks_result. */
 int rks_batch_result(rks_batch *b, int32_t m, rks_result_t *out, double *eps_out, double *D_out,
                      int32_t cap_nbf);
+/* Free the batch's device memory (waits for its work). */
 int rks_batch_destroy(rks_batch *b);
 
 /* ------------------------------------------------- stage-level entries */
-/* Run only the iteration-0 steps (one-electron integrals, Schwarz screening,
- * packing, ERIs, grid, orthogonaliser) for the batch. */
+/* Run only the iteration-0 steps of Section 3.1 (V, T, S, I^2e: one-electron
+ * integrals, Schwarz screening, packing, ERIs; the grid; the orthogonaliser
+ * and the initial density) for the batch. */
 int rks_batch_setup(rks_batch *b);
-/* With the batch set up, build F[D] for the given densities (one nbf*nbf
- * FP64 matrix per molecule, concatenated): J, K, V_xc, E_xc and E at D.
- * final_step = 1 uses the precision of the final correction. */
+/* With the batch set up, build the operator of Eq. 1 at the given densities
+ * rho (one nbf*nbf FP64 matrix per molecule, concatenated): J(rho), K(rho),
+ * V_XC(rho), E_xc and E at rho (read back with rks_batch_dump).
+ * final_step = 1 uses the precision of the final correction, 0 the
+ * iterations' precision (rks_options.iter_precision). */
 int rks_batch_fock(rks_batch *b, const double *D_all, int32_t final_step);
 
 /* Copy a per-molecule array out for inspection (parity tests).
@@ -235,7 +286,11 @@ int rks_batch_fock(rks_batch *b, const double *D_all, int32_t final_step);
 #define RKS_DUMP_F 12       /* last Fock matrix */
 #define RKS_DUMP_EPS 13     /* orbital energies [nbf] */
 #define RKS_DUMP_X 14       /* S^-1/2 */
-#define RKS_DUMP_SCALARS 15 /* double [8]: E, E_xc, E_nuc, n_pair_all, n_quartets, store elements, npts, near-tie count */
+#define RKS_DUMP_SCALARS 15 /* double [10]: E, E_xc, E_nuc, n_pair_all, n_quartets, store elements, npts,
+                               near-tie count, and the screened work of one tensor-core grid pass:
+                               sum over 128-point blocks of 128 n_sig^2 (n_sig: AOs significant in
+                               the block), iterations, final step (0 for molecules the tensor-core
+                               kernel does not take) */
 #define RKS_DUMP_QUARTETS 16 /* kept quartet count per row: int32 [npair] */
 int64_t rks_batch_dump(rks_batch *b, int32_t m, int32_t what, void *out, int64_t cap_bytes);
 
@@ -258,9 +313,26 @@ int rks_profile_read(rks_ctx *ctx, rks_stage_time *out, int32_t cap);
 int rks_eval_boys(rks_ctx *ctx, int32_t mmax, int32_t n, const double *T, double *out,
                   int32_t precision);
 /* B3LYP energy density and potentials (e, v_rho, v_sigma) at n points of
- * (rho, sigma = |grad rho|^2), by the device kernel.  Host buffers. */
+ * (rho, sigma = |grad rho|^2), by the device kernel (the V_XC of Eq. 1,
+ * Section 3.2 "Libxc").  Host buffers.  precision RKS_FP64 or RKS_MIXED
+ * (FP32), anything else RKS_EINVAL.  Allocates and frees device memory per
+ * call (see rks_eval_xc_noalloc for callers that cannot). */
 int rks_eval_xc(rks_ctx *ctx, int32_t n, const double *rho, const double *sigma, double *e,
                 double *v_rho, double *v_sigma, int32_t precision);
+
+/* ------------------------------------------------------ measurement */
+/* Peak rate of one operation on the context's device, measured by a probe
+ * kernel (the roofline denominators of kernels bound by that operation; the
+ * paper has no counterpart).  kind: RKS_PROBE_FP32_FMA or RKS_PROBE_FP64_FMA
+ * (flop/s, 2 per FMA, every SM full of independent FMA chains), or
+ * RKS_PROBE_TF32_MMA (flop/s of back-to-back dense tcgen05.mma kind::tf32,
+ * M = 128, N = 256, K = 8, on every SM).  Best of three timed launches after
+ * one warm-up, CUDA events on the context stream; synchronous, ~0.1 s.
+ * Errors: RKS_EINVAL (kind, null), RKS_ECUDA, RKS_EDEVICE (a bounded wait gave up). */
+#define RKS_PROBE_FP32_FMA 0
+#define RKS_PROBE_FP64_FMA 1
+#define RKS_PROBE_TF32_MMA 2
+int rks_probe_peak(rks_ctx *ctx, int32_t kind, double *ops_per_s);
 
 /* ------------------------------------------------------ diagnostics */
 /* Exercise the device-side failure path without a fault: one block waits on
@@ -285,8 +357,10 @@ int rks_selftest_bounded_wait(rks_ctx *ctx, int32_t spins);
  *    static array, with that device made current for the call); make it
  *    before any stream capture on that device.
  *  - The scratch is shared by every call in the process on that device:
- *    overlapping calls would race on it, so the library serialises them with
- *    a lock (a second thread waits for the first call to return).
+ *    overlapping calls would race on it, so the library serialises the calls
+ *    of one device with a lock (a second thread waits for the first call to
+ *    return, also when that call failed part way); calls on different
+ *    devices do not wait for each other.
  *  - Nothing needs to start at zero; the call is synchronous (returns with
  *    the outputs in the caller's host arrays). */
 #define RKS_XC_NOALLOC_MAX 65536

@@ -124,6 +124,12 @@ def solve_fock(F, X, nocc):
     return e, C, D
 
 
+def diis_error(F, D, S, X):
+    """Pulay's error matrix in the orthonormal (Loewdin) basis:
+    e = X^T (F D S - S D F) X, zero when F and D commute through S."""
+    return X.T @ (F @ D @ S - S @ D @ F) @ X
+
+
 class DIIS:
     def __init__(self, space=8):
         self.space = space
@@ -243,7 +249,7 @@ def run_scf(sysm: System, protocol="converge", n_iter=20, e_tol=1e-9, err_tol=1e
     for it in range(1, n + 1):
         F, E, _ = sysm.fock(D)
         energies.append(E)
-        err = sysm.X.T @ (F @ D @ sysm.S - sysm.S @ D @ F) @ sysm.X
+        err = diis_error(F, D, sysm.S, sysm.X)
         if protocol == "converge" and E_prev is not None:
             if abs(E - E_prev) < e_tol and np.max(np.abs(err)) < err_tol:
                 converged = True
@@ -263,7 +269,7 @@ def run_scf(sysm: System, protocol="converge", n_iter=20, e_tol=1e-9, err_tol=1e
     nocc = sysm.nocc
     homo = float(eps[nocc - 1])
     lumo = float(eps[nocc]) if nocc < len(eps) else float("nan")
-    err = sysm.X.T @ (F @ D @ sysm.S - sysm.S @ D @ F) @ sysm.X
+    err = diis_error(F, D, sysm.S, sysm.X)
     paper_flag = len(energies) >= 5 and float(np.std(energies[-5:])) < 0.01
     return dict(E=E, eps=eps, homo=homo, lumo=lumo, gap=lumo - homo, D=D_out, D_in=D,
                 C=C, F=F, iters=it, converged=converged if protocol == "converge" else None,

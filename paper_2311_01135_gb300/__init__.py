@@ -20,6 +20,8 @@ RKS_ECUDA, RKS_ETIMEOUT, RKS_ENOTFOUND, RKS_EDEVICE = -5, -6, -7, -8
 RKS_PENDING, RKS_RUNNING, RKS_DONE, RKS_FAILED = 0, 1, 2, 3
 RKS_FP64, RKS_MIXED = 0, 1
 RKS_GUESS_SAD, RKS_GUESS_CORE = 0, 1
+RKS_ITER_JK_FINAL, RKS_ITER_GRID_FINAL = 1, 2
+RKS_PROBE_FP32_FMA, RKS_PROBE_FP64_FMA, RKS_PROBE_TF32_MMA = 0, 1, 2
 RKS_XC_NOALLOC_MAX = 65536
 RKS_MAX_NBF = 96
 RKS_STATUS = {0: "ok", 1: "not_converged", 2: "nonfinite", 3: "s_ill", 4: "eigh"}
@@ -38,7 +40,9 @@ class rks_options(ctypes.Structure):
                 ("use_graphs", ctypes.c_int32), ("pad0", ctypes.c_int32), ("fix_theta", ctypes.c_double),
                 ("grid_tc", ctypes.c_int32), ("guess", ctypes.c_int32),
                 ("max_cohorts", ctypes.c_int32), ("admit_wait_us", ctypes.c_int32),
-                ("grid_chunks", ctypes.c_int32), ("jk_chunks", ctypes.c_int32)]
+                ("grid_chunks", ctypes.c_int32), ("jk_chunks", ctypes.c_int32),
+                ("iter_precision", ctypes.c_int32), ("pad1", ctypes.c_int32), ("recheck_err", ctypes.c_double),
+                ("recheck_fp64_err", ctypes.c_double)]
 
 
 class rks_result_t(ctypes.Structure):
@@ -46,7 +50,7 @@ class rks_result_t(ctypes.Structure):
                 ("iters", ctypes.c_int32), ("e_total", ctypes.c_double), ("e_homo", ctypes.c_double),
                 ("e_lumo", ctypes.c_double), ("gap", ctypes.c_double), ("e_xc", ctypes.c_double),
                 ("e_nuc", ctypes.c_double), ("latency_s", ctypes.c_double),
-                ("paper_converged", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("paper_converged", ctypes.c_int32), ("rechecked", ctypes.c_int32),
                 ("err_max", ctypes.c_double), ("de_last", ctypes.c_double)]
 
 
@@ -85,6 +89,7 @@ _SIGS = {
     "rks_eval_xc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32]),
     "rks_eval_xc_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32]),
     "rks_selftest_bounded_wait": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "rks_probe_peak": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -221,6 +226,12 @@ class Context:
                                precision), "rks_eval_xc")
         return e, vr, vs
 
+    def probe_peak(self, kind):
+        """rks_probe_peak: measured operations per second of RKS_PROBE_* kind."""
+        v = ctypes.c_double()
+        _chk(lib().rks_probe_peak(self.h, kind, ctypes.byref(v)), "rks_probe_peak")
+        return v.value
+
     def selftest_bounded_wait(self, spins=100000):
         """rks_selftest_bounded_wait: the return code (RKS_EDEVICE expected)."""
         return lib().rks_selftest_bounded_wait(self.h, spins)
@@ -239,7 +250,7 @@ def _res_dict(r, eps, D):
     return dict(status=RKS_STATUS.get(r.status, r.status), nbf=r.nbf, nocc=r.n_occ, iters=r.iters,
                 E=r.e_total, homo=r.e_homo, lumo=r.e_lumo, gap=r.gap, Exc=r.e_xc, Enuc=r.e_nuc,
                 latency_s=r.latency_s, paper_converged=bool(r.paper_converged), err_max=r.err_max,
-                de_last=r.de_last, eps=eps, D=D)
+                de_last=r.de_last, rechecked=int(r.rechecked), eps=eps, D=D)
 
 
 class Batch:

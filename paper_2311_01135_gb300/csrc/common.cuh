@@ -58,7 +58,10 @@ struct MolState {
     int err_flag;           // device-side bounds / consistency failures
     int n_quartets;
     int near_ties;
+    int rechecked;          // fixed protocol: 1 run again at the final step's precision, 2 redone in FP64
     long long n_elem;       // store elements written
+    double grid_pairs[2];   // sum over grid blocks of 128 n_sig^2 (n_sig: AOs significant in the
+                            // block), iterations / final step: the screened work of one grid pass
     double eps[RKS_NBF_CAP];
 };
 
@@ -138,6 +141,10 @@ struct DevBatch {
     double fix_theta;
     // grid (SoA, padded blocks; padding points have w = 0)
     void *gx, *gy, *gz, *gw;
+    // per 128-point block: shells significant in it, bit per shell (packing
+    // order), [2 * block] iterations, [2 * block + 1] final step; filled for
+    // the molecules the tensor-core grid kernel takes (mixed path), else null
+    unsigned long long *blk_mask;
     // FP64 matrices
     double *mat;
     // accumulators J', K', V' (3 * nbf^2 per molecule at acc0): 64-bit fixed
@@ -155,6 +162,8 @@ struct DevBatch {
     int fixed_iters, max_iters;
     int guess;              // 0 superposed atoms, 1 core Hamiltonian
     double e_tol, err_tol;
+    double recheck_err;     // fixed protocol: DIIS error above which a molecule is run again
+    double recheck_fp64_err; // and above which it is redone on the FP64 path
 };
 
 __host__ __device__ inline long long nbf2(int n) { return (long long)n * n; }

@@ -152,6 +152,9 @@ extern "C" int rks_options_default(rks_options *o) {
     o->guess = RKS_GUESS_SAD;
     o->max_cohorts = 4;
     o->admit_wait_us = 20000;
+    o->iter_precision = 0;
+    o->recheck_err = 1e-4;
+    o->recheck_fp64_err = 1e-3;
     return RKS_OK;
 }
 
@@ -199,6 +202,7 @@ struct rks_ctx {
     // pinned host words for asynchronous readbacks, one per live batch
     int *pin = nullptr;
     std::vector<int> pin_free;
+    int nsm = 152;              // multiprocessors of the device
 };
 static const int kPinSlots = 256;
 
@@ -289,12 +293,28 @@ struct rks_batch {
     double wall_s = 0.0;
     std::vector<MolState> st_host;
     bool st_valid = false;
-    cudaGraphExec_t graph = nullptr;   // one SCF iteration, captured on first use
+    // one SCF iteration per iteration precision (RKS_ITER_* flags), captured
+    // after one direct run of that launch sequence
+    cudaGraphExec_t graph[4] = {};
+    bool graph_warm[4] = {};
     bool graph_failed = false;
-    int pin_slot = -1;                 // ctx->pin word receiving the active count
+    int *recheck_d = nullptr;          // [2] molecules marked for the precise rerun / the FP64 redo
+    int *recheck_list = nullptr;       // [nmol] indices marked for the FP64 redo
+    // inputs kept for the FP64 redo of unconverged molecules (coordinates in bohr)
+    std::vector<int32_t> hZ, hnat;
+    std::vector<double> hxyz;
+    std::vector<long long> hatom0;
+    rks_batch *child = nullptr;        // FP64 batch of the molecules being redone
+    int *child_map = nullptr;          // device: child molecule -> parent molecule
+    cudaEvent_t child_done = nullptr;
+    int pin_slot = -1;                 // ctx->pin words 2 pin_slot, 2 pin_slot + 1: readbacks (active
+                                       // count; recheck counts)
     int *active_d = nullptr;
     int it_enq = 0;                    // SCF iterations enqueued so far
 };
+
+// The batch's two pinned host words for asynchronous readbacks.
+static int *pinw(const rks_batch *b) { return b->ctx->pin + 2 * b->pin_slot; }
 
 template <typename T> static int dalloc(rks_batch *b, T **p, size_t n) {
     void *q = nullptr;
@@ -324,9 +344,19 @@ static int validate(int natom, const int *Z, const double *xyz, int *nbf_out) {
     return RKS_OK;
 }
 
+static void child_free(rks_batch *b) {
+    if (b->child) rks_batch_destroy(b->child);
+    b->child = nullptr;
+    if (b->child_done) cudaEventDestroy(b->child_done);
+    b->child_done = nullptr;
+}
+
 extern "C" int rks_batch_destroy(rks_batch *b) {
     if (!b) return RKS_EINVAL;
-    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaStreamSynchronize(b->stream);  // an adopt kernel may still read the child
+    child_free(b);
+    for (auto &gx : b->graph)
+        if (gx) cudaGraphExecDestroy(gx);
     for (void *p : b->allocs) cudaFreeAsync(p, b->stream);
     cudaStreamSynchronize(b->stream);
     if (b->own_stream) cudaStreamDestroy(b->stream);
@@ -373,19 +403,24 @@ static size_t mol_bytes(const rks_options &o, int na, const int32_t *Z) {
     if (o.precision == RKS_MIXED && o.fix_theta > 0) b += (size_t)npair * 45 * 8 + 6 * (RKS_FIX_CAP * 16 + 4);
     b += (size_t)((store_cap(ns, np) + 3) & ~3LL) * esz;
     b += (size_t)nblk * RKS_PTS_BLOCK * 4 * esz + (size_t)nblk * 4;
+    if (o.precision == RKS_MIXED) b += (size_t)nblk * 16;  // grid block masks
     b += (size_t)nbf * nbf * (M_COUNT * 8 + 3 * 8);
     return b;
 }
 
+// precision: RKS_FP64 / RKS_MIXED, or -1 for the context's; bohr: coordinates
+// are already in bohr (the FP64 redo of a batch's molecules).
 static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, int32_t nmol, const int32_t *natom,
-                           const int32_t *Z, const double *xyz, rks_batch **out) {
+                           const int32_t *Z, const double *xyz, rks_batch **out, int precision = -1,
+                           bool bohr = false) {
     if (!ctx || nmol <= 0 || !natom || !Z || !xyz || !out) {
         if (own_stream) cudaStreamDestroy(stream);
         return fail(RKS_EINVAL, "null argument");
     }
     std::call_once(g_basis_once, init_basis);
-    const rks_options &o = ctx->opt;
-    const double conv = o.coords_in_angstrom ? 1.0 / 0.52917721092 : 1.0;
+    rks_options o = ctx->opt;
+    if (precision >= 0) o.precision = precision;
+    const double conv = (o.coords_in_angstrom && !bohr) ? 1.0 / 0.52917721092 : 1.0;
     rks_batch *b = new rks_batch();
     b->ctx = ctx;
     b->stream = stream;
@@ -449,6 +484,8 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
                 hsh_co.push_back(x.sd->c[k]);
             }
         }
+        b->hatom0.push_back((long long)hZ.size());
+        b->hnat.push_back(na);
         for (int i = 0; i < na; i++) {
             hZ.push_back(Zm[i]);
             for (int k = 0; k < 3; k++) haxyz.push_back(Xm[3 * i + k] * conv);
@@ -504,6 +541,8 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     d.guess = o.guess;
     d.e_tol = o.e_tol;
     d.err_tol = o.err_tol;
+    d.recheck_err = o.recheck_err;
+    d.recheck_fp64_err = o.recheck_fp64_err;
     d.boys64 = ctx->boys64;
     d.boys32 = ctx->boys32;
     const size_t esz = o.precision ? sizeof(float) : sizeof(double);
@@ -528,6 +567,8 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
         (rc = dalloc(b, (unsigned char **)&gz, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gw, pts_off * esz)) ||
         (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) ||
         (rc = dalloc(b, &b->blk_mol, b->nblk_total)) || (rc = dalloc(b, &b->active_d, 1)) ||
+        (rc = dalloc(b, &b->recheck_d, 2)) || (rc = dalloc(b, &b->recheck_list, nmol)) ||
+        (o.precision == RKS_MIXED && (rc = dalloc(b, &d.blk_mask, 2 * b->nblk_total))) ||
         (rc = dalloc(b, &d.jk_next, nmol))) {
         rks_batch_destroy(b);
         return rc;
@@ -561,6 +602,8 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     UP(dcm, hcand_mol);
     UP(b->blk_mol, hblk_mol);
 #undef UP
+    b->hZ = hZ;
+    b->hxyz = haxyz;
     cudaError_t e = cudaMemsetAsync(dst, 0, sizeof(MolState) * nmol, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(mat, 0, sizeof(double) * mat_off, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -600,8 +643,9 @@ extern "C" int rks_batch_setup(rks_batch *b) {
     { StageScope sc(c, s, "eri", 0); launch_eri_store(d, (int)b->ncand, fp32, s); }
     if (d.fixlist) { StageScope sc(c, s, "fix_list", 0); launch_fix_list(d, s); }
     { StageScope sc(c, s, "grid_build", 0); launch_grid_build(d, b->nblk_total, b->blk_mol, c->rad, c->ang, b->max_atoms, s); }
+    { StageScope sc(c, s, "grid_masks", 0); launch_grid_masks(d, b->nblk_total, b->blk_mol, s); }
     { StageScope sc(c, s, "scf_init", 0); launch_scf_init(d, s); }
-    { StageScope sc(c, s, "scf_guess", 0); launch_scf_guess(d, b->max_nbf, s); }
+    { StageScope sc(c, s, "scf_guess", 0); launch_scf_guess(d, b->max_nbf, 0, s); }
     int rc = check_launch("setup kernels");
     if (rc) return rc;
     b->it_enq = 0;
@@ -610,8 +654,11 @@ extern "C" int rks_batch_setup(rks_batch *b) {
     return RKS_OK;
 }
 
-// One Fock build for every (active when mode 0) molecule.
-static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
+// One Fock build for every (active when mode 0) molecule.  prec: RKS_ITER_*
+// flags; on the mixed path RKS_ITER_JK_FINAL forms the J/K products in FP64
+// and adds the FP64 recompute of the largest quartets, RKS_ITER_GRID_FINAL
+// forms the density on the CUDA cores (the final step uses both).
+static int fock_pass(rks_batch *b, int prec, int mode) {
     rks_ctx *c = b->ctx;
     cudaStream_t s = b->stream;
     const DevBatch &d = b->d;
@@ -621,16 +668,27 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
     launch_reset_exc(d, s);
     // blocks per molecule; J/K rows are shared out dynamically.  Defaults from
     // the autotuner (tune.py) on the 9-11-heavy-atom workload.
-    const int nchunk_jk = c->opt.jk_chunks > 0 ? c->opt.jk_chunks : 8;
+    // Thread blocks per molecule.  J/K sums in exact fixed point (mixed) or
+    // FP64 (FP64 path), so its block count only spreads small batches over
+    // the GPU (at least two blocks per multiprocessor).  The mixed grid
+    // kernels keep 16 per molecule, so that a molecule sums its points in the
+    // same groups in any batch; the FP64 path's grid sums reorder at ~1e-16
+    // and spread like J/K.  Defaults from the autotuner (tune.py) on the
+    // 9-11-heavy-atom workload.
+    const int spread = (2 * c->nsm + b->nmol - 1) / b->nmol;
+    const int nchunk_jk = c->opt.jk_chunks > 0 ? c->opt.jk_chunks : std::min(256, std::max(8, spread));
     CUDA_OK(cudaMemsetAsync(d.jk_next, 0, sizeof(int) * b->nmol, s));
+    const int jk_fin = b->precision == 0 || (prec & RKS_ITER_JK_FINAL);
+    const int gr_fin = b->precision == 0 || (prec & RKS_ITER_GRID_FINAL);
+    const char *jk_name = mode ? "jk_final" : (jk_fin ? "jk_precise" : "jk");
     {
-        StageScope sc(c, s, acc_fp64 ? "jk_final" : "jk", 0);
-        if (launch_jk(d, nchunk_jk, acc_fp64, mode, b->max_nbf, b->max_pair, s))
+        StageScope sc(c, s, jk_name, 0);
+        if (launch_jk(d, nchunk_jk, jk_fin, mode, b->max_nbf, b->max_pair, s))
             return fail(RKS_EINVAL, "basis too large for the J/K kernel's shared memory");
     }
-    if (acc_fp64 && b->precision == RKS_MIXED && d.fixlist) {
-        StageScope sc(c, s, "jk_fp64_fix", 0);
-        launch_jk_fix(d, s);
+    if (jk_fin && b->precision == RKS_MIXED && d.fixlist) {
+        StageScope sc(c, s, mode ? "jk_fp64_fix" : "jk_fp64_fix_it", 0);
+        launch_jk_fix(d, mode, s);
     }
     if (d.xc) {
         // Molecules that fit the tensor-core kernel (grid_tc_fits, decided per
@@ -647,14 +705,15 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
             }
             if (any_tc) {
                 const int nchunk_tc = c->opt.grid_chunks > 0 ? c->opt.grid_chunks : 16;
-                StageScope sc(c, s, acc_fp64 ? "grid_xc_tc_final" : "grid_xc_tc", 0);
-                launch_grid_xc_tc(d, nchunk_tc, acc_fp64, mode, b->max_nbf, b->max_nsh, s);
+                StageScope sc(c, s, mode ? "grid_xc_tc_final" : (gr_fin ? "grid_xc_tc_precise" : "grid_xc_tc"), 0);
+                launch_grid_xc_tc(d, nchunk_tc, gr_fin, mode, b->max_nbf, b->max_nsh, s);
             }
         }
         if (need_cc) {
-            const int nchunk_gx = c->opt.grid_chunks > 0 ? c->opt.grid_chunks : 16;
-            StageScope sc(c, s, acc_fp64 ? "grid_xc_final" : "grid_xc", 0);
-            launch_grid_xc(d, nchunk_gx, acc_fp64, mode, tc ? 1 : 0, b->max_nbf, b->max_nsh, s);
+            const int nchunk_gx = c->opt.grid_chunks > 0 ? c->opt.grid_chunks
+                                  : (b->precision == RKS_FP64 ? std::min(256, std::max(16, spread)) : 16);
+            StageScope sc(c, s, mode ? "grid_xc_final" : (gr_fin ? "grid_xc_precise" : "grid_xc"), 0);
+            launch_grid_xc(d, nchunk_gx, gr_fin, mode, tc ? 1 : 0, b->max_nbf, b->max_nsh, s);
         }
     }
     return check_launch("fock pass");
@@ -662,61 +721,124 @@ static int fock_pass(rks_batch *b, int acc_fp64, int mode) {
 
 // One SCF iteration for every molecule still iterating: Fock build and the
 // per-molecule step (DIIS, diagonalisation, density, convergence flags).
-static int enqueue_one_iter(rks_batch *b) {
-    const int fp64_iter = b->precision == 0;
-    int rc = fock_pass(b, fp64_iter, 0);
+static int enqueue_one_iter(rks_batch *b, int prec) {
+    int rc = fock_pass(b, prec, 0);
     if (rc) return rc;
     StageScope sc(b->ctx, b->stream, "scf_step", 0);
-    launch_scf_step(b->d, fp64_iter, b->max_nbf, b->stream);
+    launch_scf_step(b->d, b->precision == 0, b->max_nbf, b->stream);
     return check_launch("scf step");
 }
 
-// Enqueue n iterations.  The iteration is the same launch sequence every time
-// (inactive molecules are skipped by the kernels, not by the host), so after
-// the first one it is captured once as a CUDA graph and replayed; stage
-// profiling needs per-launch events and turns the graph off.
-static int enqueue_iters(rks_batch *b, int n) {
+// Enqueue n iterations at iteration precision prec.  The iteration is the
+// same launch sequence every time (inactive molecules are skipped by the
+// kernels, not by the host), so after one direct run it is captured once as a
+// CUDA graph and replayed; stage profiling needs per-launch events and turns
+// the graph off.
+static int enqueue_iters(rks_batch *b, int n, int prec) {
     rks_ctx *c = b->ctx;
     cudaStream_t s = b->stream;
     int rc;
+    prec &= 3;
     for (int k = 0; k < n; k++, b->it_enq++) {
-        const bool use_graph = c->opt.use_graphs && !c->prof && !b->graph_failed && b->it_enq > 0;
-        if (use_graph && !b->graph) {
+        const bool use_graph = c->opt.use_graphs && !c->prof && !b->graph_failed && b->graph_warm[prec];
+        cudaGraphExec_t &gx = b->graph[prec];
+        if (use_graph && !gx) {
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                rc = enqueue_one_iter(b);
+                rc = enqueue_one_iter(b, prec);
                 e = cudaStreamEndCapture(s, &g);
-                if (e == cudaSuccess && rc == RKS_OK) e = cudaGraphInstantiate(&b->graph, g, 0);
+                if (e == cudaSuccess && rc == RKS_OK) e = cudaGraphInstantiate(&gx, g, 0);
                 if (g) cudaGraphDestroy(g);
             }
-            if (e != cudaSuccess || !b->graph) {
+            if (e != cudaSuccess || !gx) {
                 // capture is an optimisation: fall back to direct launches
                 cudaGetLastError();
-                b->graph = nullptr;
+                gx = nullptr;
                 b->graph_failed = true;
             }
         }
-        if (b->graph && use_graph) {
-            CUDA_OK(cudaGraphLaunch(b->graph, s));
-        } else if ((rc = enqueue_one_iter(b))) {
-            return rc;
+        if (gx && use_graph) {
+            CUDA_OK(cudaGraphLaunch(gx, s));
+        } else {
+            if ((rc = enqueue_one_iter(b, prec))) return rc;
+            b->graph_warm[prec] = true;
         }
     }
     return RKS_OK;
 }
 
+// Iteration precision of the first pass: the option on the mixed path.
+static int iter_prec(const rks_batch *b) { return b->precision == RKS_MIXED ? (b->ctx->opt.iter_precision & 3) : 0; }
+static const int kPrecise = RKS_ITER_JK_FINAL | RKS_ITER_GRID_FINAL;
+
+static bool recheck_on(const rks_batch *b) {
+    return b->precision == RKS_MIXED && b->d.fixed_iters > 0 && (b->d.recheck_err > 0.0 || b->d.recheck_fp64_err > 0.0);
+}
+
+// Mark the molecules to run again (precise rerun, started from the initial
+// guess here) or to redo in FP64; the two counts go to the batch's pinned
+// words, the FP64 list to recheck_list.
+static int enqueue_recheck_start(rks_batch *b) {
+    cudaStream_t s = b->stream;
+    {
+        StageScope sc(b->ctx, s, "recheck_mark", 0);
+        launch_mark_recheck(b->d, b->recheck_d, b->recheck_list, s);
+    }
+    {
+        StageScope sc(b->ctx, s, "scf_guess", 0);
+        launch_scf_guess(b->d, b->max_nbf, 1, s);
+    }
+    CUDA_OK(cudaMemcpyAsync(pinw(b), b->recheck_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    return check_launch("recheck start");
+}
+
+// Start the FP64 redo of the n molecules in recheck_list (host-visible once
+// the marking has completed): a child batch on its own stream, whose work
+// overlaps the parent's precise rerun and final step.
+static int start_fp64_redo(rks_batch *b, int n) {
+    std::vector<int> list(n);
+    CUDA_OK(cudaMemcpy(list.data(), b->recheck_list, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    std::sort(list.begin(), list.end());
+    std::vector<int32_t> na, Z;
+    std::vector<double> xyz;
+    for (int m : list) {
+        na.push_back(b->hnat[m]);
+        Z.insert(Z.end(), b->hZ.begin() + b->hatom0[m], b->hZ.begin() + b->hatom0[m] + b->hnat[m]);
+        xyz.insert(xyz.end(), b->hxyz.begin() + 3 * b->hatom0[m], b->hxyz.begin() + 3 * (b->hatom0[m] + b->hnat[m]));
+    }
+    cudaStream_t cs = nullptr;
+    CUDA_OK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    int rc = batch_create_on(b->ctx, cs, true, n, na.data(), Z.data(), xyz.data(), &b->child, RKS_FP64, true);
+    if (rc) return rc;
+    if ((rc = dalloc(b->child, &b->child_map, n))) return rc;
+    CUDA_OK(cudaMemcpyAsync(b->child_map, list.data(), sizeof(int) * n, cudaMemcpyHostToDevice, cs));
+    if ((rc = rks_batch_run(b->child))) return rc;
+    CUDA_OK(cudaEventCreateWithFlags(&b->child_done, cudaEventDisableTiming));
+    CUDA_OK(cudaEventRecord(b->child_done, cs));
+    return RKS_OK;
+}
+
+// After the parent's final step: wait for the FP64 redo and take its results.
+static int enqueue_adopt(rks_batch *b) {
+    if (!b->child) return RKS_OK;
+    CUDA_OK(cudaStreamWaitEvent(b->stream, b->child_done, 0));
+    StageScope sc(b->ctx, b->stream, "recheck_adopt", 0);
+    launch_adopt(b->d, b->child->d, b->child_map, b->child->nmol, b->stream);
+    return check_launch("adopt");
+}
+
 // Count of molecules still iterating, copied to the batch's pinned word.
 static int enqueue_active_count(rks_batch *b) {
     launch_count_active(b->d, b->active_d, b->stream);
-    CUDA_OK(cudaMemcpyAsync(b->ctx->pin + b->pin_slot, b->active_d, sizeof(int), cudaMemcpyDeviceToHost,
+    CUDA_OK(cudaMemcpyAsync(pinw(b), b->active_d, sizeof(int), cudaMemcpyDeviceToHost,
                             b->stream));
     return check_launch("count active");
 }
 
 // Final step: every molecule, FP64 accumulation.
 static int enqueue_final(rks_batch *b) {
-    int rc = fock_pass(b, 1, 1);
+    int rc = fock_pass(b, kPrecise, 1);
     if (rc) return rc;
     StageScope sc(b->ctx, b->stream, "scf_final", 0);
     launch_scf_final(b->d, 1, b->max_nbf, b->stream);
@@ -732,17 +854,27 @@ extern "C" int rks_batch_run(rks_batch *b) {
     int rc;
     if (!b->set_up && (rc = rks_batch_setup(b))) return rc;
     const DevBatch &d = b->d;
+    const int prec = iter_prec(b);
+    child_free(b);
     if (d.fixed_iters > 0) {
-        if ((rc = enqueue_iters(b, d.fixed_iters))) return rc;
+        if ((rc = enqueue_iters(b, d.fixed_iters, prec))) return rc;
+        if (recheck_on(b)) {
+            if ((rc = enqueue_recheck_start(b))) return rc;
+            CUDA_OK(cudaStreamSynchronize(b->stream));
+            const int n_precise = pinw(b)[0], n_fp64 = pinw(b)[1];
+            if (n_fp64 > 0 && (rc = start_fp64_redo(b, n_fp64))) return rc;
+            if (n_precise > 0 && (rc = enqueue_iters(b, d.fixed_iters, kPrecise))) return rc;
+        }
     } else {
         while (b->it_enq < d.max_iters) {
-            if ((rc = enqueue_iters(b, std::min(kCheckEvery, d.max_iters - b->it_enq)))) return rc;
+            if ((rc = enqueue_iters(b, std::min(kCheckEvery, d.max_iters - b->it_enq), prec))) return rc;
             if ((rc = enqueue_active_count(b))) return rc;
             CUDA_OK(cudaStreamSynchronize(b->stream));
-            if (b->ctx->pin[b->pin_slot] == 0) break;
+            if (pinw(b)[0] == 0) break;
         }
     }
     if ((rc = enqueue_final(b))) return rc;
+    if ((rc = enqueue_adopt(b))) return rc;
     b->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return RKS_OK;
 }
@@ -772,7 +904,7 @@ extern "C" int rks_batch_fock(rks_batch *b, const double *D_all, int32_t final_s
         off += nn;
     }
     const int acc64 = final_step || b->precision == 0;
-    if ((rc = fock_pass(b, acc64, 1))) return rc;
+    if ((rc = fock_pass(b, final_step ? kPrecise : iter_prec(b), 1))) return rc;
     launch_fock_only(b->d, acc64, b->stream);
     b->st_valid = false;
     return check_launch("fock only");
@@ -815,6 +947,7 @@ extern "C" int rks_batch_result(rks_batch *b, int32_t m, rks_result_t *out, doub
     out->e_nuc = st.Enuc;
     out->latency_s = b->wall_s;
     out->paper_converged = paper_std(st) < 0.01;
+    out->rechecked = st.rechecked;
     out->err_max = st.max_err;
     out->de_last = st.iter >= 2 ? fabs(st.Ehist[(st.iter - 1) % RKS_NHIST] - st.Ehist[(st.iter - 2) % RKS_NHIST]) : 0.0;
     if (eps_out) memcpy(eps_out, st.eps, sizeof(double) * md.nbf);
@@ -917,55 +1050,84 @@ extern "C" int64_t rks_batch_dump(rks_batch *b, int32_t m, int32_t what, void *o
         return bytes;
     }
     case RKS_DUMP_SCALARS: {
-        if (cap < 64) return RKS_EINVAL;
+        if (cap < 80) return RKS_EINVAL;
         double *o = (double *)out;
         o[0] = st.E; o[1] = st.Exc; o[2] = st.Enuc; o[3] = md.npair_all; o[4] = st.n_quartets;
         o[5] = (double)st.n_elem; o[6] = md.npts; o[7] = st.near_ties;
-        return 64;
+        o[8] = st.grid_pairs[0]; o[9] = st.grid_pairs[1];
+        return 80;
     }
     default: return RKS_EINVAL;
     }
 }
 
 // -------------------------------------------------------- unit entries
+// Arguments of the unit entries, checked the same way by every variant.
+static int check_unit_precision(int32_t precision) {
+    if (precision != RKS_FP64 && precision != RKS_MIXED) return fail(RKS_EINVAL, "precision must be RKS_FP64 or RKS_MIXED");
+    return RKS_OK;
+}
+
 extern "C" int rks_eval_boys(rks_ctx *ctx, int32_t mmax, int32_t n, const double *T, double *out, int32_t precision) {
-    if (!ctx || n <= 0 || !T || !out || mmax < 0 || mmax > 4) return RKS_EINVAL;
-    double *dT, *dO;
-    CUDA_OK(cudaMalloc(&dT, n * sizeof(double)));
-    CUDA_OK(cudaMalloc(&dO, (size_t)n * (mmax + 1) * sizeof(double)));
-    // on the context stream: a legacy-stream copy from pageable memory may
-    // return before its DMA lands, and that stream does not order the kernel
-    CUDA_OK(cudaMemcpyAsync(dT, T, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    launch_boys_eval(mmax, n, dT, dO, precision == RKS_MIXED, ctx->boys64, ctx->boys32, ctx->stream);
-    CUDA_OK(cudaStreamSynchronize(ctx->stream));
-    CUDA_OK(cudaMemcpy(out, dO, (size_t)n * (mmax + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    if (!ctx || n <= 0 || !T || !out || mmax < 0 || mmax > 4) return fail(RKS_EINVAL, "null argument, n <= 0 or mmax");
+    int rc = check_unit_precision(precision);
+    if (rc) return rc;
+    double *dT = nullptr, *dO = nullptr;
+    cudaStream_t st = ctx->stream;
+    // every device step on the context stream: a legacy-stream copy from
+    // pageable memory may return before its DMA lands, and that stream does
+    // not order the kernel
+    cudaError_t e = cudaMalloc(&dT, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dO, (size_t)n * (mmax + 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dT, T, n * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        launch_boys_eval(mmax, n, dT, dO, precision == RKS_MIXED, ctx->boys64, ctx->boys32, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, dO, (size_t)n * (mmax + 1) * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    else cudaStreamSynchronize(st);  // nothing queued may still use the buffers freed below
     cudaFree(dT);
     cudaFree(dO);
-    return RKS_OK;
+    return e == cudaSuccess ? RKS_OK : rks_cuda_fail(e, "rks_eval_boys", __FILE__, __LINE__);
 }
 
 extern "C" int rks_eval_xc(rks_ctx *ctx, int32_t n, const double *rho, const double *sigma, double *e, double *vr,
                            double *vs, int32_t precision) {
-    if (!ctx || n <= 0 || !rho || !sigma || !e || !vr || !vs) return RKS_EINVAL;
-    double *dr, *ds, *dO;
-    CUDA_OK(cudaMalloc(&dr, n * sizeof(double)));
-    CUDA_OK(cudaMalloc(&ds, n * sizeof(double)));
-    CUDA_OK(cudaMalloc(&dO, 3ull * n * sizeof(double)));
-    CUDA_OK(cudaMemcpyAsync(dr, rho, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CUDA_OK(cudaMemcpyAsync(ds, sigma, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    launch_eval_xc(n, dr, ds, dO, precision == RKS_MIXED, ctx->stream);
-    CUDA_OK(cudaStreamSynchronize(ctx->stream));
-    std::vector<double> o(3ull * n);
-    CUDA_OK(cudaMemcpy(o.data(), dO, 3ull * n * sizeof(double), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < n; i++) {
-        e[i] = o[3 * i];
-        vr[i] = o[3 * i + 1];
-        vs[i] = o[3 * i + 2];
+    if (!ctx || n <= 0 || !rho || !sigma || !e || !vr || !vs) return fail(RKS_EINVAL, "null argument or n <= 0");
+    int rc = check_unit_precision(precision);
+    if (rc) return rc;
+    double *dr = nullptr, *ds = nullptr, *dO = nullptr;
+    cudaStream_t st = ctx->stream;
+    cudaError_t err = cudaMalloc(&dr, n * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&ds, n * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&dO, 3ull * n * sizeof(double));
+    if (err == cudaSuccess) err = cudaMemcpyAsync(dr, rho, n * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(ds, sigma, n * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess) {
+        launch_eval_xc(n, dr, ds, dO, precision == RKS_MIXED, st);
+        err = cudaGetLastError();
     }
+    double *outs[3] = {e, vr, vs};
+    for (int k = 0; k < 3 && err == cudaSuccess; k++)
+        err = cudaMemcpy2DAsync(outs[k], sizeof(double), dO + k, 3 * sizeof(double), sizeof(double), n,
+                                cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    else cudaStreamSynchronize(st);  // drain before the buffers are freed
     cudaFree(dr);
     cudaFree(ds);
     cudaFree(dO);
-    return RKS_OK;
+    return err == cudaSuccess ? RKS_OK : rks_cuda_fail(err, "rks_eval_xc", __FILE__, __LINE__);
+}
+
+extern "C" int rks_probe_peak(rks_ctx *ctx, int32_t kind, double *ops_per_s) {
+    if (!ctx || !ops_per_s || kind < RKS_PROBE_FP32_FMA || kind > RKS_PROBE_TF32_MMA)
+        return fail(RKS_EINVAL, "null argument or unknown probe kind");
+    CUDA_OK(cudaSetDevice(ctx->opt.device));
+    int rc = probe_rate(kind, ctx->stream, ops_per_s);
+    if (rc == RKS_EDEVICE) return fail(rc, "probe: bounded wait gave up");
+    return rc;
 }
 
 extern "C" int rks_selftest_bounded_wait(rks_ctx *ctx, int32_t spins) {
@@ -992,8 +1154,9 @@ extern "C" int rks_selftest_bounded_wait(rks_ctx *ctx, int32_t spins) {
 // element a call reads was written earlier in that call.
 static __device__ __align__(256) double g_xc_scratch[5 * RKS_XC_NOALLOC_MAX];
 
-static std::mutex g_xc_scratch_mu;           // one scratch per device: calls are serialised
-static double *g_xc_scratch_ptr[64] = {};    // device address per ordinal, looked up on first use
+#define RKS_MAX_DEVICES 64
+static std::mutex g_xc_scratch_mu[RKS_MAX_DEVICES];      // one scratch per device: its calls are serialised
+static double *g_xc_scratch_ptr[RKS_MAX_DEVICES] = {};   // device address per ordinal, looked up on first use
 
 extern "C" int rks_eval_xc_noalloc(rks_ctx *ctx, int32_t n, const double *rho, const double *sigma, double *e,
                                    double *vr, double *vs, int32_t precision) {
@@ -1001,14 +1164,14 @@ extern "C" int rks_eval_xc_noalloc(rks_ctx *ctx, int32_t n, const double *rho, c
     if (n > RKS_XC_NOALLOC_MAX)
         return fail(RKS_EINVAL, "n = " + std::to_string(n) + " exceeds the static scratch (RKS_XC_NOALLOC_MAX = " +
                                     std::to_string(RKS_XC_NOALLOC_MAX) + " points)");
-    if (precision != RKS_FP64 && precision != RKS_MIXED) return fail(RKS_EINVAL, "bad precision");
+    int rc = check_unit_precision(precision);
+    if (rc) return rc;
     const int dev = ctx->opt.device;
-    if (dev < 0 || dev >= 64) return fail(RKS_EINVAL, "device ordinal out of range");
-    std::lock_guard<std::mutex> lk(g_xc_scratch_mu);
+    if (dev < 0 || dev >= RKS_MAX_DEVICES) return fail(RKS_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_xc_scratch_mu[dev]);
     int prev = 0;
     CUDA_OK(cudaGetDevice(&prev));
     if (prev != dev) CUDA_OK(cudaSetDevice(dev));
-    int rc = RKS_OK;
     double *base = g_xc_scratch_ptr[dev];
     cudaError_t err = cudaSuccess;
     if (!base) {
@@ -1029,7 +1192,11 @@ extern "C" int rks_eval_xc_noalloc(rks_ctx *ctx, int32_t n, const double *rho, c
         for (int k = 0; k < 3 && err == cudaSuccess; k++)
             err = cudaMemcpy2DAsync(outs[k], sizeof(double), dO + k, 3 * sizeof(double), sizeof(double), n,
                                     cudaMemcpyDeviceToHost, st);
+        // on an error after the first enqueue, drain the stream anyway: the
+        // lock is released on return, and the next holder must find the
+        // scratch idle
         if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        else cudaStreamSynchronize(st);
     }
     if (err != cudaSuccess) rc = rks_cuda_fail(err, "rks_eval_xc_noalloc", __FILE__, __LINE__);
     if (prev != dev) cudaSetDevice(prev);
@@ -1049,7 +1216,8 @@ extern "C" int rks_eval_xc_noalloc(rks_ctx *ctx, int32_t n, const double *rho, c
 struct Cohort {
     rks_batch *b = nullptr;
     std::vector<uint64_t> ids;
-    int phase = 0;  // 0 iterating, 1 final step enqueued
+    int phase = 0;  // 0 iterating, 2 recheck marked, 3 rechecking, 1 final step enqueued
+    int rc_enq = 0; // recheck iterations enqueued
     bool counted = false;  // the last chunk ended with an active-count readback
     cudaEvent_t ev = nullptr;
 };
@@ -1071,16 +1239,44 @@ static int cohort_next(Cohort &h) {
     rks_batch *b = h.b;
     const DevBatch &d = b->d;
     int rc = RKS_OK;
-    if (h.phase == 0) {
+    if (h.phase == 2) {
+        // the marked counts have landed in the pinned words (the chunk's event completed)
+        const int n_precise = pinw(b)[0], n_fp64 = pinw(b)[1];
+        if (n_fp64 > 0) rc = start_fp64_redo(b, n_fp64);
+        if (!rc && n_precise > 0) {
+            h.phase = 3;
+            const int k = std::min(kCheckEvery, d.fixed_iters);
+            rc = enqueue_iters(b, k, kPrecise);
+            h.rc_enq = k;
+        } else if (!rc) {
+            rc = enqueue_final(b);
+            if (!rc) rc = enqueue_adopt(b);
+            h.phase = 1;
+        }
+    } else if (h.phase == 3) {
+        if (h.rc_enq >= d.fixed_iters) {
+            rc = enqueue_final(b);
+            if (!rc) rc = enqueue_adopt(b);
+            h.phase = 1;
+        } else {
+            const int k = std::min(kCheckEvery, d.fixed_iters - h.rc_enq);
+            rc = enqueue_iters(b, k, kPrecise);
+            h.rc_enq += k;
+        }
+    } else if (h.phase == 0) {
         bool done;
         if (d.fixed_iters > 0) done = b->it_enq >= d.fixed_iters;
-        else done = b->it_enq >= d.max_iters || (h.counted && b->ctx->pin[b->pin_slot] == 0);
-        if (done) {
+        else done = b->it_enq >= d.max_iters || (h.counted && pinw(b)[0] == 0);
+        if (done && recheck_on(b)) {
+            rc = enqueue_recheck_start(b);
+            h.phase = 2;
+        } else if (done) {
             rc = enqueue_final(b);
+            if (!rc) rc = enqueue_adopt(b);
             h.phase = 1;
         } else {
             const int lim = d.fixed_iters > 0 ? d.fixed_iters : d.max_iters;
-            rc = enqueue_iters(b, std::min(kCheckEvery, lim - b->it_enq));
+            rc = enqueue_iters(b, std::min(kCheckEvery, lim - b->it_enq), iter_prec(b));
             if (!rc && d.fixed_iters == 0) {
                 rc = enqueue_active_count(b);
                 h.counted = true;
@@ -1212,7 +1408,7 @@ static void worker_main(rks_ctx *c) {
             }
             progressed = true;
             int rc = q == cudaSuccess ? RKS_OK : rks_cuda_fail(q, "cohort", __FILE__, __LINE__);
-            if (!rc && h.phase == 0) rc = cohort_next(h);
+            if (!rc && h.phase != 1) rc = cohort_next(h);
             else if (!rc) {
                 cohort_publish(c, h);
                 cohort_free(h);
@@ -1246,6 +1442,7 @@ extern "C" int rks_create(const rks_options *options, rks_ctx **out) {
     if (o.basis != 0 || o.n_rad <= 0 || o.n_theta <= 0 || o.n_theta > 64 || o.n_phi <= 0 || o.becke_iters < 0 ||
         (o.precision != RKS_FP64 && o.precision != RKS_MIXED) || o.max_iters <= 0 || o.max_slots <= 0 ||
         !(o.fix_theta >= 0) || (o.guess != RKS_GUESS_SAD && o.guess != RKS_GUESS_CORE) || o.max_cohorts <= 0 ||
+        o.iter_precision < 0 || o.iter_precision > 3 || !(o.recheck_err >= 0) || !(o.recheck_fp64_err >= 0) ||
         o.admit_wait_us < 0 || o.grid_chunks < 0 || o.grid_chunks > 256 || o.jk_chunks < 0 || o.jk_chunks > 256)
         return fail(RKS_EINVAL, "bad options");
     int ndev = 0;
@@ -1254,12 +1451,13 @@ extern "C" int rks_create(const rks_options *options, rks_ctx **out) {
     CUDA_OK(cudaSetDevice(o.device));
     rks_ctx *c = new rks_ctx();
     c->opt = o;
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, o.device);
     cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->boys64, sizeof(double) * BOYS_N64 * BOYS_COL64);
     if (e == cudaSuccess) e = cudaMalloc(&c->boys32, sizeof(float) * BOYS_N32 * BOYS_COL32);
     if (e == cudaSuccess) e = cudaMalloc(&c->rad, sizeof(double) * 5 * o.n_rad * 2);
     if (e == cudaSuccess) e = cudaMalloc(&c->ang, sizeof(double) * o.n_theta * o.n_phi * 4);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->pin, sizeof(int) * kPinSlots, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->pin, sizeof(int) * 2 * kPinSlots, cudaHostAllocDefault);
     if (e != cudaSuccess) {
         delete c;
         return rks_cuda_fail(e, "context allocation", __FILE__, __LINE__);

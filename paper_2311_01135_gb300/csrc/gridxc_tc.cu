@@ -4,29 +4,39 @@
 // Section 3.2 B3LYP, AOs recomputed per block as in Section 5):
 //   GEMM1  T = Phi D            (M = 128 points, N = K = nbf padded to 16)
 //   rho_p = sum_n T_pn phi_pn,  grad rho_p = 2 sum_n T_pn grad phi_pn
-//   GEMM2  V' += Phi^T X        (M = 128 AO rows, N = nbf padded, K = points)
+//   GEMM2  V' += Phi^T X        (M = 128 AO rows, N = nbf padded, K = 128 points)
 // Split products (Ootomo & Yokota 2022): a = a_hi + a_lo with a_hi the TF32
 // rounding of a; a b ~= a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32.
 //
-// All tcgen05 operands are K-major in the no-swizzle core-matrix layout: a
-// core is 8 rows x 16 bytes (4 FP32 values along K), 128 contiguous bytes;
-// core (row group g, K chunk c) sits at g * SBO + c * LBO.  GEMM1 contracts
-// over AOs (Phi stored point-row / AO-column), GEMM2 over points (Phi^T and X
-// stored AO-row / point-column), so Phi is written in both arrangements
-// (TF32 operands must be K-major).
+// Operand layouts (every tcgen05 TF32 operand is K-major):
+//  * GEMM1 contracts over AOs: Phi as a [point][AO] tile and D as a [nu][mu]
+//    tile of 8 x 16-byte core matrices (8 rows x 4 K values, 128 contiguous
+//    bytes); the core of (row group g, K chunk c) sits at g * SG + c * 128,
+//    SG = np / 4 * 128.  A thread writes its point's 4 AOs with one 16-byte store.
+//  * GEMM2 contracts over points: Phi^T and X as [AO][point] tiles in the
+//    128-byte swizzled layout: an atom is 8 AO rows x 32 points (1 KB), the
+//    16-byte chunk c of row r sits at chunk position c ^ r, the four atoms of a
+//    row group follow each other and row groups are 4 KB apart.  A warp (32
+//    points, one AO) writes one 128-byte row with 32 scalar stores that hit
+//    32 different banks, without the padding an unswizzled tile would need.
+//    A K step of 8 points is 32 bytes inside an atom.
 //
 // One thread block (512 threads, one per SM) owns 1/nchunk of a molecule's
-// 128-point grid blocks and keeps V' in registers across them.  Per block:
-//   top  point data (prefetched), R_owner - C table, per-shell significance
-//        from the block's radius range
-//   A    radial parts g = sum c e^(-a r^2), g' = sum -2ac e^(-a r^2) per
-//        (shell, point), one set of exponentials per radial set (2s/2p)
-//   B    Phi (hi, lo) in GEMM1 layout; thread 0 issues GEMM1 (3 MMAs per K step)
-//   D    each thread reads its point's T row segment from TMEM and forms rho,
-//        grad rho shell by shell; B3LYP in three parts on three warp groups
-//   F    32-point slices: warps 0-14 build Phi^T and X (hi, lo) in GEMM2
-//        layout, warp 15 issues each slice's MMAs behind named barriers
-//   drain  the block's V' from TMEM into registers (FP32 round-to-nearest)
+// 128-point grid blocks and keeps V' in registers across them.  Thread t
+// serves point p = t % 128 and the AO column quarter q4 = t / 128; the radial
+// values g, g' of its columns stay in its registers between phases.  Per block:
+//   A   radial values of the thread's columns (one set of exponentials per
+//       shell, shared by an atom's 2s and 2p): overlaps the previous block's GEMM2
+//   B   the previous block's V' from tensor memory into registers
+//   C   Phi (hi, lo); one thread issues GEMM1
+//   E   each thread reads its point's T row segment and forms its share of rho
+//       and grad rho shell by shell
+//   F   B3LYP in three parts on three warp groups
+//   G   Phi^T and X = w (v_rho/2 phi + 2 v_sigma grad rho . grad phi)
+//       (hi, lo) into the GEMM2 tiles (over GEMM1's Phi tile, done with);
+//       one thread issues GEMM2
+// Which shells matter in a block (AO screening) is decided once, when the
+// grid is built (grid_mask_kernel), from the block's radius range.
 // FINAL (the mixed final step) forms T on the CUDA cores instead of GEMM1.
 // Waits on the MMA barriers are bounded: on expiry the block records an error
 // flag, waits (bounded) once more, frees its tensor memory and returns.
@@ -38,21 +48,31 @@
 
 #define TC_BP 128
 #define TC_NPMAX RKS_TC_NPMAX   // padded basis size this kernel handles
-#define TC_NSHMAX RKS_TC_NSHMAX // shells this kernel handles
+#define TC_NSHMAX RKS_TC_NSHMAX // shells this kernel handles (one 64-bit mask per block)
 #define TC_TMEM_COLS 256
+#define TC_TCOL 0               // TMEM columns of T (GEMM1)
+#define TC_VCOL 128             // and of V' (GEMM2)
 #define TC_SPIN_LIMIT 4000000  // polls before a wait gives up: >= ~40 ms, far above any MMA here
+#define TC_THREADS 512
+#define TC_SCREEN 1e-9f         // per-block AO screening threshold, iterations
+#define TC_SCREEN_FINAL 1e-14f  // and final step
+#define TC_SHX 12               // floats per shell in shx: a[3], c[3], -2ac[3], pad
+
+static_assert(TC_NSHMAX <= 64, "one 64-bit significance mask per block");
+static_assert(TC_NPMAX / 4 == 20, "a thread owns at most 20 AO columns");
 
 namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Shared-memory matrix descriptor (no swizzle, sm_100-family version bits).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);
     d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for sm_100-family tcgen05
-    return d;                // no swizzle, base offset 0, relative LBO
+    d |= (uint64_t)1 << 46;
+    return d;
 }
 
 // kind::tf32 instruction descriptor: D F32, A/B TF32, both K-major, M and N.
@@ -97,71 +117,65 @@ __device__ __forceinline__ void split4(const float *v, float4 &hi, float4 &lo) {
     lo.x = v[0] - hi.x; lo.y = v[1] - hi.y; lo.z = v[2] - hi.z; lo.w = v[3] - hi.w;
 }
 
-// byte offset of element (row, k) in a K-major core layout with row-group stride sg
+// byte offset of element (row, k) in the core-matrix tile with row-group stride sg
 __device__ __forceinline__ uint32_t coff(int row, int k, uint32_t sg) {
     return (uint32_t)(row >> 3) * sg + (uint32_t)(k >> 2) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 3) * 4u;
 }
 
-// Named barriers (ids 1, 2) between the operand builders and the MMA warp.
-__device__ __forceinline__ void bar_arrive(int id, int count) {
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+// byte offset of element (row, point) in a 128-byte-swizzled K-major tile of
+// 128 points: atoms of 8 rows x 32 points, four per row group
+__device__ __forceinline__ uint32_t soff(int row, int pt) {
+    return (uint32_t)(row >> 3) * 4096u + (uint32_t)(pt >> 5) * 1024u + (uint32_t)(row & 7) * 128u +
+           (uint32_t)((((pt >> 2) & 7) ^ (row & 7)) * 16) + (uint32_t)(pt & 3) * 4u;
 }
-__device__ __forceinline__ void bar_sync(int id, int count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+
+// descriptor of a 128-byte-swizzled K-major tile (row groups 4 KB apart)
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    return sdesc(saddr, 16, 4096) | ((uint64_t)2 << 61);
 }
 
 }  // namespace tc
 
+// Byte offsets inside the dynamic shared buffer.  GEMM1's Phi tiles and
+// GEMM2's Phi^T / X tiles share one region (GEMM1 is done before the latter
+// are written; the next block's Phi waits for GEMM2).  GEMM2's A operand
+// reads M = 128 AO rows, past the np rows of a Phi^T tile into the tiles
+// after it (rows >= np are discarded): the X tiles follow, so every read stays
+// inside the buffer.  The rho partials alias the start of the region
+// (written after GEMM1, read before the GEMM2 tiles are written).
 struct TcSmem {
-    // byte offsets inside the dynamic shared buffer
-    uint32_t D_hi, D_lo, R_g, R_gp, work, set1, pts, part, xcp, grd, shx, shf, aoc, rset;
+    uint32_t D_hi, D_lo, phi_hi, phi_lo, pt_hi, pt_lo, x_hi, x_lo, part, xcp, grd, shx, shf, col;
     uint32_t total;
 };
-
-// GEMM2 operand slices (32 points): K-direction core stride padded to 144 B
-// so that 32 threads storing one AO row at 32 consecutive points hit 32
-// distinct banks; row-group stride 8 cores x 144 B.
-#define TC_SLICE 32
-#define TC_LBO2 144u
-#define TC_SBO2 (8u * TC_LBO2)
-#define TC_SHX 12  // floats per shell in shx: a[3], c[3], -2ac[3], l, ao0, pad
 
 __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
     TcSmem s;
     uint32_t o = 0;
-    const uint32_t dsz = (uint32_t)np * np * 4;
+    const uint32_t dsz = (uint32_t)np * np * 4, opsz = (uint32_t)TC_BP * np * 4;
     s.D_hi = o; o += dsz;
-    s.D_lo = o; o += dsz;
-    s.R_g = o; o += (uint32_t)nsh * TC_BP * 4;
-    s.R_gp = o; o += (uint32_t)nsh * TC_BP * 4;
-    o = (o + 127) & ~127u;
-    s.work = o;
-    // GEMM1: Phi hi, lo (128 points x np AOs, K-major, 128-byte core stride).
-    // GEMM2: two sets of {Phi^T hi, Phi^T lo, X hi, X lo}, each np/8 row groups
-    // of 32-point slices.  The M = 128 reads of an A operand run past its np
-    // rows into the next buffer of the same set (rows >= np are never read back).
-    const uint32_t w1 = 2u * TC_BP * np * 4;
-    const uint32_t opsz = (uint32_t)(np / 8) * TC_SBO2;
-    const uint32_t w2 = 8u * opsz;
-    s.set1 = 4u * opsz;
-    o += (w1 > w2 ? w1 : w2);
-    s.pts = o; o += 4 * TC_BP * 4;          // per point: offset x, y, z and weight (float4)
-    s.part = o; o += 4 * 4 * TC_BP * 4;     // rho, grad rho partials per AO quarter
+    s.D_lo = o; o += dsz;   // 8 np^2 bytes: the swizzled tiles below start 1 KB aligned
+    s.phi_hi = o;
+    s.phi_lo = o + opsz;
+    s.pt_hi = o;            // swizzled tiles, np / 8 row groups of 4 KB = opsz bytes each
+    s.pt_lo = o + opsz;
+    s.x_hi = o + 2 * opsz;
+    s.x_lo = o + 3 * opsz;
+    o += 4 * opsz;
+    s.part = s.pt_hi;                       // rho, grad rho partials per AO quarter (4 x 4 x 128 floats)
     s.xcp = o; o += 3 * 2 * TC_BP * 4;      // v_rho, v_sigma per XC part
     s.grd = o; o += 3 * TC_BP * 4;          // grad rho
     s.shx = o; o += (uint32_t)nsh * TC_SHX * 4;
     s.shf = o; o += (uint32_t)nsh * 8 * 4;  // per shell: R_owner0 - C (3), pad, R_owner1 - C (3), pad
-    s.aoc = o; o += (uint32_t)np * 4;       // per AO: shell * 4 + component + 1, -1 if zero in this block
-    s.rset = o; o += (uint32_t)nsh * 4;     // radial sets: lead shell | partner << 8 (255: none)
-    s.total = o;
+    s.col = o; o += (uint32_t)np * 4;       // per AO column: shell << 2 | (component + 1), bit 8: shares the
+                                            // previous column's exponentials; -1 for padding
+    // GEMM2's A operand reads 128 rows (16 row groups of 4 KB, plus the K
+    // offset inside an atom) from the start of the Phi^T lo tile: for small
+    // bases that runs past the tiles, so the buffer extends to cover it
+    const uint32_t reach = s.pt_lo + 16u * 4096u + 1024u;
+    s.total = o > reach ? o : reach;
     return s;
 }
 
-#define TC_THREADS 512
-#define TC_SCREEN 1e-9f         // per-block AO screening threshold, iterations
-#define TC_SCREEN_FINAL 1e-14f  // and final step
-
-static_assert(TC_NPMAX / 4 == 20, "ld20 reads one quarter of the padded basis");
 // This thread's row of 20 TMEM columns starting at taddr (5 loads of 4
 // columns, one wait; the wait names the registers so that no use moves above it).
 __device__ __forceinline__ void ld20(uint32_t taddr, float *v) {
@@ -188,6 +202,126 @@ __device__ __forceinline__ float shell_rmin(float d, float lo, float hi) {
     return d > hi ? d - hi : (d < lo ? lo - d : 0.f);
 }
 
+// ------------------------------------------------------- block masks (setup)
+// One thread block per 128-point grid block of a molecule the tensor-core
+// kernel takes: bit s of mask[0] (iterations) / mask[1] (final step) is set
+// when shell s may exceed the screening threshold somewhere in the block:
+// |phi|, |grad phi| <= sum_k |c_k| e^(-a_k r^2) (1 + r + 2 a_k r^3), which
+// decreases in r beyond r = 4 bohr for every STO-3G exponent, evaluated at
+// the smallest distance from the shell centre to the block's points.
+__global__ void __launch_bounds__(TC_BP) grid_mask_kernel(DevBatch b, const int *blk_mol,
+                                                          unsigned long long *mask) {
+    const long long gblk = blockIdx.x;
+    const int m = blk_mol[gblk];
+    const MolDesc md = b.mol[m];
+    if (!grid_tc_fits(md.nbf, md.nsh)) return;
+    __shared__ unsigned blk_r[4];  // radius range per owner (float bits; r >= 0 orders as unsigned)
+    __shared__ unsigned long long bits[2][2];
+    __shared__ int nsig[2][2];
+    const int t = threadIdx.x, lane = t & 31;
+    if (t < 4) blk_r[t] = (t & 1) ? 0u : 0x7f800000u;
+    if (t < 4) bits[t >> 1][t & 1] = 0ull;
+    __syncthreads();
+    const long long p0 = gblk * TC_BP - md.pts0;  // first point of the block, molecule-local
+    const int npa = b.n_rad * b.n_theta * b.n_phi;
+    const int own0 = min((int)(p0 / npa), md.natom - 1);
+    const float *gx = (const float *)b.gx, *gy = (const float *)b.gy, *gz = (const float *)b.gz;
+    const long long gi = gblk * TC_BP + t;
+    const float x = gx[gi], y = gy[gi], z = gz[gi];
+    const int h = min((int)((p0 + t) / npa), md.natom - 1) - own0;
+    const unsigned rb = __float_as_uint(sqrtf(x * x + y * y + z * z));
+    const unsigned lo0 = __reduce_min_sync(0xffffffffu, h == 0 ? rb : 0x7f800000u);
+    const unsigned hi0 = __reduce_max_sync(0xffffffffu, h == 0 ? rb : 0u);
+    const unsigned lo1 = __reduce_min_sync(0xffffffffu, h == 1 ? rb : 0x7f800000u);
+    const unsigned hi1 = __reduce_max_sync(0xffffffffu, h == 1 ? rb : 0u);
+    if (lane == 0) {
+        atomicMin(&blk_r[0], lo0);
+        atomicMax(&blk_r[1], hi0);
+        atomicMin(&blk_r[2], lo1);
+        atomicMax(&blk_r[3], hi1);
+    }
+    __syncthreads();
+    bool on_it = false, on_fin = false;
+    if (t < md.nsh) {
+        const int g = md.sh0 + t;
+        float rmin = 3.4e38f;
+#pragma unroll
+        for (int hh = 0; hh < 2; hh++) {
+            const float lo = __uint_as_float(blk_r[2 * hh]), hi = __uint_as_float(blk_r[2 * hh + 1]);
+            if (lo > hi) continue;  // no point of this owner in the block
+            const int A = min(own0 + hh, md.natom - 1);
+            const double *ra = b.axyz + (md.atom0 + A) * 3, *rc = b.sh_xyz + g * 3;
+            const float dx = (float)(ra[0] - rc[0]), dy = (float)(ra[1] - rc[1]), dz = (float)(ra[2] - rc[2]);
+            rmin = fminf(rmin, shell_rmin(sqrtf(dx * dx + dy * dy + dz * dz), lo, hi));
+        }
+        if (rmin < 4.f) {
+            on_it = on_fin = true;
+        } else {
+            float bound = 0.f;
+            for (int k = 0; k < 3; k++) {
+                const float a = (float)b.sh_ex[g * 3 + k];
+                bound += fabsf((float)b.sh_co[g * 3 + k]) * __expf(-a * rmin * rmin) *
+                         (1.f + rmin + 2.f * a * rmin * rmin * rmin);
+            }
+            on_it = bound > TC_SCREEN;
+            on_fin = bound > TC_SCREEN_FINAL;
+        }
+    }
+    const unsigned bi = __ballot_sync(0xffffffffu, on_it), bf = __ballot_sync(0xffffffffu, on_fin);
+    // significant AOs (1 per s shell, 3 per p shell)
+    const int ncomp = t < md.nsh ? (b.sh_l[md.sh0 + t] ? 3 : 1) : 0;
+    const int ni = __reduce_add_sync(0xffffffffu, on_it ? ncomp : 0);
+    const int nf = __reduce_add_sync(0xffffffffu, on_fin ? ncomp : 0);
+    if (lane == 0 && t < 64) {
+        bits[0][t >> 5] = bi;
+        bits[1][t >> 5] = bf;
+        nsig[0][t >> 5] = ni;
+        nsig[1][t >> 5] = nf;
+    }
+    __syncthreads();
+    if (t == 0) {
+        mask[2 * gblk] = bits[0][0] | (bits[0][1] << 32);
+        mask[2 * gblk + 1] = bits[1][0] | (bits[1][1] << 32);
+        const double si = nsig[0][0] + nsig[0][1], sf = nsig[1][0] + nsig[1][1];
+        atomicAdd(&b.st[m].grid_pairs[0], (double)TC_BP * si * si);
+        atomicAdd(&b.st[m].grid_pairs[1], (double)TC_BP * sf * sf);
+    }
+}
+
+__global__ void grid_pairs_reset_kernel(DevBatch b) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < b.nmol) b.st[m].grid_pairs[0] = b.st[m].grid_pairs[1] = 0.0;
+}
+
+void launch_grid_masks(const DevBatch &b, long long nblk_total, const int *blk_mol, cudaStream_t s) {
+    grid_pairs_reset_kernel<<<(b.nmol + 127) / 128, 128, 0, s>>>(b);
+    if (b.blk_mask) grid_mask_kernel<<<(unsigned)nblk_total, TC_BP, 0, s>>>(b, blk_mol, b.blk_mask);
+}
+
+// ------------------------------------------------------------ the kernel
+// Column loop helper: the thread's columns c0 .. c0 + nq - 1 (nq <= 20), the
+// code of each (shell, component), whether it is significant in this block,
+// and when a new shell starts (the same for every thread of a warp group).
+struct ColIt {
+    int code;   // shell << 2 | (component + 1); -1: padding or screened
+    int s, c;   // shell, component (-1 for an s shell)
+    bool fresh; // first column of its shell in this thread's run
+    bool share; // same atom and exponents as the previous column's shell
+};
+__device__ __forceinline__ ColIt col_info(const int *col, int c0, int j, unsigned long long mask, int &prev_s) {
+    ColIt it;
+    const int raw = col[c0 + j];
+    const int s = raw >= 0 ? (raw >> 2) & 63 : -1;
+    const bool on = raw >= 0 && ((mask >> s) & 1ull);
+    it.code = on ? (raw & 0xff) : -1;
+    it.s = s;
+    it.c = (raw & 3) - 1;
+    it.fresh = on && (j == 0 || s != prev_s);
+    it.share = on && j > 0 && (raw & 0x100) && prev_s >= 0 && prev_s != s;
+    prev_s = on ? s : -1;
+    return it;
+}
+
 // FINAL (the mixed path's final step, TA = double): the density contraction
 // T = Phi D runs on the CUDA cores in FP32 with round-to-nearest sums (the
 // tensor cores' truncating accumulation would bias rho and E_xc), V_xc stays
@@ -196,39 +330,36 @@ __device__ __forceinline__ float shell_rmin(float d, float lo, float hi) {
 template <typename TA, bool FINAL>
 __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar1, bar2[2];
+    __shared__ __align__(8) uint64_t bar1, bar2;
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_fail, s_nset;
-    __shared__ __align__(16) int owner_h[TC_BP];
-    __shared__ int sig[TC_NSHMAX];        // shell significant somewhere in this block
-    __shared__ unsigned blk_r[4];         // radius range of the block per owner (float bits)
+    __shared__ int s_fail;
     const int m = blockIdx.y, chunk = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
     if (!grid_tc_fits(md.nbf, md.nsh)) return;  // the CUDA-core kernel takes this molecule
+    if (chunk >= md.nblk) return;
     const int n = md.nbf, nsh = md.nsh;
     const int np = (n + 15) & ~15;
     const int nq = np / 4;  // AO columns per thread quarter (multiple of 4)
     const TcSmem L = tc_layout(np, nsh);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int p = t & (TC_BP - 1), q4 = t >> 7;  // point, column quarter
+    const int c0 = q4 * nq;
     unsigned char *sm = smem;
-    float *Rg = (float *)(sm + L.R_g), *Rgp = (float *)(sm + L.R_gp);
-    float4 *pt4 = (float4 *)(sm + L.pts);
     float *part = (float *)(sm + L.part);
     float *xcp = (float *)(sm + L.xcp), *grd = (float *)(sm + L.grd);
     float *shx = (float *)(sm + L.shx), *shf = (float *)(sm + L.shf);
-    int *shxi = (int *)shx;
-    int *aoc = (int *)(sm + L.aoc), *rset = (int *)(sm + L.rset);
-    const uint32_t sg1 = (uint32_t)(np / 4) * 128u;  // row-group stride, K = np (GEMM1 A and B)
+    int *col = (int *)(sm + L.col);
+    const uint32_t sg = (uint32_t)(np / 4) * 128u;  // bytes per 8-row group of every tile
 
-    // ---- per-CTA constants: D (hi, lo) as GEMM1's B (rows nu, K = mu), or plain
-    // FP32 D[mu][nu] for the CUDA-core contraction of the final step; shells, radial sets
+    // ---- per-CTA constants: D (hi, lo) as GEMM1's B, or plain FP32 D[mu][nu]
+    // for the CUDA-core contraction of the final step; shells; column codes
     const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
     if constexpr (FINAL) {
         float *Dp = (float *)(sm + L.D_hi);
         for (int i = t; i < np * np; i += blockDim.x) {
-            const int row = i / np, col = i % np;
-            Dp[i] = (row < n && col < n) ? (float)D[row * n + col] : 0.f;
+            const int row = i / np, cc = i % np;
+            Dp[i] = (row < n && cc < n) ? (float)D[row * n + cc] : 0.f;
         }
     } else {
         for (int i = t; i < np * np / 4; i += blockDim.x) {
@@ -241,39 +372,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
             }
             float4 hi, lo;
             tc::split4(v, hi, lo);
-            *(float4 *)(sm + L.D_hi + tc::coff(row, kc * 4, sg1)) = hi;
-            *(float4 *)(sm + L.D_lo + tc::coff(row, kc * 4, sg1)) = lo;
+            *(float4 *)(sm + L.D_hi + tc::coff(row, kc * 4, sg)) = hi;
+            *(float4 *)(sm + L.D_lo + tc::coff(row, kc * 4, sg)) = lo;
         }
     }
     for (int s = t; s < nsh; s += blockDim.x) {
         const int g = md.sh0 + s;
-        const int l = b.sh_l[g], a0 = b.sh_ao0[g];
         for (int k = 0; k < 3; k++) {
             const double a = b.sh_ex[g * 3 + k], c = b.sh_co[g * 3 + k];
             shx[s * TC_SHX + k] = (float)a;
             shx[s * TC_SHX + 3 + k] = (float)c;
             shx[s * TC_SHX + 6 + k] = (float)(-2.0 * a * c);
         }
-        shxi[s * TC_SHX + 9] = l;
-        shxi[s * TC_SHX + 10] = a0;
+        shx[s * TC_SHX + 9] = shx[s * TC_SHX + 10] = shx[s * TC_SHX + 11] = 0.f;
     }
-    if (t == 0) s_nset = 0;
+    for (int mu = t; mu < np; mu += blockDim.x) col[mu] = -1;
     __syncthreads();
-    if (t < nsh) {
-        // radial sets: a p shell shares the exponents of its atom's 2s shell
-        // (STO-3G 2sp), so one set of exponentials serves both
-        const int g = md.sh0 + t;
-        const int l = b.sh_l[g], at = b.sh_atom[g];
-        const double e0 = b.sh_ex[g * 3], e1 = b.sh_ex[g * 3 + 1], e2 = b.sh_ex[g * 3 + 2];
-        int partner = 255;
-        for (int q2 = 0; q2 < nsh; q2++) {
-            const int h = md.sh0 + q2;
-            if (b.sh_l[h] != l && b.sh_atom[h] == at && b.sh_ex[h * 3] == e0 && b.sh_ex[h * 3 + 1] == e1 &&
-                b.sh_ex[h * 3 + 2] == e2)
-                partner = q2;
+    for (int s = t; s < nsh; s += blockDim.x) {
+        const int g = md.sh0 + s;
+        const int l = b.sh_l[g], a0 = b.sh_ao0[g];
+        // an atom's 2p shell follows its 2s shell in AO order with the same exponents
+        bool share = false;
+        if (l == 1 && a0 > 0) {
+            for (int s2 = 0; s2 < nsh; s2++) {
+                const int h2 = md.sh0 + s2;
+                if (b.sh_l[h2] == 0 && b.sh_ao0[h2] == a0 - 1 && b.sh_atom[h2] == b.sh_atom[g] &&
+                    b.sh_ex[h2 * 3] == b.sh_ex[g * 3] && b.sh_ex[h2 * 3 + 1] == b.sh_ex[g * 3 + 1] &&
+                    b.sh_ex[h2 * 3 + 2] == b.sh_ex[g * 3 + 2])
+                    share = true;
+            }
         }
-        if (l == 0) rset[atomicAdd(&s_nset, 1)] = t | (partner << 8);      // s shell leads its set
-        else if (partner == 255) rset[atomicAdd(&s_nset, 1)] = t | (255 << 8);  // unpaired p shell
+        if (l == 0) col[a0] = s << 2;
+        else
+            for (int c = 0; c < 3; c++) col[a0 + c] = (s << 2) | (c + 1) | (share && c == 0 ? 0x100 : 0);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_slot)),
@@ -283,8 +414,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     }
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar1)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar2[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar2[1])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar2)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
@@ -292,56 +422,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const uint32_t tT = tmem, tV = tmem + TC_NPMAX;  // column bases of T (GEMM1) and V (GEMM2)
-    const uint32_t id1 = tc::idesc(128, np), id2 = tc::idesc(128, np);
+    const uint32_t tT = tmem + TC_TCOL, tV = tmem + TC_VCOL;
+    const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;  // this warp's TMEM lane quarter
+    const uint32_t id1 = tc::idesc(128, np), id2 = id1;
     const uint32_t su = tc::smem_u32(sm);
-    const int nset = s_nset;
-    uint32_t ph1 = 0, ph2[2] = {0, 0};
+    uint32_t ph1 = 0, ph2 = 0;
+    bool pending = false;  // a GEMM2 in flight whose V' is not yet in vacc
+    bool in1 = false;      // a GEMM1 in flight
     double exc = 0.0;
-    // thread quarter g4 (0..3) and TMEM lane quarter q: V' row q*32 + lane, columns [g4*nq, g4*nq + nq)
-    const int q = warp & 3, g4 = warp >> 2;
     float vacc[TC_NPMAX / 4];
 #pragma unroll
     for (int j = 0; j < TC_NPMAX / 4; j++) vacc[j] = 0.f;
-    bool any_block = false;
+    bool any_block = false, failed = false;
 
     const float *gxp = (const float *)b.gx + md.pts0, *gyp = (const float *)b.gy + md.pts0;
     const float *gzp = (const float *)b.gz + md.pts0, *gwp = (const float *)b.gw + md.pts0;
-    bool failed = false;
+    const unsigned long long *bmask = b.blk_mask + 2 * (md.pts0 / TC_BP) + (FINAL ? 1 : 0);
     const int npa = b.n_rad * b.n_theta * b.n_phi;
-    // point data of the next block, prefetched into registers (threads < 128)
-    float nx = 0.f, ny = 0.f, nz = 0.f, nw = 0.f;
-    if (t < TC_BP && chunk < md.nblk) {
-        const int i0 = chunk * TC_BP + t;
-        nx = gxp[i0]; ny = gyp[i0]; nz = gzp[i0]; nw = gwp[i0];
-    }
+    float nx = gxp[chunk * TC_BP + p], ny = gyp[chunk * TC_BP + p], nz = gzp[chunk * TC_BP + p];
+    float nw = gwp[chunk * TC_BP + p];
     int shf_owner = -1;  // owner atom the shf table was built for
-    for (int blk = chunk; blk < md.nblk && !failed; blk += nchunk) {
+
+    // drain the pending GEMM2: V' row segment into vacc
+    auto drain = [&]() -> bool {
+        const bool ok = __syncthreads_and(tc::wait(&bar2, ph2));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) return false;  // still pending: the exit path waits on the same phase
+        ph2 ^= 1;
+        float v[TC_NPMAX / 4];
+        ld20(tV + lanes + c0, v);
+#pragma unroll
+        for (int j = 0; j < TC_NPMAX / 4; j++)
+            if (j < nq) vacc[j] += v[j];
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        return true;
+    };
+
+    for (int blk = chunk; blk < md.nblk; blk += nchunk) {
         const int p0 = blk * TC_BP;
         const int own0 = min(p0 / npa, md.natom - 1);
-        if (t < 4) blk_r[t] = (t & 1) ? 0u : 0x7f800000u;  // lo = +inf, hi = 0 per owner
-        __syncthreads();
-        if (t < TC_BP) {
-            const int h = min((p0 + t) / npa, md.natom - 1) - own0;
-            owner_h[t] = h;
-            pt4[t] = make_float4(nx, ny, nz, nw);
-            const unsigned rb = __float_as_uint(sqrtf(nx * nx + ny * ny + nz * nz));  // r >= 0: bits order as floats
-            const unsigned lo0 = __reduce_min_sync(0xffffffffu, h == 0 ? rb : 0x7f800000u);
-            const unsigned hi0 = __reduce_max_sync(0xffffffffu, h == 0 ? rb : 0u);
-            const unsigned lo1 = __reduce_min_sync(0xffffffffu, h == 1 ? rb : 0x7f800000u);
-            const unsigned hi1 = __reduce_max_sync(0xffffffffu, h == 1 ? rb : 0u);
-            if (lane == 0) {
-                atomicMin(&blk_r[0], lo0);
-                atomicMax(&blk_r[1], hi0);
-                atomicMin(&blk_r[2], lo1);
-                atomicMax(&blk_r[3], hi1);
-            }
-            const int i1 = p0 + nchunk * TC_BP + t;  // next block of this CTA
-            if (blk + nchunk < md.nblk) {
-                nx = gxp[i1]; ny = gyp[i1]; nz = gzp[i1]; nw = gwp[i1];
-            }
+        const float px = nx, py = ny, pz = nz, pw = nw;
+        if (blk + nchunk < md.nblk) {  // this thread's point of the next block
+            const int i1 = p0 + nchunk * TC_BP + p;
+            nx = gxp[i1]; ny = gyp[i1]; nz = gzp[i1]; nw = gwp[i1];
         }
+        const unsigned long long mask = bmask[2 * blk];
+        if (mask == 0ull) continue;  // every AO below the screen: rho under the XC cutoff everywhere
+        any_block = true;
         if (own0 != shf_owner) {  // R_owner - C for the block's (at most two) owners
+            __syncthreads();
             for (int i = t; i < 2 * nsh; i += blockDim.x) {
                 const int hh = i / nsh, s = i % nsh;
                 const int A = min(own0 + hh, md.natom - 1);
@@ -350,377 +479,265 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
                     make_float4((float)(ra[0] - rc[0]), (float)(ra[1] - rc[1]), (float)(ra[2] - rc[2]), 0.f);
             }
             shf_owner = own0;
-        }
-        __syncthreads();
-        // ---- shell significance from the block's radius range (one thread per shell)
-        bool sig_t = false;
-        if (t < nsh) {
-            const int s = t;
-            float rmin = 3.4e38f;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const float lo = __uint_as_float(blk_r[2 * h]), hi = __uint_as_float(blk_r[2 * h + 1]);
-                if (lo > hi) continue;  // no point of this owner in the block
-                const float *dl = shf + s * 8 + h * 4;
-                const float d = sqrtf(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
-                rmin = fminf(rmin, shell_rmin(d, lo, hi));
-            }
-            // |phi|, |grad phi| <= sum_k |c_k| e^(-a_k r^2) (1 + r + 2 a_k r^3), decreasing in r
-            // beyond r = 4 bohr for every STO-3G exponent
-            bool on = rmin < 4.f;
-            if (!on) {
-                float bound = 0.f;
-                for (int k = 0; k < 3; k++) {
-                    const float a = shx[s * TC_SHX + k];
-                    bound += fabsf(shx[s * TC_SHX + 3 + k]) * __expf(-a * rmin * rmin) *
-                             (1.f + rmin + 2.f * a * rmin * rmin * rmin);
-                }
-                on = bound > (FINAL ? TC_SCREEN_FINAL : TC_SCREEN);
-            }
-            sig[s] = on;
-            sig_t = on;
-        }
-        const int nsig = __syncthreads_count(sig_t);
-        if (nsig == 0) continue;  // every AO below the screen: rho under the XC cutoff everywhere
-        any_block = true;
-        for (int mu = t; mu < np; mu += blockDim.x) aoc[mu] = -1;
-        __syncthreads();
-        for (int s = t; s < nsh; s += blockDim.x) {
-            if (!sig[s]) continue;
-            const int l = shxi[s * TC_SHX + 9], a0 = shxi[s * TC_SHX + 10];
-            if (l == 0) aoc[a0] = s * 4;
-            else for (int c = 0; c < 3; c++) aoc[a0 + c] = s * 4 + c + 1;
-        }
-        // ---- A: radial parts g = sum c e^(-a r^2), g' = sum -2ac e^(-a r^2) per (shell, point),
-        // one set of exponentials per radial set
-#pragma unroll 2
-        for (int i = t; i < nset * TC_BP; i += blockDim.x) {
-            const int k = i >> 7, p = i & (TC_BP - 1);
-            const int s1 = rset[k] & 255, s2 = rset[k] >> 8;
-            const bool on1 = sig[s1], on2 = s2 != 255 && sig[s2];
-            if (!on1 && !on2) continue;
-            const float4 dl = *(const float4 *)(shf + s1 * 8 + owner_h[p] * 4);
-            const float4 q4 = pt4[p];
-            const float dx = dl.x + q4.x, dy = dl.y + q4.y, dz = dl.z + q4.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const float4 xa = *(const float4 *)(shx + s1 * TC_SHX), xb = *(const float4 *)(shx + s1 * TC_SHX + 4);
-            const float xc9 = shx[s1 * TC_SHX + 8];
-            const float e0 = __expf(-xa.x * r2), e1 = __expf(-xa.y * r2), e2 = __expf(-xa.z * r2);
-            if (on1) {
-                Rg[s1 * TC_BP + p] = xa.w * e0 + xb.x * e1 + xb.y * e2;
-                Rgp[s1 * TC_BP + p] = xb.z * e0 + xb.w * e1 + xc9 * e2;
-            }
-            if (on2) {
-                const float4 ya = *(const float4 *)(shx + s2 * TC_SHX), yb = *(const float4 *)(shx + s2 * TC_SHX + 4);
-                const float yc9 = shx[s2 * TC_SHX + 8];
-                Rg[s2 * TC_BP + p] = ya.w * e0 + yb.x * e1 + yb.y * e2;
-                Rgp[s2 * TC_BP + p] = yb.z * e0 + yb.w * e1 + yc9 * e2;
-            }
-        }
-        __syncthreads();
-        // ---- B: Phi (points x AOs) for GEMM1; thread = (point, AO quarter)
-        const int p = t & (TC_BP - 1);
-        const float4 pq4 = pt4[p];
-        const float px = pq4.x, py = pq4.y, pz = pq4.z;
-        const int hp = owner_h[p];
-        if constexpr (FINAL) {
-            // plain FP32 Phi[mu][point] for the CUDA-core contraction
-            float *phi = (float *)(sm + L.work);
-            for (int kc = g4 * (nq / 4); kc < (g4 + 1) * (nq / 4); kc++) {
-                const int4 code4 = *(const int4 *)(aoc + kc * 4);
-                const int codes[4] = {code4.x, code4.y, code4.z, code4.w};
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int code = codes[j];
-                    float val = 0.f;
-                    if (code >= 0) {
-                        const int s = code >> 2, c = (code & 3) - 1;
-                        const float gg = Rg[s * TC_BP + p];
-                        const float pc = c == 0 ? px : (c == 1 ? py : pz);
-                        val = (c < 0) ? gg : (shf[s * 8 + hp * 4 + c] + pc) * gg;
-                    }
-                    phi[(kc * 4 + j) * TC_BP + p] = val;
-                }
-            }
             __syncthreads();
-        } else {
-            const uint32_t phi_hi = L.work, phi_lo = L.work + (uint32_t)TC_BP * np * 4;
-            for (int kc = g4 * (nq / 4); kc < (g4 + 1) * (nq / 4); kc++) {
-                float v[4];
-                const int4 code4 = *(const int4 *)(aoc + kc * 4);
-                const int codes[4] = {code4.x, code4.y, code4.z, code4.w};
+        }
+        const int hp = min((p0 + p) / npa, md.natom - 1) - own0;
+        const float *shfp = shf + hp * 4;
+
+        // ---- A: radial values g = sum c e^(-a r^2), g' = sum -2ac e^(-a r^2) of the thread's columns
+        float gj[TC_NPMAX / 4], gpj[TC_NPMAX / 4];
+        {
+            int prev_s = -1;
+            float e0 = 0.f, e1 = 0.f, e2 = 0.f, cg = 0.f, cgp = 0.f;
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int code = codes[j];
-                    float val = 0.f;
-                    if (code >= 0) {
-                        const int s = code >> 2, c = (code & 3) - 1;
-                        const float gg = Rg[s * TC_BP + p];
-                        const float pc = c == 0 ? px : (c == 1 ? py : pz);
-                        val = (c < 0) ? gg : (shf[s * 8 + hp * 4 + c] + pc) * gg;
+            for (int j = 0; j < TC_NPMAX / 4; j++) {
+                gj[j] = gpj[j] = 0.f;
+                if (j < nq) {
+                    const ColIt it = col_info(col, c0, j, mask, prev_s);
+                    if (it.fresh) {
+                        const float4 xa = *(const float4 *)(shx + it.s * TC_SHX);
+                        const float4 xb = *(const float4 *)(shx + it.s * TC_SHX + 4);
+                        const float xc9 = shx[it.s * TC_SHX + 8];
+                        if (!it.share) {
+                            const float4 dl = *(const float4 *)(shfp + it.s * 8);
+                            const float dx = dl.x + px, dy = dl.y + py, dz = dl.z + pz;
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            e0 = __expf(-xa.x * r2);
+                            e1 = __expf(-xa.y * r2);
+                            e2 = __expf(-xa.z * r2);
+                        }
+                        cg = xa.w * e0 + xb.x * e1 + xb.y * e2;
+                        cgp = xb.z * e0 + xb.w * e1 + xc9 * e2;
                     }
-                    v[j] = val;
+                    if (it.code >= 0) {
+                        gj[j] = cg;
+                        gpj[j] = cgp;
+                    }
                 }
-                float4 hi, lo;
-                tc::split4(v, hi, lo);
-                *(float4 *)(sm + phi_hi + tc::coff(p, kc * 4, sg1)) = hi;
-                *(float4 *)(sm + phi_lo + tc::coff(p, kc * 4, sg1)) = lo;
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
+        }
+        // ---- B: the previous block's V'
+        if (pending) {
+            if (!drain()) {
+                failed = true;
+                break;
+            }
+            pending = false;
+        }
+        // ---- C: Phi (hi, lo) into the [point][AO] tile
+        {
+            int prev_s = -1;
+            float dx = 0.f, dy = 0.f, dz = 0.f;
+#pragma unroll
+            for (int kc = 0; kc < TC_NPMAX / 16; kc++) {
+                if (kc * 4 < nq) {
+                    float v[4];
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const int j = kc * 4 + i;
+                        const ColIt it = col_info(col, c0, j, mask, prev_s);
+                        if (it.fresh) {
+                            const float4 dl = *(const float4 *)(shfp + it.s * 8);
+                            dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
+                        }
+                        const float dc = it.c == 0 ? dx : (it.c == 1 ? dy : dz);
+                        v[i] = it.code < 0 ? 0.f : (it.c < 0 ? gj[j] : dc * gj[j]);
+                    }
+                    float4 hi, lo;
+                    tc::split4(v, hi, lo);
+                    *(float4 *)(sm + L.phi_hi + tc::coff(p, c0 + kc * 4, sg)) = hi;
+                    *(float4 *)(sm + L.phi_lo + tc::coff(p, c0 + kc * 4, sg)) = lo;
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        float Tv[TC_NPMAX / 4];
+        if constexpr (!FINAL) {
             if (t == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int s = 0; s < np / 8; s++) {
                     const uint32_t ka = 2u * s * 128u;
-                    const uint64_t ah = tc::sdesc(su + phi_hi + ka, 128, sg1), al = tc::sdesc(su + phi_lo + ka, 128, sg1);
-                    const uint64_t bh = tc::sdesc(su + L.D_hi + ka, 128, sg1), bl = tc::sdesc(su + L.D_lo + ka, 128, sg1);
+                    const uint64_t ah = tc::sdesc(su + L.phi_hi + ka, 128, sg), al = tc::sdesc(su + L.phi_lo + ka, 128, sg);
+                    const uint64_t bh = tc::sdesc(su + L.D_hi + ka, 128, sg), bl = tc::sdesc(su + L.D_lo + ka, 128, sg);
                     tc::mma(tT, ah, bh, id1, s > 0);
                     tc::mma(tT, ah, bl, id1, 1);
                     tc::mma(tT, al, bh, id1, 1);
                 }
                 tc::commit(&bar1);
             }
-        }
-        // ---- D: density from the T rows, shell by shell (thread = point, AO quarter):
-        // with u = sum_c T_c d_c (p shell; u = T for an s shell) and Tv = (T_x, T_y, T_z),
-        // rho += g u and grad rho += 2 (g' u d + g Tv)
-        float Tacc[TC_NPMAX / 4];  // FINAL: this thread's T columns, from the CUDA cores
-        if constexpr (FINAL) {
-#pragma unroll
-            for (int j = 0; j < TC_NPMAX / 4; j++) Tacc[j] = 0.f;
-            const float *phi = (const float *)(sm + L.work);
-            const float *Dp = (const float *)(sm + L.D_hi);
-            for (int mu = 0; mu < n; mu++) {
-                if (aoc[mu] < 0) continue;  // zero in this block (uniform)
-                const float ph = phi[mu * TC_BP + p];
-                const float4 *drow = (const float4 *)(Dp + mu * np + g4 * nq);
-#pragma unroll
-                for (int k = 0; k < TC_NPMAX / 16; k++) {
-                    if (k * 4 < nq) {
-                        const float4 d4 = drow[k];
-                        Tacc[4 * k] += ph * d4.x;
-                        Tacc[4 * k + 1] += ph * d4.y;
-                        Tacc[4 * k + 2] += ph * d4.z;
-                        Tacc[4 * k + 3] += ph * d4.w;
-                    }
-                }
-            }
-        } else {
+            in1 = true;
             const bool ok1 = __syncthreads_and(tc::wait(&bar1, ph1));
-            ph1 ^= 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (!ok1) {
                 failed = true;
                 break;
             }
-            // the thread's T row segment (columns g4*nq .. +20 lie inside the
-            // 256-column allocation; those past nq are not used)
-            ld20(tT + ((uint32_t)(q * 32) << 16) + g4 * nq, Tacc);
+            ph1 ^= 1;
+            in1 = false;
+            ld20(tT + lanes + c0, Tv);
+        } else {
+            // T on the CUDA cores: this point's row of Phi (hi + lo is the FP32
+            // value) against D's rows, the thread's column quarter
+#pragma unroll
+            for (int j = 0; j < TC_NPMAX / 4; j++) Tv[j] = 0.f;
+            const float *Dp = (const float *)(sm + L.D_hi);
+            for (int mc = 0; mc < np / 4; mc++) {
+                const float4 h4 = *(const float4 *)(sm + L.phi_hi + tc::coff(p, mc * 4, sg));
+                const float4 l4 = *(const float4 *)(sm + L.phi_lo + tc::coff(p, mc * 4, sg));
+                const float ph[4] = {h4.x + l4.x, h4.y + l4.y, h4.z + l4.z, h4.w + l4.w};
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const float4 *drow = (const float4 *)(Dp + (mc * 4 + i) * np + c0);
+#pragma unroll
+                    for (int k = 0; k < TC_NPMAX / 16; k++) {
+                        if (k * 4 < nq) {
+                            const float4 d4 = drow[k];
+                            Tv[4 * k] += ph[i] * d4.x;
+                            Tv[4 * k + 1] += ph[i] * d4.y;
+                            Tv[4 * k + 2] += ph[i] * d4.z;
+                            Tv[4 * k + 3] += ph[i] * d4.w;
+                        }
+                    }
+                }
+            }
+            __syncthreads();  // every thread's reads of the Phi tile precede the partials written over it
         }
+        // ---- E: this thread's share of rho and grad rho, shell by shell:
+        // with u = sum_c T_c d_c (p shell; u = T for an s shell) and Tv = (T_x, T_y, T_z),
+        // rho += g u and grad rho += 2 (g' u d + g Tv)
         {
             float rho = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-            int cur = -1;
             float cg = 0.f, cgp = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, u = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+            bool open = false;
+            int prev_s = -1;
 #pragma unroll
-            for (int k4 = 0; k4 < TC_NPMAX / 16; k4++) {
-                if (k4 * 4 >= nq) break;
-                const int cc = g4 * nq + k4 * 4;
-                const float tv[4] = {Tacc[4 * k4], Tacc[4 * k4 + 1], Tacc[4 * k4 + 2], Tacc[4 * k4 + 3]};
-                const int4 code4 = *(const int4 *)(aoc + cc);
-                const int codes[4] = {code4.x, code4.y, code4.z, code4.w};
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int code = codes[j];
-                    if (code < 0) continue;
-                    const int s = code >> 2, c = (code & 3) - 1;
-                    if (s != cur) {
-                        if (cur >= 0) {
+            for (int j = 0; j < TC_NPMAX / 4; j++) {
+                if (j < nq) {
+                    const ColIt it = col_info(col, c0, j, mask, prev_s);
+                    if (it.fresh) {
+                        if (open) {
                             rho += cg * u;
                             rx += cgp * u * dx + cg * tx;
                             ry += cgp * u * dy + cg * ty;
                             rz += cgp * u * dz + cg * tz;
                         }
-                        cur = s;
-                        cg = Rg[s * TC_BP + p];
-                        cgp = Rgp[s * TC_BP + p];
-                        const float4 dl = *(const float4 *)(shf + s * 8 + hp * 4);
+                        open = true;
+                        cg = gj[j];
+                        cgp = gpj[j];
+                        const float4 dl = *(const float4 *)(shfp + it.s * 8);
                         dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
                         u = tx = ty = tz = 0.f;
                     }
-                    if (c < 0) {
-                        u = tv[j];
-                    } else if (c == 0) {
-                        u += tv[j] * dx; tx = tv[j];
-                    } else if (c == 1) {
-                        u += tv[j] * dy; ty = tv[j];
-                    } else {
-                        u += tv[j] * dz; tz = tv[j];
+                    if (it.code >= 0) {
+                        const float tv = Tv[j];
+                        if (it.c < 0) {
+                            u = tv;
+                        } else if (it.c == 0) {
+                            u += tv * dx; tx = tv;
+                        } else if (it.c == 1) {
+                            u += tv * dy; ty = tv;
+                        } else {
+                            u += tv * dz; tz = tv;
+                        }
                     }
                 }
             }
-            if (cur >= 0) {
+            if (open) {
                 rho += cg * u;
                 rx += cgp * u * dx + cg * tx;
                 ry += cgp * u * dy + cg * ty;
                 rz += cgp * u * dz + cg * tz;
             }
-            part[(g4 * 4 + 0) * TC_BP + p] = rho;
-            part[(g4 * 4 + 1) * TC_BP + p] = rx;
-            part[(g4 * 4 + 2) * TC_BP + p] = ry;
-            part[(g4 * 4 + 3) * TC_BP + p] = rz;
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            // XC in three parts on three warp groups (exchange, VWN5, LYP)
-            if (t < 3 * TC_BP) {
-                const int gi = t >> 7;
-                float r = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-                for (int gq = 0; gq < 4; gq++) {
-                    r += part[(gq * 4 + 0) * TC_BP + p];
-                    gx += part[(gq * 4 + 1) * TC_BP + p];
-                    gy += part[(gq * 4 + 2) * TC_BP + p];
-                    gz += part[(gq * 4 + 3) * TC_BP + p];
-                }
-                gx *= 2.f; gy *= 2.f; gz *= 2.f;
-                const float w = pq4.w;
-                float e = 0.f, vr = 0.f, vs = 0.f;
-                if (w != 0.f) xc::b3lyp_part<float>(gi, r, gx * gx + gy * gy + gz * gz, e, vr, vs);
-                exc += (double)w * (double)e;
-                xcp[(gi * 2 + 0) * TC_BP + p] = vr;
-                xcp[(gi * 2 + 1) * TC_BP + p] = vs;
-                if (gi == 0) {
-                    grd[p] = gx;
-                    grd[TC_BP + p] = gy;
-                    grd[2 * TC_BP + p] = gz;
-                }
-            }
-            __syncthreads();
+            part[(q4 * 4 + 0) * TC_BP + p] = rho;
+            part[(q4 * 4 + 1) * TC_BP + p] = rx;
+            part[(q4 * 4 + 2) * TC_BP + p] = ry;
+            part[(q4 * 4 + 3) * TC_BP + p] = rz;
         }
-        // ---- F: GEMM2 in 32-point slices, ping-pong operand sets.  Warps 0-14
-        // build a slice's operands (lane = point, warp = every 15th shell) and
-        // arrive on the set's named barrier; warp 15 waits there and issues the
-        // slice's MMAs, so the next slice is built while the tensor core runs.
-        {
-            const int nb = TC_THREADS / 32 - 1;  // builder warps
-            const bool issuer = warp == nb;
-            const uint32_t opsz = (uint32_t)(np / 8) * TC_SBO2;
-            for (int k = 0; k < TC_BP / TC_SLICE; k++) {
-                const int set = k & 1;
-                const uint32_t base = L.work + (set ? L.set1 : 0u);
-                const uint32_t at_hi = base, at_lo = base + opsz, x_hi = base + 2 * opsz, x_lo = base + 3 * opsz;
-                if (!issuer) {
-                    // the set's previous MMAs (slice k - 2) must be done before it is rewritten
-                    bool ok = true;
-                    if (k >= 2) ok = tc::wait(&bar2[set], ph2[set]);
-                    if (!ok) s_fail = 1;  // benign race: every writer stores 1
-                    const int pl = lane, pp = k * TC_SLICE + pl;
-                    const float *dlb = shf + owner_h[pp] * 4;
-                    const float4 o4 = pt4[pp];
-                    const float ox = o4.x, oy = o4.y, oz = o4.z, w = o4.w;
-                    const float vr = xcp[pp] + xcp[2 * TC_BP + pp] + xcp[4 * TC_BP + pp];
-                    const float vs2 = 2.f * w * (xcp[TC_BP + pp] + xcp[5 * TC_BP + pp]);
-                    const float a = 0.5f * w * vr;
-                    const float bx = vs2 * grd[pp], by = vs2 * grd[TC_BP + pp], bz = vs2 * grd[2 * TC_BP + pp];
-                    const uint32_t pofs = (uint32_t)(pl >> 2) * TC_LBO2 + (uint32_t)(pl & 3) * 4u;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        // ---- F: XC in three parts on three warp groups (exchange, VWN5, LYP)
+        if (t < 3 * TC_BP) {
+            const int gi = t >> 7;
+            float r = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
-                    for (int j = 0; j < (TC_NSHMAX + 14) / 15; j++) {
-                        const int s = warp + nb * j;
-                        if (s >= nsh) break;
-                        const int l = shxi[s * TC_SHX + 9], a0 = shxi[s * TC_SHX + 10];
-                        const int ncomp = l ? 3 : 1;
-                        const uint32_t off0 = pofs + (uint32_t)(a0 >> 3) * TC_SBO2 + (uint32_t)(a0 & 7) * 16u;
-                        if (!sig[s]) {
-                            for (int c = 0; c < ncomp; c++) {
-                                const int mu = a0 + c;
-                                const uint32_t off = pofs + (uint32_t)(mu >> 3) * TC_SBO2 + (uint32_t)(mu & 7) * 16u;
-                                *(float *)(sm + at_hi + off) = 0.f;
-                                *(float *)(sm + at_lo + off) = 0.f;
-                                *(float *)(sm + x_hi + off) = 0.f;
-                                *(float *)(sm + x_lo + off) = 0.f;
-                            }
-                            continue;
-                        }
-                        const float gg = Rg[s * TC_BP + pp], gp = Rgp[s * TC_BP + pp];
-                        const float4 dl = *(const float4 *)(dlb + s * 8);
-                        const float dx = dl.x + ox, dy = dl.y + oy, dz = dl.z + oz;
-                        const float basev = a * gg + gp * (bx * dx + by * dy + bz * dz);
-                        if (!l) {
-                            const float fh = tc::tf32_hi(gg), xh = tc::tf32_hi(basev);
-                            *(float *)(sm + at_hi + off0) = fh;
-                            *(float *)(sm + at_lo + off0) = gg - fh;
-                            *(float *)(sm + x_hi + off0) = xh;
-                            *(float *)(sm + x_lo + off0) = basev - xh;
-                        } else {
-                            const float dd[3] = {dx, dy, dz}, bb[3] = {bx, by, bz};
-#pragma unroll
-                            for (int c = 0; c < 3; c++) {
-                                const int mu = a0 + c;
-                                const uint32_t off = pofs + (uint32_t)(mu >> 3) * TC_SBO2 + (uint32_t)(mu & 7) * 16u;
-                                const float f = dd[c] * gg, x = dd[c] * basev + bb[c] * gg;
-                                const float fh = tc::tf32_hi(f), xh = tc::tf32_hi(x);
-                                *(float *)(sm + at_hi + off) = fh;
-                                *(float *)(sm + at_lo + off) = f - fh;
-                                *(float *)(sm + x_hi + off) = xh;
-                                *(float *)(sm + x_lo + off) = x - xh;
-                            }
-                        }
-                    }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    tc::bar_arrive(1 + set, TC_THREADS);
-                } else {
-                    tc::bar_sync(1 + set, TC_THREADS);
-                    if (lane == 0 && !s_fail) {
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        for (int s2 = 0; s2 < TC_SLICE / 8; s2++) {
-                            const uint32_t ka = 2u * s2 * TC_LBO2;
-                            const uint64_t ah = tc::sdesc(su + at_hi + ka, TC_LBO2, TC_SBO2);
-                            const uint64_t al = tc::sdesc(su + at_lo + ka, TC_LBO2, TC_SBO2);
-                            const uint64_t bh = tc::sdesc(su + x_hi + ka, TC_LBO2, TC_SBO2);
-                            const uint64_t bl = tc::sdesc(su + x_lo + ka, TC_LBO2, TC_SBO2);
-                            tc::mma(tV, ah, bh, id2, (k > 0 || s2 > 0) ? 1u : 0u);
-                            tc::mma(tV, ah, bl, id2, 1);
-                            tc::mma(tV, al, bh, id2, 1);
-                        }
-                    }
-                    if (lane == 0) tc::commit(&bar2[set]);  // arrives even when nothing was issued
-                }
-                if (k >= 2) ph2[set] ^= 1;
+            for (int gq = 0; gq < 4; gq++) {
+                r += part[(gq * 4 + 0) * TC_BP + p];
+                gx += part[(gq * 4 + 1) * TC_BP + p];
+                gy += part[(gq * 4 + 2) * TC_BP + p];
+                gz += part[(gq * 4 + 3) * TC_BP + p];
             }
-            failed = __syncthreads_or(s_fail != 0);
-        }
-        if (failed) break;
-        // drain the last two slices, then fold this block's V' into registers
-        // (round-to-nearest sums across blocks; the tensor-core accumulation
-        // only spans one block)
-        {
-            const bool okA = tc::wait(&bar2[0], ph2[0]);
-            const bool okB = tc::wait(&bar2[1], ph2[1]);
-            const bool ok = __syncthreads_and(okA && okB);
-            ph2[0] ^= 1;
-            ph2[1] ^= 1;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (!ok) {
-                failed = true;
-                break;
+            gx *= 2.f; gy *= 2.f; gz *= 2.f;
+            float e = 0.f, vr = 0.f, vs = 0.f;
+            if (pw != 0.f) xc::b3lyp_part<float>(gi, r, gx * gx + gy * gy + gz * gz, e, vr, vs);
+            exc += (double)pw * (double)e;
+            xcp[(gi * 2 + 0) * TC_BP + p] = vr;
+            xcp[(gi * 2 + 1) * TC_BP + p] = vs;
+            if (gi == 0) {
+                grd[p] = gx;
+                grd[TC_BP + p] = gy;
+                grd[2 * TC_BP + p] = gz;
             }
-            float v[TC_NPMAX / 4];
-            ld20(tV + ((uint32_t)(q * 32) << 16) + g4 * nq, v);
-#pragma unroll
-            for (int j = 0; j < TC_NPMAX / 4; j++)
-                if (j < nq) vacc[j] += v[j];
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
         __syncthreads();
+        // ---- G: Phi^T and X = a phi + b . grad phi with a = w v_rho / 2, b = 2 w v_sigma
+        // grad rho: s shell X = a g + g' (b . d); p component c: X_c = d_c (a g + g' (b . d)) + b_c g
+        {
+            const float vr = xcp[p] + xcp[2 * TC_BP + p] + xcp[4 * TC_BP + p];
+            const float vs2 = 2.f * pw * (xcp[TC_BP + p] + xcp[5 * TC_BP + p]);
+            const float a = 0.5f * pw * vr;
+            const float bx = vs2 * grd[p], by = vs2 * grd[TC_BP + p], bz = vs2 * grd[2 * TC_BP + p];
+            int prev_s = -1;
+            float dx = 0.f, dy = 0.f, dz = 0.f, S = 0.f;
+#pragma unroll
+            for (int j = 0; j < TC_NPMAX / 4; j++) {
+                if (j < nq) {
+                    const ColIt it = col_info(col, c0, j, mask, prev_s);
+                    if (it.fresh) {
+                        const float4 dl = *(const float4 *)(shfp + it.s * 8);
+                        dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
+                        S = a * gj[j] + gpj[j] * (bx * dx + by * dy + bz * dz);
+                    }
+                    const float dc = it.c == 0 ? dx : (it.c == 1 ? dy : dz);
+                    const float bc = it.c == 0 ? bx : (it.c == 1 ? by : bz);
+                    const float f = it.code < 0 ? 0.f : (it.c < 0 ? gj[j] : dc * gj[j]);
+                    const float x = it.code < 0 ? 0.f : (it.c < 0 ? S : dc * S + bc * gj[j]);
+                    const float fh = tc::tf32_hi(f), xh = tc::tf32_hi(x);
+                    const uint32_t o = tc::soff(c0 + j, p);
+                    *(float *)(sm + L.pt_hi + o) = fh;
+                    *(float *)(sm + L.pt_lo + o) = f - fh;
+                    *(float *)(sm + L.x_hi + o) = xh;
+                    *(float *)(sm + L.x_lo + o) = x - xh;
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        // ---- H: GEMM2 over the block's 128 points (K steps of 8 points: 32 bytes in an atom)
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int k = 0; k < TC_BP / 8; k++) {
+                const uint32_t ko = (uint32_t)(k >> 2) * 1024u + (uint32_t)(k & 3) * 32u;
+                const uint64_t ah = tc::sdesc_sw128(su + L.pt_hi + ko), al = tc::sdesc_sw128(su + L.pt_lo + ko);
+                const uint64_t bh = tc::sdesc_sw128(su + L.x_hi + ko), bl = tc::sdesc_sw128(su + L.x_lo + ko);
+                tc::mma(tV, ah, bh, id2, k > 0);
+                tc::mma(tV, ah, bl, id2, 1);
+                tc::mma(tV, al, bh, id2, 1);
+            }
+            tc::commit(&bar2);
+        }
+        pending = true;
     }
+    if (!failed && pending) failed = !drain();
     if (failed && t == 0) s_fail = 1;
     __syncthreads();
     // ---- flush V' (row mu = this thread's lane row, columns of its quarter) and E_xc
     if (!s_fail && any_block) {
-        const int mu = q * 32 + lane;
+        const int mu = (warp & 3) * 32 + lane;
         Fx *gV = b.accx + md.acc0 + 2 * n * n;  // mixed path: fixed point in every pass
 #pragma unroll
         for (int j = 0; j < TC_NPMAX / 4; j++) {
-            const int nu = g4 * nq + j;
+            const int nu = c0 + j;
             if (j < nq && mu < n && nu < n && vacc[j] != 0.f) acc_add(&gV[mu * n + nu], (TA)vacc[j]);
         }
     }
@@ -729,9 +746,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     if (s_fail && t == 0) {
         atomicOr(&b.st[m].err_flag, 4);
         // give in-flight MMAs a bounded chance to drain before freeing tensor memory
-        if (!FINAL) tc::wait(&bar1, ph1);
-        tc::wait(&bar2[0], ph2[0]);
-        tc::wait(&bar2[1], ph2[1]);
+        if (in1) tc::wait(&bar1, ph1);
+        if (pending) tc::wait(&bar2, ph2);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -743,7 +759,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
 void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
                        cudaStream_t s) {
     const int np = min((max_nbf + 15) & ~15, TC_NPMAX);  // larger molecules return at once
-    const size_t sm = tc_layout(np, min(max_nsh, TC_NSHMAX)).total + 128;
+    const size_t sm = tc_layout(np, min(max_nsh, TC_NSHMAX)).total;
     if (acc_fp64) {
         cudaFuncSetAttribute(grid_xc_tc_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         grid_xc_tc_kernel<double, true><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);
@@ -779,4 +795,3 @@ __global__ void wait_selftest_kernel(int *gave_up, int spins) {
 }
 
 void launch_wait_selftest(int *gave_up, int spins, cudaStream_t s) { wait_selftest_kernel<<<1, 32, 0, s>>>(gave_up, spins); }
-

@@ -424,8 +424,9 @@ void launch_fix_list(const DevBatch &b, cudaStream_t s) { fix_list_kernel<<<b.nm
 // pair data minus the FP32 store block, contracted with the FP64 density and
 // added to the FP64 J'/K' accumulators.
 template <int LA, int LB, int LC, int LD>
-__global__ void __launch_bounds__(128) jk_fix_kernel(DevBatch b, int ci) {
+__global__ void __launch_bounds__(128) jk_fix_kernel(DevBatch b, int ci, int mode) {
     const int m = blockIdx.y;
+    if (mode == 0 && !b.st[m].active) return;
     const int cntm = min(b.fixcount[m * 6 + ci], RKS_FIX_CAP);
     const MolDesc md = b.mol[m];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cntm; k += gridDim.x * blockDim.x) {
@@ -502,12 +503,12 @@ __global__ void __launch_bounds__(128) jk_fix_kernel(DevBatch b, int ci) {
     }
 }
 
-void launch_jk_fix(const DevBatch &b, cudaStream_t s) {
+void launch_jk_fix(const DevBatch &b, int mode, cudaStream_t s) {
     const dim3 g(8, b.nmol);  // grid-stride over each molecule's list
-    jk_fix_kernel<0, 0, 0, 0><<<g, 128, 0, s>>>(b, 0);
-    jk_fix_kernel<1, 0, 0, 0><<<g, 128, 0, s>>>(b, 1);
-    jk_fix_kernel<1, 0, 1, 0><<<g, 128, 0, s>>>(b, 2);
-    jk_fix_kernel<1, 1, 0, 0><<<g, 128, 0, s>>>(b, 3);
-    jk_fix_kernel<1, 1, 1, 0><<<g, 128, 0, s>>>(b, 4);
-    jk_fix_kernel<1, 1, 1, 1><<<g, 128, 0, s>>>(b, 5);
+    jk_fix_kernel<0, 0, 0, 0><<<g, 128, 0, s>>>(b, 0, mode);
+    jk_fix_kernel<1, 0, 0, 0><<<g, 128, 0, s>>>(b, 1, mode);
+    jk_fix_kernel<1, 0, 1, 0><<<g, 128, 0, s>>>(b, 2, mode);
+    jk_fix_kernel<1, 1, 0, 0><<<g, 128, 0, s>>>(b, 3, mode);
+    jk_fix_kernel<1, 1, 1, 0><<<g, 128, 0, s>>>(b, 4, mode);
+    jk_fix_kernel<1, 1, 1, 1><<<g, 128, 0, s>>>(b, 5, mode);
 }

@@ -25,11 +25,14 @@ int launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf
 // step one thread per listed quartet recomputes it in FP64 and contracts
 // (I64 - I32) with D into the FP64 accumulators.
 void launch_fix_list(const DevBatch &b, cudaStream_t s);
-void launch_jk_fix(const DevBatch &b, cudaStream_t s);
+void launch_jk_fix(const DevBatch &b, int mode, cudaStream_t s);
 // AO + density + B3LYP + V_xc on the grid; acc_fp64 and mode as above.
 // skip_tc: leave out the molecules the tensor-core kernel takes (grid_tc_fits).
 void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int skip_tc, int max_nbf, int max_nsh,
                     cudaStream_t s);
+// Per-block shell significance masks of the tensor-core grid kernel (setup,
+// after the grid is built; molecules the kernel does not take are skipped).
+void launch_grid_masks(const DevBatch &b, long long nblk_total, const int *blk_mol, cudaStream_t s);
 // Tensor-core (tcgen05, 3xTF32) version for the mixed path; takes the
 // molecules with grid_tc_fits() and skips the others.  acc_fp64 = 1 is the
 // final step: density contraction on the CUDA cores (round-to-nearest sums).
@@ -37,7 +40,18 @@ void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, in
                        cudaStream_t s);
 // Per-molecule FP64 SCF stages.
 void launch_scf_init(const DevBatch &b, cudaStream_t s);
-void launch_scf_guess(const DevBatch &b, int max_nbf, cudaStream_t s);
+// only_rechecked: guess only for the molecules marked by launch_mark_recheck
+void launch_scf_guess(const DevBatch &b, int max_nbf, int only_rechecked, cudaStream_t s);
+// Fixed protocol, after the iterations: molecules whose DIIS error exceeds
+// recheck_fp64_err (or whose status is not OK) are marked for the FP64 redo
+// (rechecked = 2, inactive; their indices appended to list); those above
+// recheck_err are reset to iterate again from the initial guess (active,
+// rechecked = 1); the others become inactive.  counts[0] / counts[1] get the
+// number of each; list has room for every molecule.
+void launch_mark_recheck(const DevBatch &b, int *counts, int *list, cudaStream_t s);
+// Results of the FP64 redo: child molecule k replaces parent molecule map[k]
+// (state, orbital energies, output density); marks it rechecked = 2.
+void launch_adopt(const DevBatch &parent, const DevBatch &child, const int *map, int nchild, cudaStream_t s);
 void launch_scf_step(const DevBatch &b, int acc_fp64, int max_nbf, cudaStream_t s);
 void launch_scf_final(const DevBatch &b, int acc_fp64, int max_nbf, cudaStream_t s);
 void launch_fock_only(const DevBatch &b, int acc_fp64, cudaStream_t s);
@@ -46,3 +60,5 @@ void launch_count_active(const DevBatch &b, int *out, cudaStream_t s);
 void launch_eval_xc(int n, const double *rho, const double *sigma, double *out, int fp32, cudaStream_t s);
 // Waits on an mbarrier that is never arrived at, `spins` bounded polls; *gave_up = 1 on expiry.
 void launch_wait_selftest(int *gave_up, int spins, cudaStream_t s);
+// Peak-rate probe (probe.cu): operations per second of one RKS_PROBE_* kind.
+int probe_rate(int kind, cudaStream_t s, double *ops_per_s);

@@ -103,17 +103,18 @@ __global__ void scf_init_kernel(DevBatch b) {
         st.Enuc = e;
         st.E = 0.0; st.E_prev = 0.0; st.Exc = 0.0; st.max_err = 0.0;
         st.diis_n = 0; st.diis_head = 0; st.iter = 0; st.active = 1; st.converged = 0;
-        st.status = RKS_STATUS_OK_; st.eigh_fail = 0; st.c_valid = 0;
+        st.status = RKS_STATUS_OK_; st.eigh_fail = 0; st.c_valid = 0; st.rechecked = 0;
     }
 }
 
 void launch_scf_init(const DevBatch &b, cudaStream_t s) { scf_init_kernel<<<b.nmol, 256, 0, s>>>(b); }
 
 // ------------------------------------------- orthogonaliser + core guess
-__global__ void scf_guess_kernel(DevBatch b, int nmax) {
+__global__ void scf_guess_kernel(DevBatch b, int nmax, int only_rechecked) {
     extern __shared__ unsigned char raw[];
     ScfSmem sm = scf_smem(raw, nmax);
     const int m = blockIdx.x;
+    if (only_rechecked && !b.st[m].rechecked) return;
     const MolDesc md = b.mol[m];
     const int n = md.nbf, nn = n * n;
     double *S = b.mat + md.mat0 + (long long)M_S * nn;
@@ -174,10 +175,84 @@ __global__ void scf_guess_kernel(DevBatch b, int nmax) {
     }
 }
 
-void launch_scf_guess(const DevBatch &b, int max_nbf, cudaStream_t s) {
+void launch_scf_guess(const DevBatch &b, int max_nbf, int only_rechecked, cudaStream_t s) {
     const size_t sm = scf_smem_bytes(max_nbf);
     cudaFuncSetAttribute(scf_guess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    scf_guess_kernel<<<b.nmol, 256, sm, s>>>(b, max_nbf);
+    scf_guess_kernel<<<b.nmol, 256, sm, s>>>(b, max_nbf, only_rechecked);
+}
+
+// Fixed protocol: after the iterations, a molecule still far from its fixed
+// point (DIIS error above recheck_err) has an energy E[D_n] that is not
+// stationary, so it depends on the path of the iterations and the FP32
+// rounding of the mixed Fock builds steers it.  Such molecules start again
+// from the initial guess (fresh DIIS history, same iteration count) with
+// every Fock build at the final step's precision.  Molecules that have not
+// converged at all (DIIS error above recheck_fp64_err, or a bad status) are
+// redone on the FP64 path: there the path is sensitive to rounding far below
+// FP32 (paper Section 3.2, "Numerical Error": the float32 results are taken
+// for the converged ~99%, the rest recomputed in float64).  The rest wait for
+// the final step.  The decision reads only the molecule's own state.
+__global__ void mark_recheck_kernel(DevBatch b, int *counts, int *list) {
+    __shared__ int tot;
+    if (threadIdx.x == 0) tot = 0;
+    __syncthreads();
+    int n = 0;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < b.nmol; m += gridDim.x * blockDim.x) {
+        MolState &st = b.st[m];
+        const bool bad = st.status != RKS_STATUS_OK_ || !(st.max_err <= b.recheck_fp64_err);
+        const bool fp64 = !st.rechecked && st.status != RKS_STATUS_S_ILL_ && b.recheck_fp64_err > 0.0 && bad;
+        const bool again = !st.rechecked && !fp64 && st.status != RKS_STATUS_S_ILL_ &&
+                           (st.status != RKS_STATUS_OK_ || !(st.max_err <= b.recheck_err));
+        if (fp64) {
+            st.rechecked = 2;
+            st.active = 0;
+            list[atomicAdd(&counts[1], 1)] = m;
+        } else if (again) {
+            st.rechecked = 1;
+            st.active = 1;
+            st.iter = 0;
+            st.diis_n = 0;
+            st.diis_head = 0;
+            st.E = 0.0;
+            st.E_prev = 0.0;
+            st.max_err = 0.0;
+            st.status = RKS_STATUS_OK_;
+            st.eigh_fail = 0;
+            st.c_valid = 0;
+            n++;
+        } else {
+            st.active = 0;
+        }
+    }
+    if (n) atomicAdd(&tot, n);
+    __syncthreads();
+    if (threadIdx.x == 0 && tot) atomicAdd(&counts[0], tot);
+}
+
+void launch_mark_recheck(const DevBatch &b, int *counts, int *list, cudaStream_t s) {
+    cudaMemsetAsync(counts, 0, 2 * sizeof(int), s);
+    mark_recheck_kernel<<<(b.nmol + 255) / 256, 256, 0, s>>>(b, counts, list);
+}
+
+// One block per redone molecule: its FP64 state and output density replace
+// the parent's (the parent's own final step for it is discarded).
+__global__ void adopt_kernel(DevBatch parent, DevBatch child, const int *map) {
+    const int k = blockIdx.x, m = map[k];
+    const MolDesc mp = parent.mol[m], mc = child.mol[k];
+    const long long nn = nbf2(mp.nbf);
+    const double *src = child.mat + mc.mat0 + (long long)M_D * nn;
+    double *dst = parent.mat + mp.mat0 + (long long)M_D * nn;
+    for (long long i = threadIdx.x; i < nn; i += blockDim.x) dst[i] = src[i];
+    const int words = (int)(sizeof(MolState) / sizeof(int));
+    const int *s = (const int *)(child.st + k);
+    int *d = (int *)(parent.st + m);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+    if (threadIdx.x == 0) parent.st[m].rechecked = 2;
+}
+
+void launch_adopt(const DevBatch &parent, const DevBatch &child, const int *map, int nchild, cudaStream_t s) {
+    if (nchild > 0) adopt_kernel<<<nchild, 256, 0, s>>>(parent, child, map);
 }
 
 // ----------------------------------------------------- Fock assembly

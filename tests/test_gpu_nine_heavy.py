@@ -1,10 +1,17 @@
-"""GPU parity on the seeded 9-heavy-atom molecule (seed 1) and a few workload
-molecules (9-11 heavy atoms, seed 2): stage by stage at a fixed density
-(the oracle's core-Hamiltonian guess), then the whole SCF.
+"""GPU parity on the seeded 9-heavy-atom molecule (seed 1; nbf 61, padded to
+64 in the tensor-core grid kernel): stage by stage at a fixed density (the
+oracle's core-Hamiltonian guess), then the whole SCF.  The workload molecules
+that pad to 80 are in test_gpu_workload.py.
 
-Tolerances as in test_gpu_parity.py; stage values at a fixed density use the
-FP64 path (<= 1e-10 abs on J/K/V_xc/E) and the mixed path (<= 2e-5 abs on the
-energy at that density, which is not variational there).
+Tolerances: stage values at a fixed density use the FP64 path (<= 1e-10 abs
+on J/K/V_xc, 1e-9 on E) and the mixed final step (<= 2e-5 abs on J/K/V_xc
+elements; the energy pieces E_J = tr(D J)/2, E_K = -a0 tr(D K)/4 and E_xc
+within 1e-5 Ha, E within 5e-6 Ha).  The energy-piece bound is the rounding
+floor of an FP32 store: ~2.5e6 stored elements, each off by up to 2^-24 of
+its value, summed against densities of order 1 at the core guess (a random
+walk of ~1e-6 .. 1e-5 Ha; measured 3.5e-6 Ha on E_J).  E itself sits lower
+(1.9e-7 measured): the stored quartets with Q_pq Q_rs >= 0.1 are recomputed
+in FP64.
 """
 import numpy as np
 import pytest
@@ -85,7 +92,9 @@ def test_c1_setup_and_fock_mixed(c1):
         assert np.max(np.abs(J - parts0["J"])) < 2e-5
         assert np.max(np.abs(K - parts0["K"])) < 2e-5
         assert np.max(np.abs(V - parts0["Vxc"])) < 2e-5
-        assert abs(sc[0] - E0) < 2e-4
+        assert abs(dEJ) < 1e-5 and abs(dEK) < 1e-5
+        assert abs(sc[1] - parts0["Exc"]) < 1e-5
+        assert abs(sc[0] - E0) < 5e-6
 
 
 @pytest.fixture(scope="module")

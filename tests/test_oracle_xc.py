@@ -7,7 +7,8 @@ Independent references:
   E_x[rho_a, 0] = E_x^closed[2 rho_a] / 2.
 * B88 correction vanishes for a uniform gas (sigma -> 0).
 * VWN5: high-density limit slope d eps_c / d ln r_s -> (1 - ln 2)/pi^2 (Gell-Mann-Brueckner),
-  and agreement with the independent Perdew-Wang 1992 fit to the same QMC data.
+  the exact high-density constant (as built into the Perdew-Wang 1992 fit), and
+  agreement with that independent fit to the same QMC data.
 * LYP: the Laplacian-free Miehlich form integrates to the same energy as the
   original Lee-Yang-Parr form (with t_W and the Laplacian) for spherical densities.
 * Potentials: complex-step derivatives vs central finite differences; and
@@ -62,6 +63,20 @@ def test_vwn5_high_density_slope():
     for rs in (1e-6, 1e-8):
         slope = (xc.vwn5_eps(rs * math.exp(h)) - xc.vwn5_eps(rs * math.exp(-h))) / (2 * h)
         assert slope == pytest.approx((1 - math.log(2)) / math.pi ** 2, rel=2e-4)
+
+
+def test_vwn5_high_density_constant():
+    """eps_c = A ln r_s - c1 + O(r_s ln r_s) as r_s -> 0, with c1 the exact
+    high-density constant of the uniform gas.  Perdew-Wang 1992 build it into
+    their fit through beta1 = exp(-c1 / 2A) / 2A, so c1 = -2A ln(2A beta1) from
+    their printed A = 0.031091, beta1 = 7.5957 (0.046644).  VWN5's Pade form
+    reproduces the same constant; a slip of a few units in the third or fourth
+    digit of b, c or x0 moves it by more than the tolerance."""
+    A_pw, beta1 = 0.031091, 7.5957
+    c1 = -2 * A_pw * math.log(2 * A_pw * beta1)
+    for rs in (1e-9, 1e-11):
+        const = xc.vwn5_eps(rs) - xc.VWN_A * math.log(rs)
+        assert const == pytest.approx(-c1, abs=3e-6)
 
 
 def test_vwn5_matches_pw92_fit():
