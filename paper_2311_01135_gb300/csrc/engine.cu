@@ -304,6 +304,7 @@ struct rks_batch {
     std::vector<int32_t> hZ, hnat;
     std::vector<double> hxyz;
     std::vector<long long> hatom0;
+    TcClasses tcc{};                   // molecules of the tensor-core grid kernel by size class
     rks_batch *child = nullptr;        // FP64 batch of the molecules being redone
     int *child_map = nullptr;          // device: child molecule -> parent molecule
     cudaEvent_t child_done = nullptr;
@@ -344,16 +345,23 @@ static int validate(int natom, const int *Z, const double *xyz, int *nbf_out) {
     return RKS_OK;
 }
 
+// Release the FP64 redo batch of the previous run.  Its results are read by
+// the adopt kernel on the parent's stream, which may still be queued (a
+// caller may enqueue the next run without waiting): drain the parent's
+// stream before the child's memory goes.
 static void child_free(rks_batch *b) {
-    if (b->child) rks_batch_destroy(b->child);
+    if (b->child) {
+        cudaStreamSynchronize(b->stream);
+        rks_batch_destroy(b->child);
+    }
     b->child = nullptr;
+    b->child_map = nullptr;
     if (b->child_done) cudaEventDestroy(b->child_done);
     b->child_done = nullptr;
 }
 
 extern "C" int rks_batch_destroy(rks_batch *b) {
     if (!b) return RKS_EINVAL;
-    cudaStreamSynchronize(b->stream);  // an adopt kernel may still read the child
     child_free(b);
     for (auto &gx : b->graph)
         if (gx) cudaGraphExecDestroy(gx);
@@ -569,6 +577,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
         (rc = dalloc(b, &b->blk_mol, b->nblk_total)) || (rc = dalloc(b, &b->active_d, 1)) ||
         (rc = dalloc(b, &b->recheck_d, 2)) || (rc = dalloc(b, &b->recheck_list, nmol)) ||
         (o.precision == RKS_MIXED && (rc = dalloc(b, &d.blk_mask, 2 * b->nblk_total))) ||
+        (o.precision == RKS_MIXED && (rc = dalloc(b, (int **)&b->tcc.list, nmol))) ||
         (rc = dalloc(b, &d.jk_next, nmol))) {
         rks_batch_destroy(b);
         return rc;
@@ -601,6 +610,23 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     UP(dcand, hcand);
     UP(dcm, hcand_mol);
     UP(b->blk_mol, hblk_mol);
+    if (b->tcc.list) {
+        // tensor-core grid kernel: molecules by padded basis size class
+        std::vector<int> lst;
+        for (int k = 0; k < 5; k++) {
+            b->tcc.off[k] = (int)lst.size();
+            b->tcc.max_nsh[k] = 0;
+            for (int m = 0; m < nmol; m++) {
+                const MolDesc &q = b->md[m];
+                if (grid_tc_fits(q.nbf, q.nsh) && ((q.nbf + 15) / 16) - 1 == k) {
+                    lst.push_back(m);
+                    b->tcc.max_nsh[k] = std::max(b->tcc.max_nsh[k], q.nsh);
+                }
+            }
+            b->tcc.count[k] = (int)lst.size() - b->tcc.off[k];
+        }
+        UP((int *)b->tcc.list, lst);
+    }
 #undef UP
     b->hZ = hZ;
     b->hxyz = haxyz;
@@ -706,7 +732,7 @@ static int fock_pass(rks_batch *b, int prec, int mode) {
             if (any_tc) {
                 const int nchunk_tc = c->opt.grid_chunks > 0 ? c->opt.grid_chunks : 16;
                 StageScope sc(c, s, mode ? "grid_xc_tc_final" : (gr_fin ? "grid_xc_tc_precise" : "grid_xc_tc"), 0);
-                launch_grid_xc_tc(d, nchunk_tc, gr_fin, mode, b->max_nbf, b->max_nsh, s);
+                launch_grid_xc_tc(d, nchunk_tc, gr_fin, mode, b->tcc, s);
             }
         }
         if (need_cc) {

@@ -49,9 +49,10 @@
 #define TC_BP 128
 #define TC_NPMAX RKS_TC_NPMAX   // padded basis size this kernel handles
 #define TC_NSHMAX RKS_TC_NSHMAX // shells this kernel handles (one 64-bit mask per block)
-#define TC_TMEM_COLS 256
+#define TC_TMEM_COLS 512
 #define TC_TCOL 0               // TMEM columns of T (GEMM1)
-#define TC_VCOL 128             // and of V' (GEMM2)
+#define TC_VCOL 128             // of V' (GEMM2, one block)
+#define TC_SCOL 256             // and of the running sum of V' over the CTA's blocks
 #define TC_SPIN_LIMIT 4000000  // polls before a wait gives up: >= ~40 ms, far above any MMA here
 #define TC_THREADS 512
 #define TC_SCREEN 1e-9f         // per-block AO screening threshold, iterations
@@ -195,6 +196,22 @@ __device__ __forceinline__ void ld20(uint32_t taddr, float *v) {
     for (int j = 0; j < 20; j++) v[j] = __uint_as_float(r[j]);
 }
 
+// Four TMEM columns of this thread's lane row (load, wait), and the store back.
+__device__ __forceinline__ void ld4(uint32_t taddr, float *v) {
+    uint32_t r0, r1, r2, r3;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3) : : "memory");
+    v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
+}
+__device__ __forceinline__ void st4(uint32_t taddr, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3]))
+                 : "memory");
+}
+
 // Lower bound on the distance from a shell centre to any point of a block:
 // the points of owner h lie on atom-centred spheres with radii in [lo, hi],
 // and the centre sits at distance d from that atom.
@@ -299,27 +316,411 @@ void launch_grid_masks(const DevBatch &b, long long nblk_total, const int *blk_m
 }
 
 // ------------------------------------------------------------ the kernel
-// Column loop helper: the thread's columns c0 .. c0 + nq - 1 (nq <= 20), the
-// code of each (shell, component), whether it is significant in this block,
-// and when a new shell starts (the same for every thread of a warp group).
-struct ColIt {
-    int code;   // shell << 2 | (component + 1); -1: padding or screened
-    int s, c;   // shell, component (-1 for an s shell)
-    bool fresh; // first column of its shell in this thread's run
-    bool share; // same atom and exponents as the previous column's shell
+// What a CTA keeps across its blocks (set up once, before the block loop).
+struct TcCta {
+    const MolDesc *md;
+    TcSmem L;
+    unsigned char *sm;
+    const int *col;
+    const float *shx, *shf;
+    float *part, *xcp, *grd;
+    uint64_t *bar1, *bar2;
+    int *s_fail;
+    uint32_t su, sg, tT, tV, tS, lanes, id;
+    int m, chunk, nchunk, n, nsh, np, t, lane, warp, p, q4, c0;
 };
-__device__ __forceinline__ ColIt col_info(const int *col, int c0, int j, unsigned long long mask, int &prev_s) {
-    ColIt it;
-    const int raw = col[c0 + j];
-    const int s = raw >= 0 ? (raw >> 2) & 63 : -1;
-    const bool on = raw >= 0 && ((mask >> s) & 1ull);
-    it.code = on ? (raw & 0xff) : -1;
-    it.s = s;
-    it.c = (raw & 3) - 1;
-    it.fresh = on && (j == 0 || s != prev_s);
-    it.share = on && j > 0 && (raw & 0x100) && prev_s >= 0 && prev_s != s;
-    prev_s = on ? s : -1;
-    return it;
+
+// The thread's columns c0 .. c0 + NQ - 1 are described once per CTA by bit
+// masks (warp-uniform: a warp's 32 threads share the quarter): valid (not
+// padding), start (first column of its shell in the run), share (2p column
+// right after its atom's 2s column, same exponents) and a 2-bit component
+// code (0 s, 1..3 p_x, p_y, p_z).  Per block only the significance bits
+// change: one ballot over the warp's lanes.
+struct ColBits {
+    uint32_t valid, start, share;
+    uint64_t comp;
+};
+
+template <int NQ> __device__ __forceinline__ ColBits col_bits(const int *col, int c0) {
+    ColBits cb{0u, 0u, 0u, 0ull};
+    int prev = -1;
+#pragma unroll
+    for (int j = 0; j < NQ; j++) {
+        const int raw = col[c0 + j];
+        if (raw >= 0) {
+            const int s = (raw >> 2) & 63;
+            cb.valid |= 1u << j;
+            if (j == 0 || s != prev) cb.start |= 1u << j;
+            if (raw & 0x100) cb.share |= 1u << j;
+            cb.comp |= (uint64_t)(raw & 3) << (2 * j);
+            prev = s;
+        } else {
+            prev = -1;
+        }
+    }
+    return cb;
+}
+
+#define TC_ON(j) ((on >> (j)) & 1u)
+#define TC_FRESH(j) (TC_ON(j) && ((cb.start >> (j)) & 1u))
+#define TC_COMP(j) ((int)((cb.comp >> (2 * (j))) & 3ull))
+#define TC_SHELL(j) ((C.col[C.c0 + (j)] >> 2) & 63)
+
+// G for one value of c0 & 7 (B = 0 or 4, known at compile time): the
+// swizzled offsets of the thread's column rows are a per-thread base plus
+// compile-time constants and one of eight per-thread XOR terms.
+template <int NQ, int B>
+__device__ __forceinline__ void tc_write_gemm2(const TcCta &C, const ColBits &cb, uint32_t on, const float *gj,
+                                               const float *gpj, const float *shfp, float px, float py, float pz,
+                                               float a, float bx, float by, float bz) {
+    const uint32_t pc = (uint32_t)(C.p >> 2) & 7u;
+    const uint32_t tbase = (uint32_t)(C.c0 >> 3) * 4096u + (uint32_t)(C.p >> 5) * 1024u + (uint32_t)(C.p & 3) * 4u;
+    unsigned char *pth = C.sm + C.L.pt_hi + tbase, *ptl = C.sm + C.L.pt_lo + tbase;
+    unsigned char *xh_ = C.sm + C.L.x_hi + tbase, *xl_ = C.sm + C.L.x_lo + tbase;
+    float dx = 0.f, dy = 0.f, dz = 0.f, S = 0.f;
+#pragma unroll
+    for (int j = 0; j < NQ; j++) {
+        constexpr int dummy = 0;
+        (void)dummy;
+        const int r = (B + j) & 7, grp = (B + j) >> 3;
+        if (TC_FRESH(j)) {
+            const float4 dl = *(const float4 *)(shfp + TC_SHELL(j) * 8);
+            dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
+            S = a * gj[j] + gpj[j] * (bx * dx + by * dy + bz * dz);
+        }
+        const int c = TC_COMP(j);
+        const float dc = c == 1 ? dx : (c == 2 ? dy : dz);
+        const float bc = c == 1 ? bx : (c == 2 ? by : bz);
+        const bool o = TC_ON(j);
+        const float f = o ? (c == 0 ? gj[j] : dc * gj[j]) : 0.f;
+        const float x = o ? (c == 0 ? S : dc * S + bc * gj[j]) : 0.f;
+        const float fh = tc::tf32_hi(f), xh = tc::tf32_hi(x);
+        const uint32_t off = (uint32_t)grp * 4096u + (uint32_t)r * 128u + ((pc ^ (uint32_t)r) << 4);
+        *(float *)(pth + off) = fh;
+        *(float *)(ptl + off) = f - fh;
+        *(float *)(xh_ + off) = xh;
+        *(float *)(xl_ + off) = x - xh;
+    }
+}
+
+// The block loop of one CTA for threads owning NQ columns each, then the
+// flush of V' and E_xc.
+template <typename TA, bool FINAL, int NQ>
+__device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
+    const MolDesc &md = *C.md;
+    const int t = C.t, p = C.p, lane = C.lane;
+    const ColBits cb = col_bits<NQ>(C.col, C.c0);
+    // the lane's own column for the per-block significance ballot
+    const int rawl = lane < NQ ? C.col[C.c0 + lane] : -1;
+    const int sl = rawl >= 0 ? (rawl >> 2) & 63 : 0;
+    const uint32_t phi_base = (uint32_t)(p >> 3) * C.sg + (uint32_t)(C.c0 >> 2) * 128u + (uint32_t)(p & 7) * 16u;
+    uint32_t ph1 = 0, ph2 = 0;
+    bool pending = false;  // a GEMM2 in flight whose V' is not yet in vacc
+    bool in1 = false;      // a GEMM1 in flight
+    bool any_block = false, failed = false;
+    double exc = 0.0;
+    bool first = true;  // the running sum of V' in TMEM is not yet written
+
+    const float *gxp = (const float *)b.gx + md.pts0, *gyp = (const float *)b.gy + md.pts0;
+    const float *gzp = (const float *)b.gz + md.pts0, *gwp = (const float *)b.gw + md.pts0;
+    const unsigned long long *bmask = b.blk_mask + 2 * (md.pts0 / TC_BP) + (FINAL ? 1 : 0);
+    const int npa = b.n_rad * b.n_theta * b.n_phi;
+    float nx = gxp[C.chunk * TC_BP + p], ny = gyp[C.chunk * TC_BP + p], nz = gzp[C.chunk * TC_BP + p];
+    float nw = gwp[C.chunk * TC_BP + p];
+    int shf_owner = -1;  // owner atom the shf table was built for
+    float *shf_w = const_cast<float *>(C.shf);
+
+    // the pending GEMM2's V' row segment added to the running sum (FP32
+    // round-to-nearest across blocks; the tensor cores' accumulation only
+    // spans one block)
+    auto drain = [&]() -> bool {
+        const bool ok = __syncthreads_and(tc::wait(C.bar2, ph2));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) return false;  // still pending: the exit path waits on the same phase
+        ph2 ^= 1;
+#pragma unroll
+        for (int kc = 0; kc < NQ / 4; kc++) {
+            float v[4], w[4];
+            ld4(C.tV + C.lanes + C.c0 + 4 * kc, v);
+            if (!first) {
+                ld4(C.tS + C.lanes + C.c0 + 4 * kc, w);
+#pragma unroll
+                for (int i = 0; i < 4; i++) v[i] += w[i];
+            }
+            st4(C.tS + C.lanes + C.c0 + 4 * kc, v);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        first = false;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        return true;
+    };
+
+    for (int blk = C.chunk; blk < md.nblk; blk += C.nchunk) {
+        const int p0 = blk * TC_BP;
+        const int own0 = min(p0 / npa, md.natom - 1);
+        const float px = nx, py = ny, pz = nz, pw = nw;
+        if (blk + C.nchunk < md.nblk) {  // this thread's point of the next block
+            const int i1 = p0 + C.nchunk * TC_BP + p;
+            nx = gxp[i1]; ny = gyp[i1]; nz = gzp[i1]; nw = gwp[i1];
+        }
+        const unsigned long long mask = bmask[2 * blk];
+        if (mask == 0ull) continue;  // every AO below the screen: rho under the XC cutoff everywhere
+        any_block = true;
+        if (own0 != shf_owner) {  // R_owner - C for the block's (at most two) owners
+            __syncthreads();
+            for (int i = t; i < 2 * C.nsh; i += TC_THREADS) {
+                const int hh = i / C.nsh, s = i % C.nsh;
+                const int A = min(own0 + hh, md.natom - 1);
+                const double *ra = b.axyz + (md.atom0 + A) * 3, *rc = b.sh_xyz + (md.sh0 + s) * 3;
+                *(float4 *)(shf_w + s * 8 + hh * 4) =
+                    make_float4((float)(ra[0] - rc[0]), (float)(ra[1] - rc[1]), (float)(ra[2] - rc[2]), 0.f);
+            }
+            shf_owner = own0;
+            __syncthreads();
+        }
+        const int hp = min((p0 + p) / npa, md.natom - 1) - own0;
+        const float *shfp = C.shf + hp * 4;
+        const uint32_t on = __ballot_sync(0xffffffffu, lane < NQ && rawl >= 0 && ((mask >> sl) & 1ull)) & cb.valid;
+
+        // ---- A: radial values g = sum c e^(-a r^2), g' = sum -2ac e^(-a r^2) of the thread's columns
+        float gj[NQ], gpj[NQ];
+        {
+            float e0 = 0.f, e1 = 0.f, e2 = 0.f, cg = 0.f, cgp = 0.f;
+#pragma unroll
+            for (int j = 0; j < NQ; j++) {
+                if (TC_FRESH(j)) {
+                    const int sh = TC_SHELL(j);
+                    const float4 xa = *(const float4 *)(C.shx + sh * TC_SHX);
+                    const float4 xb = *(const float4 *)(C.shx + sh * TC_SHX + 4);
+                    const float xc9 = C.shx[sh * TC_SHX + 8];
+                    const bool share = j > 0 && ((cb.share >> j) & 1u) && TC_ON(j > 0 ? j - 1 : 0);
+                    if (!share) {
+                        const float4 dl = *(const float4 *)(shfp + sh * 8);
+                        const float dx = dl.x + px, dy = dl.y + py, dz = dl.z + pz;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        e0 = __expf(-xa.x * r2);
+                        e1 = __expf(-xa.y * r2);
+                        e2 = __expf(-xa.z * r2);
+                    }
+                    cg = xa.w * e0 + xb.x * e1 + xb.y * e2;
+                    cgp = xb.z * e0 + xb.w * e1 + xc9 * e2;
+                }
+                gj[j] = TC_ON(j) ? cg : 0.f;
+                gpj[j] = TC_ON(j) ? cgp : 0.f;
+            }
+        }
+        // ---- B: the previous block's V'
+        if (pending) {
+            if (!drain()) {
+                failed = true;
+                break;
+            }
+            pending = false;
+        }
+        // ---- C: Phi (hi, lo) into the [point][AO] tile
+        {
+            float dx = 0.f, dy = 0.f, dz = 0.f;
+#pragma unroll
+            for (int kc = 0; kc < NQ / 4; kc++) {
+                float v[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int j = kc * 4 + i;
+                    if (TC_FRESH(j)) {
+                        const float4 dl = *(const float4 *)(shfp + TC_SHELL(j) * 8);
+                        dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
+                    }
+                    const int c = TC_COMP(j);
+                    const float dc = c == 1 ? dx : (c == 2 ? dy : dz);
+                    v[i] = c == 0 ? gj[j] : dc * gj[j];  // gj is 0 in screened columns
+                }
+                float4 hi, lo;
+                tc::split4(v, hi, lo);
+                *(float4 *)(C.sm + C.L.phi_hi + phi_base + kc * 128) = hi;
+                *(float4 *)(C.sm + C.L.phi_lo + phi_base + kc * 128) = lo;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        float Tv[NQ];  // FINAL: this thread's T columns from the CUDA cores
+        if constexpr (!FINAL) {
+            if (t == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int s = 0; s < C.np / 8; s++) {
+                    const uint32_t ka = 2u * s * 128u;
+                    const uint64_t ah = tc::sdesc(C.su + C.L.phi_hi + ka, 128, C.sg);
+                    const uint64_t al = tc::sdesc(C.su + C.L.phi_lo + ka, 128, C.sg);
+                    const uint64_t bh = tc::sdesc(C.su + C.L.D_hi + ka, 128, C.sg);
+                    const uint64_t bl = tc::sdesc(C.su + C.L.D_lo + ka, 128, C.sg);
+                    tc::mma(C.tT, ah, bh, C.id, s > 0);
+                    tc::mma(C.tT, ah, bl, C.id, 1);
+                    tc::mma(C.tT, al, bh, C.id, 1);
+                }
+                tc::commit(C.bar1);
+            }
+            in1 = true;
+            const bool ok1 = __syncthreads_and(tc::wait(C.bar1, ph1));
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok1) {
+                failed = true;
+                break;
+            }
+            ph1 ^= 1;
+            in1 = false;
+        } else {
+            // T on the CUDA cores: this point's row of Phi (hi + lo is the FP32
+            // value) against D's rows, the thread's column quarter
+#pragma unroll
+            for (int j = 0; j < NQ; j++) Tv[j] = 0.f;
+            const float *Dp = (const float *)(C.sm + C.L.D_hi);
+            const uint32_t rowb = (uint32_t)(p >> 3) * C.sg + (uint32_t)(p & 7) * 16u;
+            for (int mc = 0; mc < C.np / 4; mc++) {
+                const float4 h4 = *(const float4 *)(C.sm + C.L.phi_hi + rowb + mc * 128);
+                const float4 l4 = *(const float4 *)(C.sm + C.L.phi_lo + rowb + mc * 128);
+                const float ph[4] = {h4.x + l4.x, h4.y + l4.y, h4.z + l4.z, h4.w + l4.w};
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const float4 *drow = (const float4 *)(Dp + (mc * 4 + i) * C.np + C.c0);
+#pragma unroll
+                    for (int k = 0; k < NQ / 4; k++) {
+                        const float4 d4 = drow[k];
+                        Tv[4 * k] += ph[i] * d4.x;
+                        Tv[4 * k + 1] += ph[i] * d4.y;
+                        Tv[4 * k + 2] += ph[i] * d4.z;
+                        Tv[4 * k + 3] += ph[i] * d4.w;
+                    }
+                }
+            }
+            __syncthreads();  // every thread's reads of the Phi tile precede the partials written over it
+        }
+        // ---- E: this thread's share of rho and grad rho, shell by shell:
+        // with u = sum_c T_c d_c (p shell; u = T for an s shell) and Tv = (T_x, T_y, T_z),
+        // rho += g u and grad rho += 2 (g' u d + g Tv)
+        {
+            float rho = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+            float cg = 0.f, cgp = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, u = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+#pragma unroll
+            for (int j = 0; j < NQ; j++) {
+                if constexpr (!FINAL) {
+                    if ((j & 3) == 0) ld4(C.tT + C.lanes + C.c0 + j, Tv + j);  // T four columns at a time
+                }
+                if (TC_FRESH(j)) {
+                    rho += cg * u;  // the previous shell (zeros before the first)
+                    rx += cgp * u * dx + cg * tx;
+                    ry += cgp * u * dy + cg * ty;
+                    rz += cgp * u * dz + cg * tz;
+                    cg = gj[j];
+                    cgp = gpj[j];
+                    const float4 dl = *(const float4 *)(shfp + TC_SHELL(j) * 8);
+                    dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
+                    u = tx = ty = tz = 0.f;
+                }
+                if (TC_ON(j)) {
+                    const float tv = Tv[j];
+                    const int c = TC_COMP(j);
+                    if (c == 0) {
+                        u = tv;
+                    } else if (c == 1) {
+                        u += tv * dx; tx = tv;
+                    } else if (c == 2) {
+                        u += tv * dy; ty = tv;
+                    } else {
+                        u += tv * dz; tz = tv;
+                    }
+                }
+            }
+            rho += cg * u;
+            rx += cgp * u * dx + cg * tx;
+            ry += cgp * u * dy + cg * ty;
+            rz += cgp * u * dz + cg * tz;
+            C.part[(C.q4 * 4 + 0) * TC_BP + p] = rho;
+            C.part[(C.q4 * 4 + 1) * TC_BP + p] = rx;
+            C.part[(C.q4 * 4 + 2) * TC_BP + p] = ry;
+            C.part[(C.q4 * 4 + 3) * TC_BP + p] = rz;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        // ---- F: XC in three parts on three warp groups (exchange, VWN5, LYP)
+        if (t < 3 * TC_BP) {
+            const int gi = t >> 7;
+            float r = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+            for (int gq = 0; gq < 4; gq++) {
+                r += C.part[(gq * 4 + 0) * TC_BP + p];
+                gx += C.part[(gq * 4 + 1) * TC_BP + p];
+                gy += C.part[(gq * 4 + 2) * TC_BP + p];
+                gz += C.part[(gq * 4 + 3) * TC_BP + p];
+            }
+            gx *= 2.f; gy *= 2.f; gz *= 2.f;
+            float e = 0.f, vr = 0.f, vs = 0.f;
+            if (pw != 0.f) xc::b3lyp_part<float>(gi, r, gx * gx + gy * gy + gz * gz, e, vr, vs);
+            exc += (double)pw * (double)e;
+            C.xcp[(gi * 2 + 0) * TC_BP + p] = vr;
+            C.xcp[(gi * 2 + 1) * TC_BP + p] = vs;
+            if (gi == 0) {
+                C.grd[p] = gx;
+                C.grd[TC_BP + p] = gy;
+                C.grd[2 * TC_BP + p] = gz;
+            }
+        }
+        __syncthreads();
+        // ---- G: Phi^T and X = a phi + b . grad phi with a = w v_rho / 2, b = 2 w v_sigma
+        // grad rho: s shell X = a g + g' (b . d); p component c: X_c = d_c (a g + g' (b . d)) + b_c g
+        {
+            const float vr = C.xcp[p] + C.xcp[2 * TC_BP + p] + C.xcp[4 * TC_BP + p];
+            const float vs2 = 2.f * pw * (C.xcp[TC_BP + p] + C.xcp[5 * TC_BP + p]);
+            const float a = 0.5f * pw * vr;
+            const float bx = vs2 * C.grd[p], by = vs2 * C.grd[TC_BP + p], bz = vs2 * C.grd[2 * TC_BP + p];
+            if (C.c0 & 4) tc_write_gemm2<NQ, 4>(C, cb, on, gj, gpj, shfp, px, py, pz, a, bx, by, bz);
+            else tc_write_gemm2<NQ, 0>(C, cb, on, gj, gpj, shfp, px, py, pz, a, bx, by, bz);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        // ---- H: GEMM2 over the block's 128 points (K steps of 8 points: 32 bytes in an atom)
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int k = 0; k < TC_BP / 8; k++) {
+                const uint32_t ko = (uint32_t)(k >> 2) * 1024u + (uint32_t)(k & 3) * 32u;
+                const uint64_t ah = tc::sdesc_sw128(C.su + C.L.pt_hi + ko), al = tc::sdesc_sw128(C.su + C.L.pt_lo + ko);
+                const uint64_t bh = tc::sdesc_sw128(C.su + C.L.x_hi + ko), bl = tc::sdesc_sw128(C.su + C.L.x_lo + ko);
+                tc::mma(C.tV, ah, bh, C.id, k > 0);
+                tc::mma(C.tV, ah, bl, C.id, 1);
+                tc::mma(C.tV, al, bh, C.id, 1);
+            }
+            tc::commit(C.bar2);
+        }
+        pending = true;
+    }
+    if (!failed && pending) {
+        failed = !drain();
+        if (!failed) pending = false;
+    }
+    if (failed && t == 0) *C.s_fail = 1;
+    __syncthreads();
+    // ---- flush V' (row mu = this thread's lane row, columns of its quarter) and E_xc
+    if (!*C.s_fail && any_block && !first) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int mu = (C.warp & 3) * 32 + lane;
+        Fx *gV = b.accx + md.acc0 + 2 * C.n * C.n;  // mixed path: fixed point in every pass
+#pragma unroll
+        for (int kc = 0; kc < NQ / 4; kc++) {
+            float v[4];
+            ld4(C.tS + C.lanes + C.c0 + 4 * kc, v);
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int nu = C.c0 + 4 * kc + i;
+                if (mu < C.n && nu < C.n && v[i] != 0.f) acc_add(&gV[mu * C.n + nu], (TA)v[i]);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) exc += __shfl_xor_sync(0xffffffffu, exc, o);
+    if (lane == 0 && exc != 0.0) exc_add(&b.st[C.m].exc_fx, exc);
+    if (*C.s_fail && t == 0) {
+        atomicOr(&b.st[C.m].err_flag, 4);
+        // give in-flight MMAs a bounded chance to drain before freeing tensor memory
+        if (in1) tc::wait(C.bar1, ph1);
+        if (pending) tc::wait(C.bar2, ph2);
+    }
 }
 
 // FINAL (the mixed path's final step, TA = double): the density contraction
@@ -327,36 +728,55 @@ __device__ __forceinline__ ColIt col_info(const int *col, int c0, int j, unsigne
 // tensor cores' truncating accumulation would bias rho and E_xc), V_xc stays
 // on the tensor cores (it only moves the final eigenvalues, at ~1e-7), and
 // V_xc is accumulated in 64-bit fixed point like every mixed pass.
-template <typename TA, bool FINAL>
-__global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode) {
+// One instantiation per NQ (columns per thread = padded basis / 4), launched
+// over the molecules of that size only (list), so that each gets its own
+// register allocation and shared-memory size.
+template <typename TA, bool FINAL, int NQ>
+__global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode, const int *list) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar1, bar2;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail;
-    const int m = blockIdx.y, chunk = blockIdx.x;
+    const int m = list[blockIdx.y], chunk = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
-    if (!grid_tc_fits(md.nbf, md.nsh)) return;  // the CUDA-core kernel takes this molecule
     if (chunk >= md.nblk) return;
-    const int n = md.nbf, nsh = md.nsh;
-    const int np = (n + 15) & ~15;
-    const int nq = np / 4;  // AO columns per thread quarter (multiple of 4)
-    const TcSmem L = tc_layout(np, nsh);
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int p = t & (TC_BP - 1), q4 = t >> 7;  // point, column quarter
-    const int c0 = q4 * nq;
-    unsigned char *sm = smem;
-    float *part = (float *)(sm + L.part);
-    float *xcp = (float *)(sm + L.xcp), *grd = (float *)(sm + L.grd);
-    float *shx = (float *)(sm + L.shx), *shf = (float *)(sm + L.shf);
-    int *col = (int *)(sm + L.col);
-    const uint32_t sg = (uint32_t)(np / 4) * 128u;  // bytes per 8-row group of every tile
+    TcCta C;
+    C.md = &md;
+    C.m = m;
+    C.chunk = chunk;
+    C.nchunk = nchunk;
+    C.n = md.nbf;
+    C.nsh = md.nsh;
+    C.np = (C.n + 15) & ~15;
+    const int nq = C.np / 4;  // AO columns per thread quarter (multiple of 4)
+    C.L = tc_layout(C.np, C.nsh);
+    C.t = threadIdx.x;
+    C.lane = C.t & 31;
+    C.warp = C.t >> 5;
+    C.p = C.t & (TC_BP - 1);
+    C.q4 = C.t >> 7;
+    C.c0 = C.q4 * nq;
+    C.sm = smem;
+    C.part = (float *)(smem + C.L.part);
+    C.xcp = (float *)(smem + C.L.xcp);
+    C.grd = (float *)(smem + C.L.grd);
+    float *shx = (float *)(smem + C.L.shx);
+    C.shx = shx;
+    C.shf = (float *)(smem + C.L.shf);
+    int *col = (int *)(smem + C.L.col);
+    C.col = col;
+    C.sg = (uint32_t)(C.np / 4) * 128u;  // bytes per 8-row group of the unswizzled tiles
+    C.bar1 = &bar1;
+    C.bar2 = &bar2;
+    C.s_fail = &s_fail;
+    const int n = C.n, nsh = C.nsh, np = C.np, t = C.t;
 
     // ---- per-CTA constants: D (hi, lo) as GEMM1's B, or plain FP32 D[mu][nu]
     // for the CUDA-core contraction of the final step; shells; column codes
     const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
     if constexpr (FINAL) {
-        float *Dp = (float *)(sm + L.D_hi);
+        float *Dp = (float *)(smem + C.L.D_hi);
         for (int i = t; i < np * np; i += blockDim.x) {
             const int row = i / np, cc = i % np;
             Dp[i] = (row < n && cc < n) ? (float)D[row * n + cc] : 0.f;
@@ -372,8 +792,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
             }
             float4 hi, lo;
             tc::split4(v, hi, lo);
-            *(float4 *)(sm + L.D_hi + tc::coff(row, kc * 4, sg)) = hi;
-            *(float4 *)(sm + L.D_lo + tc::coff(row, kc * 4, sg)) = lo;
+            *(float4 *)(smem + C.L.D_hi + tc::coff(row, kc * 4, C.sg)) = hi;
+            *(float4 *)(smem + C.L.D_lo + tc::coff(row, kc * 4, C.sg)) = lo;
         }
     }
     for (int s = t; s < nsh; s += blockDim.x) {
@@ -406,7 +826,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
         else
             for (int c = 0; c < 3; c++) col[a0 + c] = (s << 2) | (c + 1) | (share && c == 0 ? 0x100 : 0);
     }
-    if (warp == 0) {
+    if (C.warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_slot)),
                      "r"(TC_TMEM_COLS)
                      : "memory");
@@ -422,351 +842,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const uint32_t tT = tmem + TC_TCOL, tV = tmem + TC_VCOL;
-    const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;  // this warp's TMEM lane quarter
-    const uint32_t id1 = tc::idesc(128, np), id2 = id1;
-    const uint32_t su = tc::smem_u32(sm);
-    uint32_t ph1 = 0, ph2 = 0;
-    bool pending = false;  // a GEMM2 in flight whose V' is not yet in vacc
-    bool in1 = false;      // a GEMM1 in flight
-    double exc = 0.0;
-    float vacc[TC_NPMAX / 4];
-#pragma unroll
-    for (int j = 0; j < TC_NPMAX / 4; j++) vacc[j] = 0.f;
-    bool any_block = false, failed = false;
-
-    const float *gxp = (const float *)b.gx + md.pts0, *gyp = (const float *)b.gy + md.pts0;
-    const float *gzp = (const float *)b.gz + md.pts0, *gwp = (const float *)b.gw + md.pts0;
-    const unsigned long long *bmask = b.blk_mask + 2 * (md.pts0 / TC_BP) + (FINAL ? 1 : 0);
-    const int npa = b.n_rad * b.n_theta * b.n_phi;
-    float nx = gxp[chunk * TC_BP + p], ny = gyp[chunk * TC_BP + p], nz = gzp[chunk * TC_BP + p];
-    float nw = gwp[chunk * TC_BP + p];
-    int shf_owner = -1;  // owner atom the shf table was built for
-
-    // drain the pending GEMM2: V' row segment into vacc
-    auto drain = [&]() -> bool {
-        const bool ok = __syncthreads_and(tc::wait(&bar2, ph2));
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok) return false;  // still pending: the exit path waits on the same phase
-        ph2 ^= 1;
-        float v[TC_NPMAX / 4];
-        ld20(tV + lanes + c0, v);
-#pragma unroll
-        for (int j = 0; j < TC_NPMAX / 4; j++)
-            if (j < nq) vacc[j] += v[j];
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        return true;
-    };
-
-    for (int blk = chunk; blk < md.nblk; blk += nchunk) {
-        const int p0 = blk * TC_BP;
-        const int own0 = min(p0 / npa, md.natom - 1);
-        const float px = nx, py = ny, pz = nz, pw = nw;
-        if (blk + nchunk < md.nblk) {  // this thread's point of the next block
-            const int i1 = p0 + nchunk * TC_BP + p;
-            nx = gxp[i1]; ny = gyp[i1]; nz = gzp[i1]; nw = gwp[i1];
-        }
-        const unsigned long long mask = bmask[2 * blk];
-        if (mask == 0ull) continue;  // every AO below the screen: rho under the XC cutoff everywhere
-        any_block = true;
-        if (own0 != shf_owner) {  // R_owner - C for the block's (at most two) owners
-            __syncthreads();
-            for (int i = t; i < 2 * nsh; i += blockDim.x) {
-                const int hh = i / nsh, s = i % nsh;
-                const int A = min(own0 + hh, md.natom - 1);
-                const double *ra = b.axyz + (md.atom0 + A) * 3, *rc = b.sh_xyz + (md.sh0 + s) * 3;
-                *(float4 *)(shf + s * 8 + hh * 4) =
-                    make_float4((float)(ra[0] - rc[0]), (float)(ra[1] - rc[1]), (float)(ra[2] - rc[2]), 0.f);
-            }
-            shf_owner = own0;
-            __syncthreads();
-        }
-        const int hp = min((p0 + p) / npa, md.natom - 1) - own0;
-        const float *shfp = shf + hp * 4;
-
-        // ---- A: radial values g = sum c e^(-a r^2), g' = sum -2ac e^(-a r^2) of the thread's columns
-        float gj[TC_NPMAX / 4], gpj[TC_NPMAX / 4];
-        {
-            int prev_s = -1;
-            float e0 = 0.f, e1 = 0.f, e2 = 0.f, cg = 0.f, cgp = 0.f;
-#pragma unroll
-            for (int j = 0; j < TC_NPMAX / 4; j++) {
-                gj[j] = gpj[j] = 0.f;
-                if (j < nq) {
-                    const ColIt it = col_info(col, c0, j, mask, prev_s);
-                    if (it.fresh) {
-                        const float4 xa = *(const float4 *)(shx + it.s * TC_SHX);
-                        const float4 xb = *(const float4 *)(shx + it.s * TC_SHX + 4);
-                        const float xc9 = shx[it.s * TC_SHX + 8];
-                        if (!it.share) {
-                            const float4 dl = *(const float4 *)(shfp + it.s * 8);
-                            const float dx = dl.x + px, dy = dl.y + py, dz = dl.z + pz;
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            e0 = __expf(-xa.x * r2);
-                            e1 = __expf(-xa.y * r2);
-                            e2 = __expf(-xa.z * r2);
-                        }
-                        cg = xa.w * e0 + xb.x * e1 + xb.y * e2;
-                        cgp = xb.z * e0 + xb.w * e1 + xc9 * e2;
-                    }
-                    if (it.code >= 0) {
-                        gj[j] = cg;
-                        gpj[j] = cgp;
-                    }
-                }
-            }
-        }
-        // ---- B: the previous block's V'
-        if (pending) {
-            if (!drain()) {
-                failed = true;
-                break;
-            }
-            pending = false;
-        }
-        // ---- C: Phi (hi, lo) into the [point][AO] tile
-        {
-            int prev_s = -1;
-            float dx = 0.f, dy = 0.f, dz = 0.f;
-#pragma unroll
-            for (int kc = 0; kc < TC_NPMAX / 16; kc++) {
-                if (kc * 4 < nq) {
-                    float v[4];
-#pragma unroll
-                    for (int i = 0; i < 4; i++) {
-                        const int j = kc * 4 + i;
-                        const ColIt it = col_info(col, c0, j, mask, prev_s);
-                        if (it.fresh) {
-                            const float4 dl = *(const float4 *)(shfp + it.s * 8);
-                            dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
-                        }
-                        const float dc = it.c == 0 ? dx : (it.c == 1 ? dy : dz);
-                        v[i] = it.code < 0 ? 0.f : (it.c < 0 ? gj[j] : dc * gj[j]);
-                    }
-                    float4 hi, lo;
-                    tc::split4(v, hi, lo);
-                    *(float4 *)(sm + L.phi_hi + tc::coff(p, c0 + kc * 4, sg)) = hi;
-                    *(float4 *)(sm + L.phi_lo + tc::coff(p, c0 + kc * 4, sg)) = lo;
-                }
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        float Tv[TC_NPMAX / 4];
-        if constexpr (!FINAL) {
-            if (t == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                for (int s = 0; s < np / 8; s++) {
-                    const uint32_t ka = 2u * s * 128u;
-                    const uint64_t ah = tc::sdesc(su + L.phi_hi + ka, 128, sg), al = tc::sdesc(su + L.phi_lo + ka, 128, sg);
-                    const uint64_t bh = tc::sdesc(su + L.D_hi + ka, 128, sg), bl = tc::sdesc(su + L.D_lo + ka, 128, sg);
-                    tc::mma(tT, ah, bh, id1, s > 0);
-                    tc::mma(tT, ah, bl, id1, 1);
-                    tc::mma(tT, al, bh, id1, 1);
-                }
-                tc::commit(&bar1);
-            }
-            in1 = true;
-            const bool ok1 = __syncthreads_and(tc::wait(&bar1, ph1));
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (!ok1) {
-                failed = true;
-                break;
-            }
-            ph1 ^= 1;
-            in1 = false;
-            ld20(tT + lanes + c0, Tv);
-        } else {
-            // T on the CUDA cores: this point's row of Phi (hi + lo is the FP32
-            // value) against D's rows, the thread's column quarter
-#pragma unroll
-            for (int j = 0; j < TC_NPMAX / 4; j++) Tv[j] = 0.f;
-            const float *Dp = (const float *)(sm + L.D_hi);
-            for (int mc = 0; mc < np / 4; mc++) {
-                const float4 h4 = *(const float4 *)(sm + L.phi_hi + tc::coff(p, mc * 4, sg));
-                const float4 l4 = *(const float4 *)(sm + L.phi_lo + tc::coff(p, mc * 4, sg));
-                const float ph[4] = {h4.x + l4.x, h4.y + l4.y, h4.z + l4.z, h4.w + l4.w};
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const float4 *drow = (const float4 *)(Dp + (mc * 4 + i) * np + c0);
-#pragma unroll
-                    for (int k = 0; k < TC_NPMAX / 16; k++) {
-                        if (k * 4 < nq) {
-                            const float4 d4 = drow[k];
-                            Tv[4 * k] += ph[i] * d4.x;
-                            Tv[4 * k + 1] += ph[i] * d4.y;
-                            Tv[4 * k + 2] += ph[i] * d4.z;
-                            Tv[4 * k + 3] += ph[i] * d4.w;
-                        }
-                    }
-                }
-            }
-            __syncthreads();  // every thread's reads of the Phi tile precede the partials written over it
-        }
-        // ---- E: this thread's share of rho and grad rho, shell by shell:
-        // with u = sum_c T_c d_c (p shell; u = T for an s shell) and Tv = (T_x, T_y, T_z),
-        // rho += g u and grad rho += 2 (g' u d + g Tv)
-        {
-            float rho = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-            float cg = 0.f, cgp = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, u = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
-            bool open = false;
-            int prev_s = -1;
-#pragma unroll
-            for (int j = 0; j < TC_NPMAX / 4; j++) {
-                if (j < nq) {
-                    const ColIt it = col_info(col, c0, j, mask, prev_s);
-                    if (it.fresh) {
-                        if (open) {
-                            rho += cg * u;
-                            rx += cgp * u * dx + cg * tx;
-                            ry += cgp * u * dy + cg * ty;
-                            rz += cgp * u * dz + cg * tz;
-                        }
-                        open = true;
-                        cg = gj[j];
-                        cgp = gpj[j];
-                        const float4 dl = *(const float4 *)(shfp + it.s * 8);
-                        dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
-                        u = tx = ty = tz = 0.f;
-                    }
-                    if (it.code >= 0) {
-                        const float tv = Tv[j];
-                        if (it.c < 0) {
-                            u = tv;
-                        } else if (it.c == 0) {
-                            u += tv * dx; tx = tv;
-                        } else if (it.c == 1) {
-                            u += tv * dy; ty = tv;
-                        } else {
-                            u += tv * dz; tz = tv;
-                        }
-                    }
-                }
-            }
-            if (open) {
-                rho += cg * u;
-                rx += cgp * u * dx + cg * tx;
-                ry += cgp * u * dy + cg * ty;
-                rz += cgp * u * dz + cg * tz;
-            }
-            part[(q4 * 4 + 0) * TC_BP + p] = rho;
-            part[(q4 * 4 + 1) * TC_BP + p] = rx;
-            part[(q4 * 4 + 2) * TC_BP + p] = ry;
-            part[(q4 * 4 + 3) * TC_BP + p] = rz;
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        // ---- F: XC in three parts on three warp groups (exchange, VWN5, LYP)
-        if (t < 3 * TC_BP) {
-            const int gi = t >> 7;
-            float r = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-            for (int gq = 0; gq < 4; gq++) {
-                r += part[(gq * 4 + 0) * TC_BP + p];
-                gx += part[(gq * 4 + 1) * TC_BP + p];
-                gy += part[(gq * 4 + 2) * TC_BP + p];
-                gz += part[(gq * 4 + 3) * TC_BP + p];
-            }
-            gx *= 2.f; gy *= 2.f; gz *= 2.f;
-            float e = 0.f, vr = 0.f, vs = 0.f;
-            if (pw != 0.f) xc::b3lyp_part<float>(gi, r, gx * gx + gy * gy + gz * gz, e, vr, vs);
-            exc += (double)pw * (double)e;
-            xcp[(gi * 2 + 0) * TC_BP + p] = vr;
-            xcp[(gi * 2 + 1) * TC_BP + p] = vs;
-            if (gi == 0) {
-                grd[p] = gx;
-                grd[TC_BP + p] = gy;
-                grd[2 * TC_BP + p] = gz;
-            }
-        }
-        __syncthreads();
-        // ---- G: Phi^T and X = a phi + b . grad phi with a = w v_rho / 2, b = 2 w v_sigma
-        // grad rho: s shell X = a g + g' (b . d); p component c: X_c = d_c (a g + g' (b . d)) + b_c g
-        {
-            const float vr = xcp[p] + xcp[2 * TC_BP + p] + xcp[4 * TC_BP + p];
-            const float vs2 = 2.f * pw * (xcp[TC_BP + p] + xcp[5 * TC_BP + p]);
-            const float a = 0.5f * pw * vr;
-            const float bx = vs2 * grd[p], by = vs2 * grd[TC_BP + p], bz = vs2 * grd[2 * TC_BP + p];
-            int prev_s = -1;
-            float dx = 0.f, dy = 0.f, dz = 0.f, S = 0.f;
-#pragma unroll
-            for (int j = 0; j < TC_NPMAX / 4; j++) {
-                if (j < nq) {
-                    const ColIt it = col_info(col, c0, j, mask, prev_s);
-                    if (it.fresh) {
-                        const float4 dl = *(const float4 *)(shfp + it.s * 8);
-                        dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
-                        S = a * gj[j] + gpj[j] * (bx * dx + by * dy + bz * dz);
-                    }
-                    const float dc = it.c == 0 ? dx : (it.c == 1 ? dy : dz);
-                    const float bc = it.c == 0 ? bx : (it.c == 1 ? by : bz);
-                    const float f = it.code < 0 ? 0.f : (it.c < 0 ? gj[j] : dc * gj[j]);
-                    const float x = it.code < 0 ? 0.f : (it.c < 0 ? S : dc * S + bc * gj[j]);
-                    const float fh = tc::tf32_hi(f), xh = tc::tf32_hi(x);
-                    const uint32_t o = tc::soff(c0 + j, p);
-                    *(float *)(sm + L.pt_hi + o) = fh;
-                    *(float *)(sm + L.pt_lo + o) = f - fh;
-                    *(float *)(sm + L.x_hi + o) = xh;
-                    *(float *)(sm + L.x_lo + o) = x - xh;
-                }
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        // ---- H: GEMM2 over the block's 128 points (K steps of 8 points: 32 bytes in an atom)
-        if (t == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int k = 0; k < TC_BP / 8; k++) {
-                const uint32_t ko = (uint32_t)(k >> 2) * 1024u + (uint32_t)(k & 3) * 32u;
-                const uint64_t ah = tc::sdesc_sw128(su + L.pt_hi + ko), al = tc::sdesc_sw128(su + L.pt_lo + ko);
-                const uint64_t bh = tc::sdesc_sw128(su + L.x_hi + ko), bl = tc::sdesc_sw128(su + L.x_lo + ko);
-                tc::mma(tV, ah, bh, id2, k > 0);
-                tc::mma(tV, ah, bl, id2, 1);
-                tc::mma(tV, al, bh, id2, 1);
-            }
-            tc::commit(&bar2);
-        }
-        pending = true;
-    }
-    if (!failed && pending) failed = !drain();
-    if (failed && t == 0) s_fail = 1;
-    __syncthreads();
-    // ---- flush V' (row mu = this thread's lane row, columns of its quarter) and E_xc
-    if (!s_fail && any_block) {
-        const int mu = (warp & 3) * 32 + lane;
-        Fx *gV = b.accx + md.acc0 + 2 * n * n;  // mixed path: fixed point in every pass
-#pragma unroll
-        for (int j = 0; j < TC_NPMAX / 4; j++) {
-            const int nu = c0 + j;
-            if (j < nq && mu < n && nu < n && vacc[j] != 0.f) acc_add(&gV[mu * n + nu], (TA)vacc[j]);
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) exc += __shfl_xor_sync(0xffffffffu, exc, o);
-    if (lane == 0 && exc != 0.0) exc_add(&b.st[m].exc_fx, exc);
-    if (s_fail && t == 0) {
-        atomicOr(&b.st[m].err_flag, 4);
-        // give in-flight MMAs a bounded chance to drain before freeing tensor memory
-        if (in1) tc::wait(&bar1, ph1);
-        if (pending) tc::wait(&bar2, ph2);
-    }
+    C.tT = tmem + TC_TCOL;
+    C.tV = tmem + TC_VCOL;
+    C.tS = tmem + TC_SCOL;
+    C.lanes = (uint32_t)((C.warp & 3) * 32) << 16;  // this warp's TMEM lane quarter
+    C.id = tc::idesc(128, np);
+    C.su = tc::smem_u32(smem);
+    (void)nq;  // == NQ: the host launches each molecule with its own size class
+    tc_loop<TA, FINAL, NQ>(b, C);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (C.warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
 }
 
 
-void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
-                       cudaStream_t s) {
-    const int np = min((max_nbf + 15) & ~15, TC_NPMAX);  // larger molecules return at once
-    const size_t sm = tc_layout(np, min(max_nsh, TC_NSHMAX)).total;
-    if (acc_fp64) {
-        cudaFuncSetAttribute(grid_xc_tc_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        grid_xc_tc_kernel<double, true><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);
-    } else {
-        cudaFuncSetAttribute(grid_xc_tc_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        grid_xc_tc_kernel<float, false><<<dim3(nchunk, b.nmol), TC_THREADS, sm, s>>>(b, nchunk, mode);
-    }
+template <typename TA, bool FINAL, int NQ>
+static void launch_tc_class(const DevBatch &b, int nchunk, int mode, int max_nsh, const int *list, int count,
+                            cudaStream_t s) {
+    const size_t sm = tc_layout(4 * NQ, max_nsh).total;
+    cudaFuncSetAttribute(grid_xc_tc_kernel<TA, FINAL, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    grid_xc_tc_kernel<TA, FINAL, NQ><<<dim3(nchunk, count), TC_THREADS, sm, s>>>(b, nchunk, mode, list);
+}
+
+template <typename TA, bool FINAL>
+static void launch_tc_all(const DevBatch &b, int nchunk, int mode, const TcClasses &cl, cudaStream_t s) {
+    const int *l = cl.list;
+    if (cl.count[0]) launch_tc_class<TA, FINAL, 4>(b, nchunk, mode, cl.max_nsh[0], l + cl.off[0], cl.count[0], s);
+    if (cl.count[1]) launch_tc_class<TA, FINAL, 8>(b, nchunk, mode, cl.max_nsh[1], l + cl.off[1], cl.count[1], s);
+    if (cl.count[2]) launch_tc_class<TA, FINAL, 12>(b, nchunk, mode, cl.max_nsh[2], l + cl.off[2], cl.count[2], s);
+    if (cl.count[3]) launch_tc_class<TA, FINAL, 16>(b, nchunk, mode, cl.max_nsh[3], l + cl.off[3], cl.count[3], s);
+    if (cl.count[4]) launch_tc_class<TA, FINAL, 20>(b, nchunk, mode, cl.max_nsh[4], l + cl.off[4], cl.count[4], s);
+}
+
+void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, const TcClasses &cl, cudaStream_t s) {
+    if (acc_fp64) launch_tc_all<double, true>(b, nchunk, mode, cl, s);
+    else launch_tc_all<float, false>(b, nchunk, mode, cl, s);
 }
 
 // ------------------------------------------------ bounded-wait self test

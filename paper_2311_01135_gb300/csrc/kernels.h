@@ -36,8 +36,14 @@ void launch_grid_masks(const DevBatch &b, long long nblk_total, const int *blk_m
 // Tensor-core (tcgen05, 3xTF32) version for the mixed path; takes the
 // molecules with grid_tc_fits() and skips the others.  acc_fp64 = 1 is the
 // final step: density contraction on the CUDA cores (round-to-nearest sums).
-void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
-                       cudaStream_t s);
+// Molecules the tensor-core kernel takes, by size class (padded basis 16, 32,
+// 48, 64, 80): device list of molecule indices, class offsets and counts,
+// largest shell count per class.
+struct TcClasses {
+    const int *list;
+    int off[5], count[5], max_nsh[5];
+};
+void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, const TcClasses &cl, cudaStream_t s);
 // Per-molecule FP64 SCF stages.
 void launch_scf_init(const DevBatch &b, cudaStream_t s);
 // only_rechecked: guess only for the molecules marked by launch_mark_recheck

@@ -81,3 +81,25 @@ def test_fp64_redo_against_the_oracle(runs):
     assert r["rechecked"] == 2
     assert abs(r["E"] - o["E"]) <= 1e-5
     assert abs(r["gap"] - o["gap"]) <= 1e-4
+
+
+def test_back_to_back_runs(mols):
+    """Runs enqueued one after the other without waiting (as a benchmark's
+    timed loop does): each run releases the previous run's FP64 redo batch,
+    whose results the previous run's last kernel may still be reading on the
+    batch's stream; the release waits for that stream.  The results of the
+    last run equal those of a single run."""
+    sub = [mols[0], mols[len(TIER1)]]  # one molecule of each tier
+    with g.Context(precision=g.RKS_MIXED, fixed_iters=20) as c, g.Batch(c, sub) as B:
+        for _ in range(3):
+            B.setup()
+            B.run()
+        B.sync()
+        rep = [B.result(m) for m in range(len(sub))]
+    with g.Context(precision=g.RKS_MIXED, fixed_iters=20) as c, g.Batch(c, sub) as B:
+        B.run()
+        B.sync()
+        one = [B.result(m) for m in range(len(sub))]
+    assert [r["rechecked"] for r in rep] == [1, 2]
+    assert rep[0]["E"] == one[0]["E"]
+    assert abs(rep[1]["E"] - one[1]["E"]) <= 1e-8
