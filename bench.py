@@ -489,8 +489,8 @@ def main():
     ap.add_argument("--nmol", type=int, default=4096)
     ap.add_argument("--fp64-budget-s", type=float, default=1800.0,
                     help="time allowed for the FP64 GPU comparison (every molecule when it fits)")
-    ap.add_argument("--serve-leg-n", type=int, default=1500)
-    ap.add_argument("--serve-leg-rate", type=float, default=200.0)
+    ap.add_argument("--serve-leg-n", type=int, default=1000)
+    ap.add_argument("--serve-leg-rate", type=float, default=50.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="one step with per-stage times")

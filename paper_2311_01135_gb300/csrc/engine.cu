@@ -300,6 +300,8 @@ struct rks_batch {
     bool graph_failed = false;
     int *recheck_d = nullptr;          // [2] molecules marked for the precise rerun / the FP64 redo
     int *recheck_list = nullptr;       // [nmol] indices marked for the FP64 redo
+    int *recheck_list1 = nullptr;      // [nmol] indices marked for the precise rerun
+    int n_precise = 0;                 // > 0 while the precise reruns are enqueued
     // inputs kept for the FP64 redo of unconverged molecules (coordinates in bohr)
     std::vector<int32_t> hZ, hnat;
     std::vector<double> hxyz;
@@ -576,6 +578,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
         (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) ||
         (rc = dalloc(b, &b->blk_mol, b->nblk_total)) || (rc = dalloc(b, &b->active_d, 1)) ||
         (rc = dalloc(b, &b->recheck_d, 2)) || (rc = dalloc(b, &b->recheck_list, nmol)) ||
+        (rc = dalloc(b, &b->recheck_list1, nmol)) ||
         (o.precision == RKS_MIXED && (rc = dalloc(b, &d.blk_mask, 2 * b->nblk_total))) ||
         (o.precision == RKS_MIXED && (rc = dalloc(b, (int **)&b->tcc.list, nmol))) ||
         (rc = dalloc(b, &d.jk_next, nmol))) {
@@ -714,7 +717,13 @@ static int fock_pass(rks_batch *b, int prec, int mode) {
     }
     if (jk_fin && b->precision == RKS_MIXED && d.fixlist) {
         StageScope sc(c, s, mode ? "jk_fp64_fix" : "jk_fp64_fix_it", 0);
-        launch_jk_fix(d, mode, s);
+        if (mode == 0 && b->n_precise > 0) {
+            // the precise reruns: only their molecules, spread over the GPU
+            const int nch = std::min(256, std::max(8, (8 * c->nsm + b->n_precise - 1) / b->n_precise));
+            launch_jk_fix(d, mode, s, b->recheck_list1, b->n_precise, nch);
+        } else {
+            launch_jk_fix(d, mode, s);
+        }
     }
     if (d.xc) {
         // Molecules that fit the tensor-core kernel (grid_tc_fits, decided per
@@ -766,7 +775,8 @@ static int enqueue_iters(rks_batch *b, int n, int prec) {
     int rc;
     prec &= 3;
     for (int k = 0; k < n; k++, b->it_enq++) {
-        const bool use_graph = c->opt.use_graphs && !c->prof && !b->graph_failed && b->graph_warm[prec];
+        const bool use_graph = c->opt.use_graphs && !c->prof && !b->graph_failed && b->graph_warm[prec] &&
+                               b->n_precise == 0;
         cudaGraphExec_t &gx = b->graph[prec];
         if (use_graph && !gx) {
             cudaGraph_t g = nullptr;
@@ -809,7 +819,7 @@ static int enqueue_recheck_start(rks_batch *b) {
     cudaStream_t s = b->stream;
     {
         StageScope sc(b->ctx, s, "recheck_mark", 0);
-        launch_mark_recheck(b->d, b->recheck_d, b->recheck_list, s);
+        launch_mark_recheck(b->d, b->recheck_d, b->recheck_list, b->recheck_list1, s);
     }
     {
         StageScope sc(b->ctx, s, "scf_guess", 0);
@@ -889,7 +899,10 @@ extern "C" int rks_batch_run(rks_batch *b) {
             CUDA_OK(cudaStreamSynchronize(b->stream));
             const int n_precise = pinw(b)[0], n_fp64 = pinw(b)[1];
             if (n_fp64 > 0 && (rc = start_fp64_redo(b, n_fp64))) return rc;
-            if (n_precise > 0 && (rc = enqueue_iters(b, d.fixed_iters, kPrecise))) return rc;
+            b->n_precise = n_precise;
+            if (n_precise > 0) rc = enqueue_iters(b, d.fixed_iters, kPrecise);
+            b->n_precise = 0;
+            if (rc) return rc;
         }
     } else {
         while (b->it_enq < d.max_iters) {
@@ -1244,6 +1257,7 @@ struct Cohort {
     std::vector<uint64_t> ids;
     int phase = 0;  // 0 iterating, 2 recheck marked, 3 rechecking, 1 final step enqueued
     int rc_enq = 0; // recheck iterations enqueued
+    int n_precise = 0;
     bool counted = false;  // the last chunk ended with an active-count readback
     cudaEvent_t ev = nullptr;
 };
@@ -1271,8 +1285,11 @@ static int cohort_next(Cohort &h) {
         if (n_fp64 > 0) rc = start_fp64_redo(b, n_fp64);
         if (!rc && n_precise > 0) {
             h.phase = 3;
+            h.n_precise = n_precise;
             const int k = std::min(kCheckEvery, d.fixed_iters);
+            b->n_precise = n_precise;
             rc = enqueue_iters(b, k, kPrecise);
+            b->n_precise = 0;
             h.rc_enq = k;
         } else if (!rc) {
             rc = enqueue_final(b);
@@ -1286,7 +1303,9 @@ static int cohort_next(Cohort &h) {
             h.phase = 1;
         } else {
             const int k = std::min(kCheckEvery, d.fixed_iters - h.rc_enq);
+            b->n_precise = h.n_precise;
             rc = enqueue_iters(b, k, kPrecise);
+            b->n_precise = 0;
             h.rc_enq += k;
         }
     } else if (h.phase == 0) {

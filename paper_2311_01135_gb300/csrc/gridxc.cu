@@ -113,17 +113,33 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
             }
         }
         __syncthreads();
-        // ---- density: G threads per point
+        // ---- density: G threads per point; thread gg owns a contiguous run of
+        // NV columns nu of T = Phi D, summed in NV independent registers (the
+        // FP64 pipe needs the independent chains to stay busy)
         {
+            constexpr int NV = (RKS_NBF_CAP + G - 1) / G;
             const int p = t / G, gg = t % G;
+            const int nper = (n + G - 1) / G, nu0 = gg * nper;
+            T tv[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) tv[v] = (T)0;
+            for (int mu = 0; mu < n; mu++) {
+                const T f = phi[mu * BP + p];
+                const T *drow = Ds + mu * n + nu0;
+#pragma unroll
+                for (int v = 0; v < NV; v++)
+                    if (v < nper && nu0 + v < n) tv[v] += f * drow[v];
+            }
             T rho = 0, rx = 0, ry = 0, rz = 0;
-            for (int nu = gg; nu < n; nu += G) {
-                T tv = 0;
-                for (int mu = 0; mu < n; mu++) tv += phi[mu * BP + p] * Ds[mu * n + nu];
-                rho += tv * phi[nu * BP + p];
-                rx += tv * phi[(n + nu) * BP + p];
-                ry += tv * phi[(2 * n + nu) * BP + p];
-                rz += tv * phi[(3 * n + nu) * BP + p];
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                const int nu = nu0 + v;
+                if (v < nper && nu < n) {
+                    rho += tv[v] * phi[nu * BP + p];
+                    rx += tv[v] * phi[(n + nu) * BP + p];
+                    ry += tv[v] * phi[(2 * n + nu) * BP + p];
+                    rz += tv[v] * phi[(3 * n + nu) * BP + p];
+                }
             }
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) {

@@ -7,6 +7,10 @@
 //   GEMM2  V' += Phi^T X        (M = 128 AO rows, N = nbf padded, K = 128 points)
 // Split products (Ootomo & Yokota 2022): a = a_hi + a_lo with a_hi the TF32
 // rounding of a; a b ~= a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32.
+// The b_hi and b_lo tiles lie one after the other, so a_hi [b_hi | b_lo] is
+// one MMA of N = 2 np (two halves of the accumulator) and a_lo b_hi a second
+// one into the first half: two MMAs per K step, and the halves are summed
+// when the accumulator is read.
 //
 // Operand layouts (every tcgen05 TF32 operand is K-major):
 //  * GEMM1 contracts over AOs: Phi as a [point][AO] tile and D as a [nu][mu]
@@ -50,9 +54,9 @@
 #define TC_NPMAX RKS_TC_NPMAX   // padded basis size this kernel handles
 #define TC_NSHMAX RKS_TC_NSHMAX // shells this kernel handles (one 64-bit mask per block)
 #define TC_TMEM_COLS 512
-#define TC_TCOL 0               // TMEM columns of T (GEMM1)
-#define TC_VCOL 128             // of V' (GEMM2, one block)
-#define TC_SCOL 256             // and of the running sum of V' over the CTA's blocks
+#define TC_TCOL 0               // TMEM columns of T (GEMM1: two halves of np columns, summed on read)
+#define TC_VCOL 160             // of V' (GEMM2, one block: two halves of np columns)
+#define TC_SCOL 320             // and of the running sum of V' over the CTA's blocks
 #define TC_SPIN_LIMIT 4000000  // polls before a wait gives up: >= ~40 ms, far above any MMA here
 #define TC_THREADS 512
 #define TC_SCREEN 1e-9f         // per-block AO screening threshold, iterations
@@ -326,7 +330,7 @@ struct TcCta {
     float *part, *xcp, *grd;
     uint64_t *bar1, *bar2;
     int *s_fail;
-    uint32_t su, sg, tT, tV, tS, lanes, id;
+    uint32_t su, sg, tT, tV, tS, lanes, id, id2;
     int m, chunk, nchunk, n, nsh, np, t, lane, warp, p, q4, c0;
 };
 
@@ -440,8 +444,11 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
         ph2 ^= 1;
 #pragma unroll
         for (int kc = 0; kc < NQ / 4; kc++) {
-            float v[4], w[4];
+            float v[4], v2[4], w[4];
             ld4(C.tV + C.lanes + C.c0 + 4 * kc, v);
+            ld4(C.tV + C.lanes + C.np + C.c0 + 4 * kc, v2);
+#pragma unroll
+            for (int i = 0; i < 4; i++) v[i] += v2[i];
             if (!first) {
                 ld4(C.tS + C.lanes + C.c0 + 4 * kc, w);
 #pragma unroll
@@ -550,11 +557,9 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
                     const uint32_t ka = 2u * s * 128u;
                     const uint64_t ah = tc::sdesc(C.su + C.L.phi_hi + ka, 128, C.sg);
                     const uint64_t al = tc::sdesc(C.su + C.L.phi_lo + ka, 128, C.sg);
-                    const uint64_t bh = tc::sdesc(C.su + C.L.D_hi + ka, 128, C.sg);
-                    const uint64_t bl = tc::sdesc(C.su + C.L.D_lo + ka, 128, C.sg);
-                    tc::mma(C.tT, ah, bh, C.id, s > 0);
-                    tc::mma(C.tT, ah, bl, C.id, 1);
-                    tc::mma(C.tT, al, bh, C.id, 1);
+                    const uint64_t bh = tc::sdesc(C.su + C.L.D_hi + ka, 128, C.sg);  // D_lo follows D_hi
+                    tc::mma(C.tT, ah, bh, C.id2, s > 0);  // [Phi_hi D_hi | Phi_hi D_lo]
+                    tc::mma(C.tT, al, bh, C.id, 1);       // + Phi_lo D_hi into the first half
                 }
                 tc::commit(C.bar1);
             }
@@ -602,7 +607,13 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
 #pragma unroll
             for (int j = 0; j < NQ; j++) {
                 if constexpr (!FINAL) {
-                    if ((j & 3) == 0) ld4(C.tT + C.lanes + C.c0 + j, Tv + j);  // T four columns at a time
+                    if ((j & 3) == 0) {  // T four columns at a time: the two halves of the accumulator
+                        float t2[4];
+                        ld4(C.tT + C.lanes + C.c0 + j, Tv + j);
+                        ld4(C.tT + C.lanes + C.np + C.c0 + j, t2);
+#pragma unroll
+                        for (int i = 0; i < 4; i++) Tv[j + i] += t2[i];
+                    }
                 }
                 if (TC_FRESH(j)) {
                     rho += cg * u;  // the previous shell (zeros before the first)
@@ -682,10 +693,9 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
             for (int k = 0; k < TC_BP / 8; k++) {
                 const uint32_t ko = (uint32_t)(k >> 2) * 1024u + (uint32_t)(k & 3) * 32u;
                 const uint64_t ah = tc::sdesc_sw128(C.su + C.L.pt_hi + ko), al = tc::sdesc_sw128(C.su + C.L.pt_lo + ko);
-                const uint64_t bh = tc::sdesc_sw128(C.su + C.L.x_hi + ko), bl = tc::sdesc_sw128(C.su + C.L.x_lo + ko);
-                tc::mma(C.tV, ah, bh, C.id, k > 0);
-                tc::mma(C.tV, ah, bl, C.id, 1);
-                tc::mma(C.tV, al, bh, C.id, 1);
+                const uint64_t bh = tc::sdesc_sw128(C.su + C.L.x_hi + ko);  // X_lo follows X_hi
+                tc::mma(C.tV, ah, bh, C.id2, k > 0);  // [Phi_hi^T X_hi | Phi_hi^T X_lo]
+                tc::mma(C.tV, al, bh, C.id, 1);       // + Phi_lo^T X_hi into the first half
             }
             tc::commit(C.bar2);
         }
@@ -847,6 +857,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     C.tS = tmem + TC_SCOL;
     C.lanes = (uint32_t)((C.warp & 3) * 32) << 16;  // this warp's TMEM lane quarter
     C.id = tc::idesc(128, np);
+    C.id2 = tc::idesc(128, 2 * np);
     C.su = tc::smem_u32(smem);
     (void)nq;  // == NQ: the host launches each molecule with its own size class
     tc_loop<TA, FINAL, NQ>(b, C);

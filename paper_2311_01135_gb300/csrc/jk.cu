@@ -424,8 +424,8 @@ void launch_fix_list(const DevBatch &b, cudaStream_t s) { fix_list_kernel<<<b.nm
 // pair data minus the FP32 store block, contracted with the FP64 density and
 // added to the FP64 J'/K' accumulators.
 template <int LA, int LB, int LC, int LD>
-__global__ void __launch_bounds__(128) jk_fix_kernel(DevBatch b, int ci, int mode) {
-    const int m = blockIdx.y;
+__global__ void __launch_bounds__(128) jk_fix_kernel(DevBatch b, int ci, int mode, const int *mlist) {
+    const int m = mlist ? mlist[blockIdx.y] : blockIdx.y;
     if (mode == 0 && !b.st[m].active) return;
     const int cntm = min(b.fixcount[m * 6 + ci], RKS_FIX_CAP);
     const MolDesc md = b.mol[m];
@@ -503,12 +503,13 @@ __global__ void __launch_bounds__(128) jk_fix_kernel(DevBatch b, int ci, int mod
     }
 }
 
-void launch_jk_fix(const DevBatch &b, int mode, cudaStream_t s) {
-    const dim3 g(8, b.nmol);  // grid-stride over each molecule's list
-    jk_fix_kernel<0, 0, 0, 0><<<g, 128, 0, s>>>(b, 0, mode);
-    jk_fix_kernel<1, 0, 0, 0><<<g, 128, 0, s>>>(b, 1, mode);
-    jk_fix_kernel<1, 0, 1, 0><<<g, 128, 0, s>>>(b, 2, mode);
-    jk_fix_kernel<1, 1, 0, 0><<<g, 128, 0, s>>>(b, 3, mode);
-    jk_fix_kernel<1, 1, 1, 0><<<g, 128, 0, s>>>(b, 4, mode);
-    jk_fix_kernel<1, 1, 1, 1><<<g, 128, 0, s>>>(b, 5, mode);
+void launch_jk_fix(const DevBatch &b, int mode, cudaStream_t s, const int *mlist, int nlist, int nchunk) {
+    const dim3 g(mlist ? nchunk : 8, mlist ? nlist : b.nmol);  // grid-stride over each molecule's list
+    if (g.y == 0) return;
+    jk_fix_kernel<0, 0, 0, 0><<<g, 128, 0, s>>>(b, 0, mode, mlist);
+    jk_fix_kernel<1, 0, 0, 0><<<g, 128, 0, s>>>(b, 1, mode, mlist);
+    jk_fix_kernel<1, 0, 1, 0><<<g, 128, 0, s>>>(b, 2, mode, mlist);
+    jk_fix_kernel<1, 1, 0, 0><<<g, 128, 0, s>>>(b, 3, mode, mlist);
+    jk_fix_kernel<1, 1, 1, 0><<<g, 128, 0, s>>>(b, 4, mode, mlist);
+    jk_fix_kernel<1, 1, 1, 1><<<g, 128, 0, s>>>(b, 5, mode, mlist);
 }

@@ -25,7 +25,10 @@ int launch_jk(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf
 // step one thread per listed quartet recomputes it in FP64 and contracts
 // (I64 - I32) with D into the FP64 accumulators.
 void launch_fix_list(const DevBatch &b, cudaStream_t s);
-void launch_jk_fix(const DevBatch &b, int mode, cudaStream_t s);
+// mlist (nlist molecules, nchunk blocks each): only those molecules (the
+// precise reruns); null: every molecule (active ones when mode 0), 8 blocks each.
+void launch_jk_fix(const DevBatch &b, int mode, cudaStream_t s, const int *mlist = nullptr, int nlist = 0,
+                   int nchunk = 8);
 // AO + density + B3LYP + V_xc on the grid; acc_fp64 and mode as above.
 // skip_tc: leave out the molecules the tensor-core kernel takes (grid_tc_fits).
 void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int skip_tc, int max_nbf, int max_nsh,
@@ -53,8 +56,9 @@ void launch_scf_guess(const DevBatch &b, int max_nbf, int only_rechecked, cudaSt
 // (rechecked = 2, inactive; their indices appended to list); those above
 // recheck_err are reset to iterate again from the initial guess (active,
 // rechecked = 1); the others become inactive.  counts[0] / counts[1] get the
-// number of each; list has room for every molecule.
-void launch_mark_recheck(const DevBatch &b, int *counts, int *list, cudaStream_t s);
+// number of each; list (FP64 redo) and list1 (precise rerun, any order) have
+// room for every molecule.
+void launch_mark_recheck(const DevBatch &b, int *counts, int *list, int *list1, cudaStream_t s);
 // Results of the FP64 redo: child molecule k replaces parent molecule map[k]
 // (state, orbital energies, output density); marks it rechecked = 2.
 void launch_adopt(const DevBatch &parent, const DevBatch &child, const int *map, int nchild, cudaStream_t s);

@@ -192,11 +192,7 @@ void launch_scf_guess(const DevBatch &b, int max_nbf, int only_rechecked, cudaSt
 // FP32 (paper Section 3.2, "Numerical Error": the float32 results are taken
 // for the converged ~99%, the rest recomputed in float64).  The rest wait for
 // the final step.  The decision reads only the molecule's own state.
-__global__ void mark_recheck_kernel(DevBatch b, int *counts, int *list) {
-    __shared__ int tot;
-    if (threadIdx.x == 0) tot = 0;
-    __syncthreads();
-    int n = 0;
+__global__ void mark_recheck_kernel(DevBatch b, int *counts, int *list, int *list1) {
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < b.nmol; m += gridDim.x * blockDim.x) {
         MolState &st = b.st[m];
         const bool bad = st.status != RKS_STATUS_OK_ || !(st.max_err <= b.recheck_fp64_err);
@@ -208,6 +204,7 @@ __global__ void mark_recheck_kernel(DevBatch b, int *counts, int *list) {
             st.active = 0;
             list[atomicAdd(&counts[1], 1)] = m;
         } else if (again) {
+            list1[atomicAdd(&counts[0], 1)] = m;
             st.rechecked = 1;
             st.active = 1;
             st.iter = 0;
@@ -219,19 +216,15 @@ __global__ void mark_recheck_kernel(DevBatch b, int *counts, int *list) {
             st.status = RKS_STATUS_OK_;
             st.eigh_fail = 0;
             st.c_valid = 0;
-            n++;
         } else {
             st.active = 0;
         }
     }
-    if (n) atomicAdd(&tot, n);
-    __syncthreads();
-    if (threadIdx.x == 0 && tot) atomicAdd(&counts[0], tot);
 }
 
-void launch_mark_recheck(const DevBatch &b, int *counts, int *list, cudaStream_t s) {
+void launch_mark_recheck(const DevBatch &b, int *counts, int *list, int *list1, cudaStream_t s) {
     cudaMemsetAsync(counts, 0, 2 * sizeof(int), s);
-    mark_recheck_kernel<<<(b.nmol + 255) / 256, 256, 0, s>>>(b, counts, list);
+    mark_recheck_kernel<<<(b.nmol + 255) / 256, 256, 0, s>>>(b, counts, list, list1);
 }
 
 // One block per redone molecule: its FP64 state and output density replace
