@@ -173,6 +173,23 @@ int rks_options_default(rks_options *o);
  * negative RKS_EINVAL for an unsupported element or natom <= 0. */
 int rks_nbf(int32_t natom, const int32_t *Z);
 
+/* The tensor-core grid kernel's column plan of a molecule (no context
+ * needed; mixed path, Section 3.1 V_xc on the grid).  The kernel's threads own
+ * AO columns in four quarters of NQ = 4, 8, 12, 16 or 20 (padded basis 4 NQ);
+ * a quarter is NQ / 5 units of five columns (a heavy atom's 1s, 2s, 2px, 2py,
+ * 2pz, or up to five hydrogens) and NQ % 5 single hydrogen columns.
+ * plan: caller-owned, RKS_TC_PLAN_INTS int32 written:
+ *   [q * 5 + k], k < NQ / 5: unit word of quarter q: bit 31 set for a heavy
+ *       atom; atom indices (0-based, molecule order) in 6-bit fields, field r
+ *       for slot r, 63 = empty slot (a heavy unit uses field 0 only)
+ *   [q * 5 + 4]: atom indices of the quarter's single columns, same fields
+ *   [20 + c], c < 80: AO index of the kernel's column c (-1: padding)
+ * Returns NQ, 0 when the kernel does not take the molecule (more than 63
+ * atoms, a basis above 80 functions, or more heavy atoms than units at every
+ * NQ; the CUDA-core grid kernel runs it), or RKS_EINVAL for invalid input. */
+#define RKS_TC_PLAN_INTS 100
+int rks_tc_plan(int32_t natom, const int32_t *Z, int32_t *plan);
+
 const char *rks_strerror(int code);
 /* Last CUDA / internal error message of the context (or the library when ctx is NULL). */
 const char *rks_last_error(rks_ctx *ctx);

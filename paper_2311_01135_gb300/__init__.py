@@ -64,6 +64,7 @@ _P = ctypes.c_void_p
 _SIGS = {
     "rks_options_default": (ctypes.c_int, [ctypes.POINTER(rks_options)]),
     "rks_nbf": (ctypes.c_int, [ctypes.c_int32, _P]),
+    "rks_tc_plan": (ctypes.c_int, [ctypes.c_int32, _P, _P]),
     "rks_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "rks_last_error": (ctypes.c_char_p, [_P]),
     "rks_create": (ctypes.c_int, [ctypes.POINTER(rks_options), ctypes.POINTER(_P)]),
@@ -142,6 +143,18 @@ def options(**kw):
 def rks_nbf(Z):
     Z = np.ascontiguousarray(Z, np.int32)
     return _chk(lib().rks_nbf(len(Z), _ptr(Z)), "rks_nbf")
+
+
+RKS_TC_PLAN_INTS = 100
+
+
+def rks_tc_plan(Z):
+    """(NQ, plan[RKS_TC_PLAN_INTS]) of the tensor-core grid kernel's column
+    plan; NQ = 0 when the CUDA-core grid kernel takes the molecule."""
+    Z = np.ascontiguousarray(Z, np.int32)
+    plan = np.zeros(RKS_TC_PLAN_INTS, np.int32)
+    nq = _chk(lib().rks_tc_plan(len(Z), _ptr(Z), _ptr(plan)), "rks_tc_plan")
+    return nq, plan
 
 
 class Context:

@@ -31,6 +31,8 @@ struct MolDesc {
     long long eri_cap;  // store capacity (unscreened upper bound, elements)
     long long mat0;     // FP64 matrix arena (doubles); see MatSlot
     long long acc0;     // accumulator arena offset (elements), 3 * nbf^2
+    int tcq;            // tensor-core grid kernel: columns per quarter NQ (0: CUDA-core kernel)
+    int pad_;
 };
 
 // FP64 matrices of one molecule, each nbf*nbf, at mat0 + slot * nbf*nbf.
@@ -98,14 +100,22 @@ __device__ __forceinline__ void exc_add(long long *p, double x) {
     atomicAdd((unsigned long long *)p, (unsigned long long)__double2ll_rn(x * RKS_FX_EXC));
 }
 
-// Molecules the tensor-core grid kernel takes (padded basis and shell count
-// of its shared-memory layout).  The choice is made per molecule, so a
-// molecule runs the same arithmetic whatever else is in its batch.
+// The tensor-core grid kernel's column plan (one per molecule it takes; the
+// choice is made per molecule, so a molecule runs the same arithmetic
+// whatever else is in its batch).  Its threads own AO columns in four
+// quarters of NQ = 4, 8, 12, 16 or 20 (padded basis 4 NQ <= 80); a quarter is
+// NQ / 5 units of five columns and NQ % 5 single columns.  A unit holds one
+// heavy atom (1s, 2s, 2px, 2py, 2pz: STO-3G for C, N, O, F, with the 2s and
+// 2p shells sharing exponents) or up to five hydrogens; a single column holds
+// one hydrogen.  Per molecule, RKS_TC_PLAN ints:
+//   [q * 5 + k], k < NQ / 5: unit word of quarter q: bit 31 heavy; atom ids
+//                             in 6-bit fields (field r = slot r; 63 = empty)
+//   [q * 5 + 4]:             the single columns' atom ids, same fields
+//   [20 + c], c < 80:        AO index of the kernel's column c (-1: padding)
 #define RKS_TC_NPMAX 80
-#define RKS_TC_NSHMAX 60
-__host__ __device__ inline bool grid_tc_fits(int nbf, int nsh) {
-    return ((nbf + 15) & ~15) <= RKS_TC_NPMAX && nsh <= RKS_TC_NSHMAX;
-}
+#define RKS_TC_NATMAX 63
+#define RKS_TC_PLAN 100
+#define RKS_TC_EMPTY 63
 
 // Device view of a batch (passed by value to kernels).
 struct DevBatch {
@@ -141,10 +151,11 @@ struct DevBatch {
     double fix_theta;
     // grid (SoA, padded blocks; padding points have w = 0)
     void *gx, *gy, *gz, *gw;
-    // per 128-point block: shells significant in it, bit per shell (packing
-    // order), [2 * block] iterations, [2 * block + 1] final step; filled for
-    // the molecules the tensor-core grid kernel takes (mixed path), else null
+    // per 128-point block: atoms with a shell significant in it, bit per
+    // atom, [2 * block] iterations, [2 * block + 1] final step; filled for the
+    // molecules the tensor-core grid kernel takes (mixed path), else null
     unsigned long long *blk_mask;
+    const int *tc_plan;     // [nmol][RKS_TC_PLAN] column plans (mixed path), else null
     // FP64 matrices
     double *mat;
     // accumulators J', K', V' (3 * nbf^2 per molecule at acc0): 64-bit fixed

@@ -112,6 +112,17 @@ extern "C" int rks_nbf(int32_t natom, const int32_t *Z) {
     return n;
 }
 
+static int tc_plan_mol(int na, const int32_t *Zm, int nbf, int *plan);
+static_assert(RKS_TC_PLAN == RKS_TC_PLAN_INTS, "one plan layout on both sides of the ABI");
+
+extern "C" int rks_tc_plan(int32_t natom, const int32_t *Z, int32_t *plan) {
+    std::call_once(g_basis_once, init_basis);
+    if (!plan) return RKS_EINVAL;
+    const int nbf = rks_nbf(natom, Z);
+    if (nbf < 0) return nbf;
+    return tc_plan_mol(natom, Z, nbf, plan);
+}
+
 extern "C" const char *rks_strerror(int code) {
     switch (code) {
     case RKS_OK: return "ok";
@@ -347,6 +358,84 @@ static int validate(int natom, const int *Z, const double *xyz, int *nbf_out) {
     return RKS_OK;
 }
 
+// Column plan of the tensor-core grid kernel for one molecule (layout in
+// common.cuh).  Heavy atoms go round-robin to the quarters' units; hydrogens
+// then fill the remaining unit slots and single columns, round-robin over the
+// quarters with room.  Returns NQ, or 0 when no class fits (more than
+// RKS_TC_NATMAX atoms, a basis above 80, or more heavy atoms than units): the
+// CUDA-core kernel takes the molecule.
+static int tc_plan_mol(int na, const int32_t *Zm, int nbf, int *plan) {
+    if (na > RKS_TC_NATMAX) return 0;
+    std::vector<int> heavy, light, ao_first(na);
+    int ao = 0;
+    for (int i = 0; i < na; i++) {
+        const ElemDef *E = elem_of(Zm[i]);
+        ao_first[i] = ao;
+        if (E->nsh == 1 && E->sh[0].l == 0) {
+            light.push_back(i);
+            ao += 1;
+        } else if (E->nsh == 3 && E->sh[0].l == 0 && E->sh[1].l == 0 && E->sh[2].l == 1 &&
+                   E->sh[1].e[0] == E->sh[2].e[0] && E->sh[1].e[1] == E->sh[2].e[1] &&
+                   E->sh[1].e[2] == E->sh[2].e[2]) {
+            heavy.push_back(i);
+            ao += 5;
+        } else {
+            return 0;
+        }
+    }
+    for (int nq = 4; nq <= RKS_TC_NPMAX / 4; nq += 4) {
+        if (4 * nq < nbf) continue;
+        const int U = nq / 5, R = nq % 5;
+        if ((int)heavy.size() > 4 * U) continue;
+        // slots[q]: atom per column slot (unit k slot r at 5k + r, single column r at 5U + r)
+        std::vector<std::vector<int>> slot(4, std::vector<int>(nq, RKS_TC_EMPTY));
+        std::vector<int> hq(4, 0), used(4, 0);
+        for (size_t i = 0; i < heavy.size(); i++) {
+            const int q = (int)(i % 4), k = (int)(i / 4);
+            slot[q][5 * k] = heavy[i];
+            hq[q] = k + 1;
+        }
+        for (int q = 0; q < 4; q++) used[q] = 5 * hq[q];
+        size_t li = 0;
+        bool room = true;
+        while (li < light.size() && room) {
+            room = false;
+            for (int q = 0; q < 4 && li < light.size(); q++)
+                if (used[q] < nq) {
+                    slot[q][used[q]++] = light[li++];
+                    room = true;
+                }
+        }
+        if (li < light.size()) continue;
+        for (int q = 0; q < 4; q++) {
+            for (int k = 0; k < 5; k++) plan[q * 5 + k] = 0;
+            for (int k = 0; k < U; k++) {
+                uint32_t w = 0;
+                if (k < hq[q]) {
+                    w = (1u << 31) | (uint32_t)slot[q][5 * k];
+                    for (int r = 1; r < 5; r++) w |= (uint32_t)RKS_TC_EMPTY << (6 * r);
+                } else {
+                    for (int r = 0; r < 5; r++) w |= (uint32_t)slot[q][5 * k + r] << (6 * r);
+                }
+                plan[q * 5 + k] = (int)w;
+            }
+            uint32_t w = 0;
+            for (int r = 0; r < 5; r++) w |= (uint32_t)(r < R ? slot[q][5 * U + r] : RKS_TC_EMPTY) << (6 * r);
+            plan[q * 5 + 4] = (int)w;
+            for (int j = 0; j < nq; j++) {
+                const int c = q * nq + j, A = slot[q][j];
+                int v = -1;
+                if (j < 5 * U && j / 5 < hq[q]) v = ao_first[slot[q][5 * (j / 5)]] + j % 5;
+                else if (A != RKS_TC_EMPTY) v = ao_first[A];
+                plan[20 + c] = v;
+            }
+        }
+        for (int c = 4 * nq; c < RKS_TC_NPMAX; c++) plan[20 + c] = -1;
+        return nq;
+    }
+    return 0;
+}
+
 // Release the FP64 redo batch of the previous run.  Its results are read by
 // the adopt kernel on the parent's stream, which may still be queued (a
 // caller may enqueue the next run without waiting): drain the parent's
@@ -454,7 +543,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     std::vector<int> hZ, hsh_atom, hsh_l, hsh_ao0, hcand_mol;
     std::vector<double> haxyz, hsh_xyz, hsh_ex, hsh_co;
     std::vector<int2> hcand;
-    std::vector<int> hblk_mol;
+    std::vector<int> hblk_mol, hplan;
     long long atom_off = 0, sh_off = 0, pair_off = 0, pts_off = 0, eri_off = 0, mat_off = 0, acc_off = 0;
     for (int m = 0; m < nmol; m++) {
         const int na = natom[m];
@@ -523,6 +612,11 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
         d.npts = npts; d.nblk = nblk; d.pts0 = pts_off;
         d.eri0 = eri_off; d.eri_cap = cap;
         d.mat0 = mat_off; d.acc0 = acc_off;
+        if (o.precision == RKS_MIXED) {
+            int pl[RKS_TC_PLAN];
+            d.tcq = tc_plan_mol(na, Zm, nbf, pl);
+            hplan.insert(hplan.end(), pl, pl + RKS_TC_PLAN);
+        }
         b->hm[m] = {na, nbf, nel / 2, nsh, npair_all, cap, npts};
         b->max_nbf = std::max(b->max_nbf, nbf);
         b->max_nsh = std::max(b->max_nsh, nsh);
@@ -581,6 +675,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
         (rc = dalloc(b, &b->recheck_list1, nmol)) ||
         (o.precision == RKS_MIXED && (rc = dalloc(b, &d.blk_mask, 2 * b->nblk_total))) ||
         (o.precision == RKS_MIXED && (rc = dalloc(b, (int **)&b->tcc.list, nmol))) ||
+        (o.precision == RKS_MIXED && (rc = dalloc(b, (int **)&d.tc_plan, (size_t)nmol * RKS_TC_PLAN))) ||
         (rc = dalloc(b, &d.jk_next, nmol))) {
         rks_batch_destroy(b);
         return rc;
@@ -614,21 +709,16 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     UP(dcm, hcand_mol);
     UP(b->blk_mol, hblk_mol);
     if (b->tcc.list) {
-        // tensor-core grid kernel: molecules by padded basis size class
+        // tensor-core grid kernel: molecules by column class NQ = 4 (k + 1)
         std::vector<int> lst;
         for (int k = 0; k < 5; k++) {
             b->tcc.off[k] = (int)lst.size();
-            b->tcc.max_nsh[k] = 0;
-            for (int m = 0; m < nmol; m++) {
-                const MolDesc &q = b->md[m];
-                if (grid_tc_fits(q.nbf, q.nsh) && ((q.nbf + 15) / 16) - 1 == k) {
-                    lst.push_back(m);
-                    b->tcc.max_nsh[k] = std::max(b->tcc.max_nsh[k], q.nsh);
-                }
-            }
+            for (int m = 0; m < nmol; m++)
+                if (b->md[m].tcq == 4 * (k + 1)) lst.push_back(m);
             b->tcc.count[k] = (int)lst.size() - b->tcc.off[k];
         }
         UP((int *)b->tcc.list, lst);
+        UP((int *)d.tc_plan, hplan);
     }
 #undef UP
     b->hZ = hZ;
@@ -726,8 +816,8 @@ static int fock_pass(rks_batch *b, int prec, int mode) {
         }
     }
     if (d.xc) {
-        // Molecules that fit the tensor-core kernel (grid_tc_fits, decided per
-        // molecule, never per batch) run it; in the final step it forms the
+        // Molecules with a tensor-core column plan (MolDesc::tcq, decided per
+        // molecule, never per batch) run that kernel; in the final step it forms the
         // density on the CUDA cores (the tensor cores' truncating accumulation
         // would bias E_xc).  The others run the CUDA-core kernel.
         const bool tc = b->precision == RKS_MIXED && c->opt.grid_tc;
@@ -735,7 +825,7 @@ static int fock_pass(rks_batch *b, int prec, int mode) {
         if (tc) {
             bool any_tc = false;
             for (auto &m : b->md) {
-                if (grid_tc_fits(m.nbf, m.nsh)) any_tc = true;
+                if (m.tcq) any_tc = true;
                 else need_cc = true;
             }
             if (any_tc) {

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
     const int m = blockIdx.y, chunk = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
-    if (skip_tc && grid_tc_fits(b.mol[m].nbf, b.mol[m].nsh)) return;  // done by the tensor-core kernel
+    if (skip_tc && b.mol[m].tcq) return;  // done by the tensor-core kernel
     const int n = md.nbf, nsh = md.nsh;
     const int XS = n | 1;  // odd row stride of X (bank-conflict free both ways)
     T *Ds = (T *)smem_raw;                 // [n][n]

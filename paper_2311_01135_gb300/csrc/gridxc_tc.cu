@@ -2,15 +2,21 @@
 // tensor cores (tcgen05, kind::tf32, 3xTF32 split products, FP32 accumulators
 // in tensor memory).  Same quantities as gridxc.cu (paper Section 3.1 V_xc,
 // Section 3.2 B3LYP, AOs recomputed per block as in Section 5):
-//   GEMM1  T = Phi D            (M = 128 points, N = K = nbf padded to 16)
+//   GEMM1  T = Phi D            (M = 128 points, N = K = np = 4 NQ)
 //   rho_p = sum_n T_pn phi_pn,  grad rho_p = 2 sum_n T_pn grad phi_pn
-//   GEMM2  V' += Phi^T X        (M = 128 AO rows, N = nbf padded, K = 128 points)
+//   GEMM2  V' += Phi^T X        (M = 128 AO rows, N = np, K = 128 points)
 // Split products (Ootomo & Yokota 2022): a = a_hi + a_lo with a_hi the TF32
-// rounding of a; a b ~= a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32.
-// The b_hi and b_lo tiles lie one after the other, so a_hi [b_hi | b_lo] is
-// one MMA of N = 2 np (two halves of the accumulator) and a_lo b_hi a second
-// one into the first half: two MMAs per K step, and the halves are summed
-// when the accumulator is read.
+// rounding of a; a b ~= a_hi b_hi + a_hi b_lo + a_lo b_hi: three MMAs per K
+// step into one FP32 accumulator.
+//
+// Column order.  The kernel works in its own order of the AO basis (the
+// molecule's column plan, built on the host, layout in common.cuh): thread
+// quarter q owns columns q NQ .. q NQ + NQ - 1, made of units of five columns
+// (a heavy atom's 1s, 2s, 2px, 2py, 2pz, or up to five hydrogens) and single
+// hydrogen columns.  Which kind a unit is does not vary across a warp, and
+// where each value sits is fixed at compile time, so the per-column work is
+// straight-line code.  D is loaded in that order and V' is written back
+// through the same map.
 //
 // Operand layouts (every tcgen05 TF32 operand is K-major):
 //  * GEMM1 contracts over AOs: Phi as a [point][AO] tile and D as a [nu][mu]
@@ -26,25 +32,27 @@
 //    A K step of 8 points is 32 bytes inside an atom.
 //
 // One thread block (512 threads, one per SM) owns 1/nchunk of a molecule's
-// 128-point grid blocks and keeps V' in registers across them.  Thread t
-// serves point p = t % 128 and the AO column quarter q4 = t / 128; the radial
-// values g, g' of its columns stay in its registers between phases.  Per block:
-//   A   radial values of the thread's columns (one set of exponentials per
-//       shell, shared by an atom's 2s and 2p): overlaps the previous block's GEMM2
-//   B   the previous block's V' from tensor memory into registers
+// 128-point grid blocks and keeps the running sum of V' in tensor memory.
+// Thread t serves point p = t % 128 and the column quarter q4 = t / 128; the
+// radial values g, g' of its columns stay in its registers between phases.
+// Per block:
+//   A   radial values, unit by unit (an atom's 2s and 2p share one set of
+//       exponentials): overlaps the previous block's GEMM2
+//   B   the previous block's V' added to the running sum
 //   C   Phi (hi, lo); one thread issues GEMM1
 //   E   each thread reads its point's T row segment and forms its share of rho
-//       and grad rho shell by shell
+//       and grad rho
 //   F   B3LYP in three parts on three warp groups
 //   G   Phi^T and X = w (v_rho/2 phi + 2 v_sigma grad rho . grad phi)
 //       (hi, lo) into the GEMM2 tiles (over GEMM1's Phi tile, done with);
 //       one thread issues GEMM2
-// Which shells matter in a block (AO screening) is decided once, when the
+// Which atoms matter in a block (AO screening) is decided once, when the
 // grid is built (grid_mask_kernel), from the block's radius range.
 // FINAL (the mixed final step) forms T on the CUDA cores instead of GEMM1.
 // Waits on the MMA barriers are bounded: on expiry the block records an error
 // flag, waits (bounded) once more, frees its tensor memory and returns.
 #include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -52,18 +60,16 @@
 
 #define TC_BP 128
 #define TC_NPMAX RKS_TC_NPMAX   // padded basis size this kernel handles
-#define TC_NSHMAX RKS_TC_NSHMAX // shells this kernel handles (one 64-bit mask per block)
 #define TC_TMEM_COLS 512
-#define TC_TCOL 0               // TMEM columns of T (GEMM1: two halves of np columns, summed on read)
-#define TC_VCOL 160             // of V' (GEMM2, one block: two halves of np columns)
+#define TC_TCOL 0               // TMEM columns of T (GEMM1, np columns)
+#define TC_VCOL 160             // of V' (GEMM2, one block)
 #define TC_SCOL 320             // and of the running sum of V' over the CTA's blocks
 #define TC_SPIN_LIMIT 4000000  // polls before a wait gives up: >= ~40 ms, far above any MMA here
 #define TC_THREADS 512
 #define TC_SCREEN 1e-9f         // per-block AO screening threshold, iterations
 #define TC_SCREEN_FINAL 1e-14f  // and final step
-#define TC_SHX 12               // floats per shell in shx: a[3], c[3], -2ac[3], pad
 
-static_assert(TC_NSHMAX <= 64, "one 64-bit significance mask per block");
+static_assert(RKS_TC_NATMAX < 64, "one 64-bit significance mask per block, bit 63 never set");
 static_assert(TC_NPMAX / 4 == 20, "a thread owns at most 20 AO columns");
 
 namespace tc {
@@ -149,11 +155,14 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 // inside the buffer.  The rho partials alias the start of the region
 // (written after GEMM1, read before the GEMM2 tiles are written).
 struct TcSmem {
-    uint32_t D_hi, D_lo, phi_hi, phi_lo, pt_hi, pt_lo, x_hi, x_lo, part, xcp, grd, shx, shf, col;
+    uint32_t D_hi, D_lo, phi_hi, phi_lo, pt_hi, pt_lo, x_hi, x_lo, part, xcp, grd, atx, atf, perm;
     uint32_t total;
 };
 
-__host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
+#define TC_NAT 64  // atom table entries: ids 0 .. 62, and 63 = empty slot (all zero)
+#define TC_ATX 32  // floats per atom: float4s a1, c1, -2 a1 c1 (1s), a2, c2s, -2 a2 c2s, c2p, -2 a2 c2p (2s, 2p)
+
+__host__ __device__ inline TcSmem tc_layout(int np) {
     TcSmem s;
     uint32_t o = 0;
     const uint32_t dsz = (uint32_t)np * np * 4, opsz = (uint32_t)TC_BP * np * 4;
@@ -169,10 +178,9 @@ __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
     s.part = s.pt_hi;                       // rho, grad rho partials per AO quarter (4 x 4 x 128 floats)
     s.xcp = o; o += 3 * 2 * TC_BP * 4;      // v_rho, v_sigma per XC part
     s.grd = o; o += 3 * TC_BP * 4;          // grad rho
-    s.shx = o; o += (uint32_t)nsh * TC_SHX * 4;
-    s.shf = o; o += (uint32_t)nsh * 8 * 4;  // per shell: R_owner0 - C (3), pad, R_owner1 - C (3), pad
-    s.col = o; o += (uint32_t)np * 4;       // per AO column: shell << 2 | (component + 1), bit 8: shares the
-                                            // previous column's exponentials; -1 for padding
+    s.atx = o; o += TC_NAT * TC_ATX * 4;    // per atom: exponents and coefficients
+    s.atf = o; o += TC_NAT * 8 * 4;         // per atom: R_owner0 - R_atom (3), pad, R_owner1 - R_atom (3), pad
+    s.perm = o; o += (uint32_t)np * 4;      // AO index of each of the kernel's columns (-1 padding)
     // GEMM2's A operand reads 128 rows (16 row groups of 4 KB, plus the K
     // offset inside an atom) from the start of the Phi^T lo tile: for small
     // bases that runs past the tiles, so the buffer extends to cover it
@@ -181,39 +189,37 @@ __host__ __device__ inline TcSmem tc_layout(int np, int nsh) {
     return s;
 }
 
-// This thread's row of 20 TMEM columns starting at taddr (5 loads of 4
-// columns, one wait; the wait names the registers so that no use moves above it).
-__device__ __forceinline__ void ld20(uint32_t taddr, float *v) {
-    uint32_t r[20];
+// W columns of this thread's TMEM lane row: the loads are issued together,
+// one wait covers them, and each register passes through an empty asm after
+// the wait so that no use of it is scheduled above the wait.
+template <int W> __device__ __forceinline__ void tld_issue(uint32_t taddr, uint32_t *r) {
 #pragma unroll
-    for (int k = 0; k < 5; k++)
+    for (int k = 0; k < W / 4; k++)
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                      : "=r"(r[4 * k]), "=r"(r[4 * k + 1]), "=r"(r[4 * k + 2]), "=r"(r[4 * k + 3])
                      : "r"(taddr + 4 * k));
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
-                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
-                   "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19])
-                 :
-                 : "memory");
+}
+template <int W> __device__ __forceinline__ void tld_done(uint32_t *r, float *v) {
 #pragma unroll
-    for (int j = 0; j < 20; j++) v[j] = __uint_as_float(r[j]);
+    for (int i = 0; i < W; i++) {
+        asm volatile("" : "+r"(r[i]));
+        v[i] = __uint_as_float(r[i]);
+    }
 }
-
-// Four TMEM columns of this thread's lane row (load, wait), and the store back.
-__device__ __forceinline__ void ld4(uint32_t taddr, float *v) {
-    uint32_t r0, r1, r2, r3;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3) : : "memory");
-    v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
+__device__ __forceinline__ void tld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+template <int W> __device__ __forceinline__ void tld(uint32_t taddr, float *v) {
+    uint32_t r[W];
+    tld_issue<W>(taddr, r);
+    tld_wait();
+    tld_done<W>(r, v);
 }
-__device__ __forceinline__ void st4(uint32_t taddr, const float *v) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr),
-                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-                 "r"(__float_as_uint(v[3]))
-                 : "memory");
+template <int W> __device__ __forceinline__ void tst(uint32_t taddr, const float *v) {
+#pragma unroll
+    for (int k = 0; k < W / 4; k++)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr + 4 * k),
+                     "r"(__float_as_uint(v[4 * k])), "r"(__float_as_uint(v[4 * k + 1])),
+                     "r"(__float_as_uint(v[4 * k + 2])), "r"(__float_as_uint(v[4 * k + 3]))
+                     : "memory");
 }
 
 // Lower bound on the distance from a shell centre to any point of a block:
@@ -225,23 +231,23 @@ __device__ __forceinline__ float shell_rmin(float d, float lo, float hi) {
 
 // ------------------------------------------------------- block masks (setup)
 // One thread block per 128-point grid block of a molecule the tensor-core
-// kernel takes: bit s of mask[0] (iterations) / mask[1] (final step) is set
-// when shell s may exceed the screening threshold somewhere in the block:
-// |phi|, |grad phi| <= sum_k |c_k| e^(-a_k r^2) (1 + r + 2 a_k r^3), which
-// decreases in r beyond r = 4 bohr for every STO-3G exponent, evaluated at
-// the smallest distance from the shell centre to the block's points.
+// kernel takes: bit A of mask[0] (iterations) / mask[1] (final step) is set
+// when a shell of atom A may exceed the screening threshold somewhere in the
+// block: |phi|, |grad phi| <= sum_k |c_k| e^(-a_k r^2) (1 + r + 2 a_k r^3),
+// which decreases in r beyond r = 4 bohr for every STO-3G exponent, evaluated
+// at the smallest distance from the shell centre to the block's points.
 __global__ void __launch_bounds__(TC_BP) grid_mask_kernel(DevBatch b, const int *blk_mol,
                                                           unsigned long long *mask) {
     const long long gblk = blockIdx.x;
     const int m = blk_mol[gblk];
     const MolDesc md = b.mol[m];
-    if (!grid_tc_fits(md.nbf, md.nsh)) return;
+    if (!md.tcq) return;
     __shared__ unsigned blk_r[4];  // radius range per owner (float bits; r >= 0 orders as unsigned)
-    __shared__ unsigned long long bits[2][2];
+    __shared__ unsigned long long abits[2];
     __shared__ int nsig[2][2];
     const int t = threadIdx.x, lane = t & 31;
     if (t < 4) blk_r[t] = (t & 1) ? 0u : 0x7f800000u;
-    if (t < 4) bits[t >> 1][t & 1] = 0ull;
+    if (t < 2) abits[t] = 0ull;
     __syncthreads();
     const long long p0 = gblk * TC_BP - md.pts0;  // first point of the block, molecule-local
     const int npa = b.n_rad * b.n_theta * b.n_phi;
@@ -262,8 +268,7 @@ __global__ void __launch_bounds__(TC_BP) grid_mask_kernel(DevBatch b, const int 
         atomicMax(&blk_r[3], hi1);
     }
     __syncthreads();
-    bool on_it = false, on_fin = false;
-    if (t < md.nsh) {
+    if (t < md.nsh) {  // nsh <= nbf <= 80 for the molecules with a plan
         const int g = md.sh0 + t;
         float rmin = 3.4e38f;
 #pragma unroll
@@ -275,9 +280,8 @@ __global__ void __launch_bounds__(TC_BP) grid_mask_kernel(DevBatch b, const int 
             const float dx = (float)(ra[0] - rc[0]), dy = (float)(ra[1] - rc[1]), dz = (float)(ra[2] - rc[2]);
             rmin = fminf(rmin, shell_rmin(sqrtf(dx * dx + dy * dy + dz * dz), lo, hi));
         }
-        if (rmin < 4.f) {
-            on_it = on_fin = true;
-        } else {
+        bool on_it = true, on_fin = true;
+        if (rmin >= 4.f) {
             float bound = 0.f;
             for (int k = 0; k < 3; k++) {
                 const float a = (float)b.sh_ex[g * 3 + k];
@@ -287,22 +291,28 @@ __global__ void __launch_bounds__(TC_BP) grid_mask_kernel(DevBatch b, const int 
             on_it = bound > TC_SCREEN;
             on_fin = bound > TC_SCREEN_FINAL;
         }
+        const unsigned long long bit = 1ull << b.sh_atom[g];
+        if (on_it) atomicOr(&abits[0], bit);
+        if (on_fin) atomicOr(&abits[1], bit);
     }
-    const unsigned bi = __ballot_sync(0xffffffffu, on_it), bf = __ballot_sync(0xffffffffu, on_fin);
-    // significant AOs (1 per s shell, 3 per p shell)
-    const int ncomp = t < md.nsh ? (b.sh_l[md.sh0 + t] ? 3 : 1) : 0;
-    const int ni = __reduce_add_sync(0xffffffffu, on_it ? ncomp : 0);
-    const int nf = __reduce_add_sync(0xffffffffu, on_fin ? ncomp : 0);
+    __syncthreads();
+    // significant AOs: 5 per heavy atom, 1 per hydrogen
+    int ni = 0, nf = 0;
+    if (t < md.natom) {
+        const int nao = b.Z[md.atom0 + t] > 1 ? 5 : 1;
+        ni = ((abits[0] >> t) & 1ull) ? nao : 0;
+        nf = ((abits[1] >> t) & 1ull) ? nao : 0;
+    }
+    ni = __reduce_add_sync(0xffffffffu, ni);
+    nf = __reduce_add_sync(0xffffffffu, nf);
     if (lane == 0 && t < 64) {
-        bits[0][t >> 5] = bi;
-        bits[1][t >> 5] = bf;
         nsig[0][t >> 5] = ni;
         nsig[1][t >> 5] = nf;
     }
     __syncthreads();
     if (t == 0) {
-        mask[2 * gblk] = bits[0][0] | (bits[0][1] << 32);
-        mask[2 * gblk + 1] = bits[1][0] | (bits[1][1] << 32);
+        mask[2 * gblk] = abits[0];
+        mask[2 * gblk + 1] = abits[1];
         const double si = nsig[0][0] + nsig[0][1], sf = nsig[1][0] + nsig[1][1];
         atomicAdd(&b.st[m].grid_pairs[0], (double)TC_BP * si * si);
         atomicAdd(&b.st[m].grid_pairs[1], (double)TC_BP * sf * sf);
@@ -325,101 +335,115 @@ struct TcCta {
     const MolDesc *md;
     TcSmem L;
     unsigned char *sm;
-    const int *col;
-    const float *shx, *shf;
+    const float *atx, *atf;
+    const int *perm;
     float *part, *xcp, *grd;
     uint64_t *bar1, *bar2;
     int *s_fail;
-    uint32_t su, sg, tT, tV, tS, lanes, id, id2;
-    int m, chunk, nchunk, n, nsh, np, t, lane, warp, p, q4, c0;
+    uint32_t su, sg, tT, tV, tS, lanes, id;
+    int m, chunk, nchunk, n, np, t, lane, warp, p, q4, c0;
 };
 
-// The thread's columns c0 .. c0 + NQ - 1 are described once per CTA by bit
-// masks (warp-uniform: a warp's 32 threads share the quarter): valid (not
-// padding), start (first column of its shell in the run), share (2p column
-// right after its atom's 2s column, same exponents) and a 2-bit component
-// code (0 s, 1..3 p_x, p_y, p_z).  Per block only the significance bits
-// change: one ballot over the warp's lanes.
-struct ColBits {
-    uint32_t valid, start, share;
-    uint64_t comp;
-};
-
-template <int NQ> __device__ __forceinline__ ColBits col_bits(const int *col, int c0) {
-    ColBits cb{0u, 0u, 0u, 0ull};
-    int prev = -1;
-#pragma unroll
-    for (int j = 0; j < NQ; j++) {
-        const int raw = col[c0 + j];
-        if (raw >= 0) {
-            const int s = (raw >> 2) & 63;
-            cb.valid |= 1u << j;
-            if (j == 0 || s != prev) cb.start |= 1u << j;
-            if (raw & 0x100) cb.share |= 1u << j;
-            cb.comp |= (uint64_t)(raw & 3) << (2 * j);
-            prev = s;
-        } else {
-            prev = -1;
-        }
-    }
-    return cb;
+// Radial values of a hydrogen slot (atom A) at the point:
+// g = sum_k c_k e^(-a_k r^2), g' = sum_k -2 a_k c_k e^(-a_k r^2), zero when the
+// atom is below the block's screen (the empty id's bit is never set).
+__device__ __forceinline__ void tc_light(const float *atx, const float *atfp, uint32_t A, unsigned long long amask,
+                                         float px, float py, float pz, float &g, float &gp) {
+    const float4 dl = *(const float4 *)(atfp + A * 8);
+    const float dx = dl.x + px, dy = dl.y + py, dz = dl.z + pz;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float *e = atx + A * TC_ATX;
+    const float4 a = *(const float4 *)e, c = *(const float4 *)(e + 4), mm = *(const float4 *)(e + 8);
+    const float e0 = __expf(-a.x * r2), e1 = __expf(-a.y * r2), e2 = __expf(-a.z * r2);
+    const bool on = (amask >> A) & 1ull;
+    g = on ? c.x * e0 + c.y * e1 + c.z * e2 : 0.f;
+    gp = on ? mm.x * e0 + mm.y * e1 + mm.z * e2 : 0.f;
 }
 
-#define TC_ON(j) ((on >> (j)) & 1u)
-#define TC_FRESH(j) (TC_ON(j) && ((cb.start >> (j)) & 1u))
-#define TC_COMP(j) ((int)((cb.comp >> (2 * (j))) & 3ull))
-#define TC_SHELL(j) ((C.col[C.c0 + (j)] >> 2) & 63)
+// A heavy atom's unit: g[0..2] = g_1s, g_2s, g_2p and gp[0..2] their
+// derivative factors (the 2s and 2p shells share one set of exponentials),
+// and the offset d = r - R_A in g[3], g[4], gp[3].
+__device__ __forceinline__ void tc_heavy(const float *atx, const float *atfp, uint32_t A, float px, float py,
+                                         float pz, float *g, float *gp) {
+    const float4 dl = *(const float4 *)(atfp + A * 8);
+    const float dx = dl.x + px, dy = dl.y + py, dz = dl.z + pz;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float *e = atx + A * TC_ATX;
+    const float4 a1 = *(const float4 *)e, c1 = *(const float4 *)(e + 4), m1 = *(const float4 *)(e + 8);
+    const float4 a2 = *(const float4 *)(e + 12), c2 = *(const float4 *)(e + 16), m2 = *(const float4 *)(e + 20);
+    const float4 c3 = *(const float4 *)(e + 24), m3 = *(const float4 *)(e + 28);
+    const float e0 = __expf(-a1.x * r2), e1 = __expf(-a1.y * r2), e2 = __expf(-a1.z * r2);
+    const float f0 = __expf(-a2.x * r2), f1 = __expf(-a2.y * r2), f2 = __expf(-a2.z * r2);
+    g[0] = c1.x * e0 + c1.y * e1 + c1.z * e2;
+    gp[0] = m1.x * e0 + m1.y * e1 + m1.z * e2;
+    g[1] = c2.x * f0 + c2.y * f1 + c2.z * f2;
+    gp[1] = m2.x * f0 + m2.y * f1 + m2.z * f2;
+    g[2] = c3.x * f0 + c3.y * f1 + c3.z * f2;
+    gp[2] = m3.x * f0 + m3.y * f1 + m3.z * f2;
+    g[3] = dx;
+    g[4] = dy;
+    gp[3] = dz;
+    gp[4] = 0.f;
+}
 
-// G for one value of c0 & 7 (B = 0 or 4, known at compile time): the
-// swizzled offsets of the thread's column rows are a per-thread base plus
-// compile-time constants and one of eight per-thread XOR terms.
+// G for one value of c0 & 7 (B = 0 or 4, known at compile time): Phi^T and X
+// (hi, lo) of the thread's columns into the swizzled GEMM2 tiles.  With
+// a = w v_rho / 2 and b = 2 w v_sigma grad rho: an s column has
+// X = a g + g' (b . d); a p column c has X_c = d_c (a g + g' (b . d)) + b_c g.
 template <int NQ, int B>
-__device__ __forceinline__ void tc_write_gemm2(const TcCta &C, const ColBits &cb, uint32_t on, const float *gj,
-                                               const float *gpj, const float *shfp, float px, float py, float pz,
+__device__ __forceinline__ void tc_write_gemm2(const TcCta &C, const uint32_t *uw, uint32_t rw, const float *g,
+                                               const float *gp, const float *atfp, float px, float py, float pz,
                                                float a, float bx, float by, float bz) {
+    constexpr int U = NQ / 5, R = NQ % 5;
     const uint32_t pc = (uint32_t)(C.p >> 2) & 7u;
     const uint32_t tbase = (uint32_t)(C.c0 >> 3) * 4096u + (uint32_t)(C.p >> 5) * 1024u + (uint32_t)(C.p & 3) * 4u;
     unsigned char *pth = C.sm + C.L.pt_hi + tbase, *ptl = C.sm + C.L.pt_lo + tbase;
     unsigned char *xh_ = C.sm + C.L.x_hi + tbase, *xl_ = C.sm + C.L.x_lo + tbase;
-    float dx = 0.f, dy = 0.f, dz = 0.f, S = 0.f;
-#pragma unroll
-    for (int j = 0; j < NQ; j++) {
-        constexpr int dummy = 0;
-        (void)dummy;
+    auto put = [&](int j, float f, float x) {
         const int r = (B + j) & 7, grp = (B + j) >> 3;
-        if (TC_FRESH(j)) {
-            const float4 dl = *(const float4 *)(shfp + TC_SHELL(j) * 8);
-            dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
-            S = a * gj[j] + gpj[j] * (bx * dx + by * dy + bz * dz);
-        }
-        const int c = TC_COMP(j);
-        const float dc = c == 1 ? dx : (c == 2 ? dy : dz);
-        const float bc = c == 1 ? bx : (c == 2 ? by : bz);
-        const bool o = TC_ON(j);
-        const float f = o ? (c == 0 ? gj[j] : dc * gj[j]) : 0.f;
-        const float x = o ? (c == 0 ? S : dc * S + bc * gj[j]) : 0.f;
-        const float fh = tc::tf32_hi(f), xh = tc::tf32_hi(x);
         const uint32_t off = (uint32_t)grp * 4096u + (uint32_t)r * 128u + ((pc ^ (uint32_t)r) << 4);
+        const float fh = tc::tf32_hi(f), xh = tc::tf32_hi(x);
         *(float *)(pth + off) = fh;
         *(float *)(ptl + off) = f - fh;
         *(float *)(xh_ + off) = xh;
         *(float *)(xl_ + off) = x - xh;
+    };
+    auto light = [&](int j, uint32_t A) {
+        const float4 dl = *(const float4 *)(atfp + A * 8);
+        const float bd = bx * (dl.x + px) + by * (dl.y + py) + bz * (dl.z + pz);
+        put(j, g[j], a * g[j] + gp[j] * bd);
+    };
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+        const int j = 5 * k;
+        if (uw[k] >> 31) {
+            const float dx = g[j + 3], dy = g[j + 4], dz = gp[j + 3];
+            const float bd = bx * dx + by * dy + bz * dz;
+            const float g2p = g[j + 2], sp = a * g2p + gp[j + 2] * bd;
+            put(j, g[j], a * g[j] + gp[j] * bd);
+            put(j + 1, g[j + 1], a * g[j + 1] + gp[j + 1] * bd);
+            put(j + 2, dx * g2p, dx * sp + bx * g2p);
+            put(j + 3, dy * g2p, dy * sp + by * g2p);
+            put(j + 4, dz * g2p, dz * sp + bz * g2p);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 5; r++) light(j + r, (uw[k] >> (6 * r)) & 63u);
+        }
     }
+#pragma unroll
+    for (int r = 0; r < R; r++) light(5 * U + r, (rw >> (6 * r)) & 63u);
 }
 
 // The block loop of one CTA for threads owning NQ columns each, then the
 // flush of V' and E_xc.
 template <typename TA, bool FINAL, int NQ>
-__device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
+__device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint32_t *uw, uint32_t rw) {
+    constexpr int U = NQ / 5, R = NQ % 5;
     const MolDesc &md = *C.md;
     const int t = C.t, p = C.p, lane = C.lane;
-    const ColBits cb = col_bits<NQ>(C.col, C.c0);
-    // the lane's own column for the per-block significance ballot
-    const int rawl = lane < NQ ? C.col[C.c0 + lane] : -1;
-    const int sl = rawl >= 0 ? (rawl >> 2) & 63 : 0;
     const uint32_t phi_base = (uint32_t)(p >> 3) * C.sg + (uint32_t)(C.c0 >> 2) * 128u + (uint32_t)(p & 7) * 16u;
     uint32_t ph1 = 0, ph2 = 0;
-    bool pending = false;  // a GEMM2 in flight whose V' is not yet in vacc
+    bool pending = false;  // a GEMM2 in flight whose V' is not yet in the running sum
     bool in1 = false;      // a GEMM1 in flight
     bool any_block = false, failed = false;
     double exc = 0.0;
@@ -431,31 +455,35 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
     const int npa = b.n_rad * b.n_theta * b.n_phi;
     float nx = gxp[C.chunk * TC_BP + p], ny = gyp[C.chunk * TC_BP + p], nz = gzp[C.chunk * TC_BP + p];
     float nw = gwp[C.chunk * TC_BP + p];
-    int shf_owner = -1;  // owner atom the shf table was built for
-    float *shf_w = const_cast<float *>(C.shf);
+    int atf_owner = -1;  // owner atom the atf table was built for
+    float *atf_w = const_cast<float *>(C.atf);
 
     // the pending GEMM2's V' row segment added to the running sum (FP32
     // round-to-nearest across blocks; the tensor cores' accumulation only
-    // spans one block)
+    // spans one block): 8 columns per batch of loads, one wait per batch
     auto drain = [&]() -> bool {
         const bool ok = __syncthreads_and(tc::wait(C.bar2, ph2));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) return false;  // still pending: the exit path waits on the same phase
         ph2 ^= 1;
-#pragma unroll
-        for (int kc = 0; kc < NQ / 4; kc++) {
-            float v[4], v2[4], w[4];
-            ld4(C.tV + C.lanes + C.c0 + 4 * kc, v);
-            ld4(C.tV + C.lanes + C.np + C.c0 + 4 * kc, v2);
-#pragma unroll
-            for (int i = 0; i < 4; i++) v[i] += v2[i];
+        auto batch = [&](auto wtag, int c) {
+            constexpr int W = decltype(wtag)::value;
+            uint32_t rv[W], rs[W];
+            float v[W], s[W];
+            tld_issue<W>(C.tV + C.lanes + C.c0 + c, rv);
+            if (!first) tld_issue<W>(C.tS + C.lanes + C.c0 + c, rs);
+            tld_wait();
+            tld_done<W>(rv, v);
             if (!first) {
-                ld4(C.tS + C.lanes + C.c0 + 4 * kc, w);
+                tld_done<W>(rs, s);
 #pragma unroll
-                for (int i = 0; i < 4; i++) v[i] += w[i];
+                for (int i = 0; i < W; i++) v[i] += s[i];
             }
-            st4(C.tS + C.lanes + C.c0 + 4 * kc, v);
-        }
+            tst<W>(C.tS + C.lanes + C.c0 + c, v);
+        };
+#pragma unroll
+        for (int c = 0; c + 8 <= NQ; c += 8) batch(std::integral_constant<int, 8>{}, c);
+        if constexpr (NQ % 8 != 0) batch(std::integral_constant<int, 4>{}, NQ - 4);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         first = false;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -470,52 +498,46 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
             const int i1 = p0 + C.nchunk * TC_BP + p;
             nx = gxp[i1]; ny = gyp[i1]; nz = gzp[i1]; nw = gwp[i1];
         }
-        const unsigned long long mask = bmask[2 * blk];
-        if (mask == 0ull) continue;  // every AO below the screen: rho under the XC cutoff everywhere
+        const unsigned long long amask = bmask[2 * blk];
+        if (amask == 0ull) continue;  // every AO below the screen: rho under the XC cutoff everywhere
         any_block = true;
-        if (own0 != shf_owner) {  // R_owner - C for the block's (at most two) owners
+        if (own0 != atf_owner) {  // R_owner - R_A for the block's (at most two) owners
             __syncthreads();
-            for (int i = t; i < 2 * C.nsh; i += TC_THREADS) {
-                const int hh = i / C.nsh, s = i % C.nsh;
-                const int A = min(own0 + hh, md.natom - 1);
-                const double *ra = b.axyz + (md.atom0 + A) * 3, *rc = b.sh_xyz + (md.sh0 + s) * 3;
-                *(float4 *)(shf_w + s * 8 + hh * 4) =
+            for (int i = t; i < 2 * md.natom; i += TC_THREADS) {
+                const int hh = i / md.natom, A = i % md.natom;
+                const int O = min(own0 + hh, md.natom - 1);
+                const double *ra = b.axyz + (md.atom0 + O) * 3, *rc = b.axyz + (md.atom0 + A) * 3;
+                *(float4 *)(atf_w + A * 8 + hh * 4) =
                     make_float4((float)(ra[0] - rc[0]), (float)(ra[1] - rc[1]), (float)(ra[2] - rc[2]), 0.f);
             }
-            shf_owner = own0;
+            atf_owner = own0;
             __syncthreads();
         }
         const int hp = min((p0 + p) / npa, md.natom - 1) - own0;
-        const float *shfp = C.shf + hp * 4;
-        const uint32_t on = __ballot_sync(0xffffffffu, lane < NQ && rawl >= 0 && ((mask >> sl) & 1ull)) & cb.valid;
+        const float *atfp = C.atf + hp * 4;
 
-        // ---- A: radial values g = sum c e^(-a r^2), g' = sum -2ac e^(-a r^2) of the thread's columns
-        float gj[NQ], gpj[NQ];
-        {
-            float e0 = 0.f, e1 = 0.f, e2 = 0.f, cg = 0.f, cgp = 0.f;
+        // ---- A: radial values of the thread's columns, unit by unit
+        float g[NQ], gp[NQ];
 #pragma unroll
-            for (int j = 0; j < NQ; j++) {
-                if (TC_FRESH(j)) {
-                    const int sh = TC_SHELL(j);
-                    const float4 xa = *(const float4 *)(C.shx + sh * TC_SHX);
-                    const float4 xb = *(const float4 *)(C.shx + sh * TC_SHX + 4);
-                    const float xc9 = C.shx[sh * TC_SHX + 8];
-                    const bool share = j > 0 && ((cb.share >> j) & 1u) && TC_ON(j > 0 ? j - 1 : 0);
-                    if (!share) {
-                        const float4 dl = *(const float4 *)(shfp + sh * 8);
-                        const float dx = dl.x + px, dy = dl.y + py, dz = dl.z + pz;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        e0 = __expf(-xa.x * r2);
-                        e1 = __expf(-xa.y * r2);
-                        e2 = __expf(-xa.z * r2);
-                    }
-                    cg = xa.w * e0 + xb.x * e1 + xb.y * e2;
-                    cgp = xb.z * e0 + xb.w * e1 + xc9 * e2;
+        for (int k = 0; k < U; k++) {
+            const int j = 5 * k;
+            if (uw[k] >> 31) {
+                const uint32_t A = uw[k] & 63u;
+                if ((amask >> A) & 1ull) {
+                    tc_heavy(C.atx, atfp, A, px, py, pz, g + j, gp + j);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 5; r++) g[j + r] = gp[j + r] = 0.f;
                 }
-                gj[j] = TC_ON(j) ? cg : 0.f;
-                gpj[j] = TC_ON(j) ? cgp : 0.f;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 5; r++)
+                    tc_light(C.atx, atfp, (uw[k] >> (6 * r)) & 63u, amask, px, py, pz, g[j + r], gp[j + r]);
             }
         }
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            tc_light(C.atx, atfp, (rw >> (6 * r)) & 63u, amask, px, py, pz, g[5 * U + r], gp[5 * U + r]);
         // ---- B: the previous block's V'
         if (pending) {
             if (!drain()) {
@@ -525,31 +547,27 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
             pending = false;
         }
         // ---- C: Phi (hi, lo) into the [point][AO] tile
-        {
-            float dx = 0.f, dy = 0.f, dz = 0.f;
 #pragma unroll
-            for (int kc = 0; kc < NQ / 4; kc++) {
-                float v[4];
+        for (int kc = 0; kc < NQ / 4; kc++) {
+            float v[4];
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const int j = kc * 4 + i;
-                    if (TC_FRESH(j)) {
-                        const float4 dl = *(const float4 *)(shfp + TC_SHELL(j) * 8);
-                        dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
-                    }
-                    const int c = TC_COMP(j);
-                    const float dc = c == 1 ? dx : (c == 2 ? dy : dz);
-                    v[i] = c == 0 ? gj[j] : dc * gj[j];  // gj is 0 in screened columns
+            for (int i = 0; i < 4; i++) {
+                const int j = kc * 4 + i, k = j / 5, r = j % 5;
+                if (j < 5 * U && r >= 2) {  // a heavy unit's p column: d_c g_2p
+                    const float dc = r == 2 ? g[5 * k + 3] : (r == 3 ? g[5 * k + 4] : gp[5 * k + 3]);
+                    v[i] = (uw[k] >> 31) ? dc * g[5 * k + 2] : g[j];
+                } else {
+                    v[i] = g[j];
                 }
-                float4 hi, lo;
-                tc::split4(v, hi, lo);
-                *(float4 *)(C.sm + C.L.phi_hi + phi_base + kc * 128) = hi;
-                *(float4 *)(C.sm + C.L.phi_lo + phi_base + kc * 128) = lo;
             }
+            float4 hi, lo;
+            tc::split4(v, hi, lo);
+            *(float4 *)(C.sm + C.L.phi_hi + phi_base + kc * 128) = hi;
+            *(float4 *)(C.sm + C.L.phi_lo + phi_base + kc * 128) = lo;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        float Tv[NQ];  // FINAL: this thread's T columns from the CUDA cores
+        float Tv[NQ];  // this thread's T columns
         if constexpr (!FINAL) {
             if (t == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -557,9 +575,11 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
                     const uint32_t ka = 2u * s * 128u;
                     const uint64_t ah = tc::sdesc(C.su + C.L.phi_hi + ka, 128, C.sg);
                     const uint64_t al = tc::sdesc(C.su + C.L.phi_lo + ka, 128, C.sg);
-                    const uint64_t bh = tc::sdesc(C.su + C.L.D_hi + ka, 128, C.sg);  // D_lo follows D_hi
-                    tc::mma(C.tT, ah, bh, C.id2, s > 0);  // [Phi_hi D_hi | Phi_hi D_lo]
-                    tc::mma(C.tT, al, bh, C.id, 1);       // + Phi_lo D_hi into the first half
+                    const uint64_t bh = tc::sdesc(C.su + C.L.D_hi + ka, 128, C.sg);
+                    const uint64_t bl = tc::sdesc(C.su + C.L.D_lo + ka, 128, C.sg);
+                    tc::mma(C.tT, ah, bh, C.id, s > 0);  // Phi_hi D_hi
+                    tc::mma(C.tT, ah, bl, C.id, 1);      // + Phi_hi D_lo
+                    tc::mma(C.tT, al, bh, C.id, 1);      // + Phi_lo D_hi
                 }
                 tc::commit(C.bar1);
             }
@@ -572,6 +592,7 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
             }
             ph1 ^= 1;
             in1 = false;
+            tld<NQ>(C.tT + C.lanes + C.c0, Tv);
         } else {
             // T on the CUDA cores: this point's row of Phi (hi + lo is the FP32
             // value) against D's rows, the thread's column quarter
@@ -598,52 +619,38 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
             }
             __syncthreads();  // every thread's reads of the Phi tile precede the partials written over it
         }
-        // ---- E: this thread's share of rho and grad rho, shell by shell:
-        // with u = sum_c T_c d_c (p shell; u = T for an s shell) and Tv = (T_x, T_y, T_z),
-        // rho += g u and grad rho += 2 (g' u d + g Tv)
+        // ---- E: this thread's share of rho and grad rho / 2:
+        // s column: rho += g T, grad += g' T d; heavy unit with u = T_p . d:
+        // rho += g_2p u, grad += g_2p' u d + g_2p T_p
         {
             float rho = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-            float cg = 0.f, cgp = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, u = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+            auto light = [&](int j, uint32_t A) {
+                const float4 dl = *(const float4 *)(atfp + A * 8);
+                const float s = gp[j] * Tv[j];
+                rho += g[j] * Tv[j];
+                rx += s * (dl.x + px);
+                ry += s * (dl.y + py);
+                rz += s * (dl.z + pz);
+            };
 #pragma unroll
-            for (int j = 0; j < NQ; j++) {
-                if constexpr (!FINAL) {
-                    if ((j & 3) == 0) {  // T four columns at a time: the two halves of the accumulator
-                        float t2[4];
-                        ld4(C.tT + C.lanes + C.c0 + j, Tv + j);
-                        ld4(C.tT + C.lanes + C.np + C.c0 + j, t2);
+            for (int k = 0; k < U; k++) {
+                const int j = 5 * k;
+                if (uw[k] >> 31) {
+                    const float dx = g[j + 3], dy = g[j + 4], dz = gp[j + 3];
+                    const float t2 = Tv[j + 2], t3 = Tv[j + 3], t4 = Tv[j + 4];
+                    const float u = dx * t2 + dy * t3 + dz * t4;
+                    rho += g[j] * Tv[j] + g[j + 1] * Tv[j + 1] + g[j + 2] * u;
+                    const float s = gp[j] * Tv[j] + gp[j + 1] * Tv[j + 1] + gp[j + 2] * u;
+                    rx += s * dx + g[j + 2] * t2;
+                    ry += s * dy + g[j + 2] * t3;
+                    rz += s * dz + g[j + 2] * t4;
+                } else {
 #pragma unroll
-                        for (int i = 0; i < 4; i++) Tv[j + i] += t2[i];
-                    }
-                }
-                if (TC_FRESH(j)) {
-                    rho += cg * u;  // the previous shell (zeros before the first)
-                    rx += cgp * u * dx + cg * tx;
-                    ry += cgp * u * dy + cg * ty;
-                    rz += cgp * u * dz + cg * tz;
-                    cg = gj[j];
-                    cgp = gpj[j];
-                    const float4 dl = *(const float4 *)(shfp + TC_SHELL(j) * 8);
-                    dx = dl.x + px; dy = dl.y + py; dz = dl.z + pz;
-                    u = tx = ty = tz = 0.f;
-                }
-                if (TC_ON(j)) {
-                    const float tv = Tv[j];
-                    const int c = TC_COMP(j);
-                    if (c == 0) {
-                        u = tv;
-                    } else if (c == 1) {
-                        u += tv * dx; tx = tv;
-                    } else if (c == 2) {
-                        u += tv * dy; ty = tv;
-                    } else {
-                        u += tv * dz; tz = tv;
-                    }
+                    for (int r = 0; r < 5; r++) light(j + r, (uw[k] >> (6 * r)) & 63u);
                 }
             }
-            rho += cg * u;
-            rx += cgp * u * dx + cg * tx;
-            ry += cgp * u * dy + cg * ty;
-            rz += cgp * u * dz + cg * tz;
+#pragma unroll
+            for (int r = 0; r < R; r++) light(5 * U + r, (rw >> (6 * r)) & 63u);
             C.part[(C.q4 * 4 + 0) * TC_BP + p] = rho;
             C.part[(C.q4 * 4 + 1) * TC_BP + p] = rx;
             C.part[(C.q4 * 4 + 2) * TC_BP + p] = ry;
@@ -675,15 +682,14 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
             }
         }
         __syncthreads();
-        // ---- G: Phi^T and X = a phi + b . grad phi with a = w v_rho / 2, b = 2 w v_sigma
-        // grad rho: s shell X = a g + g' (b . d); p component c: X_c = d_c (a g + g' (b . d)) + b_c g
+        // ---- G: Phi^T and X = a phi + b . grad phi with a = w v_rho / 2, b = 2 w v_sigma grad rho
         {
             const float vr = C.xcp[p] + C.xcp[2 * TC_BP + p] + C.xcp[4 * TC_BP + p];
             const float vs2 = 2.f * pw * (C.xcp[TC_BP + p] + C.xcp[5 * TC_BP + p]);
             const float a = 0.5f * pw * vr;
             const float bx = vs2 * C.grd[p], by = vs2 * C.grd[TC_BP + p], bz = vs2 * C.grd[2 * TC_BP + p];
-            if (C.c0 & 4) tc_write_gemm2<NQ, 4>(C, cb, on, gj, gpj, shfp, px, py, pz, a, bx, by, bz);
-            else tc_write_gemm2<NQ, 0>(C, cb, on, gj, gpj, shfp, px, py, pz, a, bx, by, bz);
+            if (C.c0 & 4) tc_write_gemm2<NQ, 4>(C, uw, rw, g, gp, atfp, px, py, pz, a, bx, by, bz);
+            else tc_write_gemm2<NQ, 0>(C, uw, rw, g, gp, atfp, px, py, pz, a, bx, by, bz);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -693,9 +699,10 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
             for (int k = 0; k < TC_BP / 8; k++) {
                 const uint32_t ko = (uint32_t)(k >> 2) * 1024u + (uint32_t)(k & 3) * 32u;
                 const uint64_t ah = tc::sdesc_sw128(C.su + C.L.pt_hi + ko), al = tc::sdesc_sw128(C.su + C.L.pt_lo + ko);
-                const uint64_t bh = tc::sdesc_sw128(C.su + C.L.x_hi + ko);  // X_lo follows X_hi
-                tc::mma(C.tV, ah, bh, C.id2, k > 0);  // [Phi_hi^T X_hi | Phi_hi^T X_lo]
-                tc::mma(C.tV, al, bh, C.id, 1);       // + Phi_lo^T X_hi into the first half
+                const uint64_t bh = tc::sdesc_sw128(C.su + C.L.x_hi + ko), bl = tc::sdesc_sw128(C.su + C.L.x_lo + ko);
+                tc::mma(C.tV, ah, bh, C.id, k > 0);  // Phi_hi^T X_hi
+                tc::mma(C.tV, ah, bl, C.id, 1);      // + Phi_hi^T X_lo
+                tc::mma(C.tV, al, bh, C.id, 1);      // + Phi_lo^T X_hi
             }
             tc::commit(C.bar2);
         }
@@ -707,20 +714,19 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
     }
     if (failed && t == 0) *C.s_fail = 1;
     __syncthreads();
-    // ---- flush V' (row mu = this thread's lane row, columns of its quarter) and E_xc
+    // ---- flush V' (row mu = this thread's lane row, columns of its quarter)
+    // into the molecule's AO order, and E_xc
     if (!*C.s_fail && any_block && !first) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int mu = (C.warp & 3) * 32 + lane;
+        const int Pm = mu < C.np ? C.perm[mu] : -1;
         Fx *gV = b.accx + md.acc0 + 2 * C.n * C.n;  // mixed path: fixed point in every pass
+        float v[NQ];
+        tld<NQ>(C.tS + C.lanes + C.c0, v);
 #pragma unroll
-        for (int kc = 0; kc < NQ / 4; kc++) {
-            float v[4];
-            ld4(C.tS + C.lanes + C.c0 + 4 * kc, v);
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const int nu = C.c0 + 4 * kc + i;
-                if (mu < C.n && nu < C.n && v[i] != 0.f) acc_add(&gV[mu * C.n + nu], (TA)v[i]);
-            }
+        for (int j = 0; j < NQ; j++) {
+            const int Pn = C.perm[C.c0 + j];
+            if (Pm >= 0 && Pn >= 0 && v[j] != 0.f) acc_add(&gV[Pm * C.n + Pn], (TA)v[j]);
         }
     }
     for (int o = 16; o > 0; o >>= 1) exc += __shfl_xor_sync(0xffffffffu, exc, o);
@@ -738,9 +744,9 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C) {
 // tensor cores' truncating accumulation would bias rho and E_xc), V_xc stays
 // on the tensor cores (it only moves the final eigenvalues, at ~1e-7), and
 // V_xc is accumulated in 64-bit fixed point like every mixed pass.
-// One instantiation per NQ (columns per thread = padded basis / 4), launched
-// over the molecules of that size only (list), so that each gets its own
-// register allocation and shared-memory size.
+// One instantiation per NQ (columns per thread quarter), launched over the
+// molecules of that class only (list), so that each gets its own register
+// allocation and shared-memory size.
 template <typename TA, bool FINAL, int NQ>
 __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, int nchunk, int mode, const int *list) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -757,48 +763,69 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     C.chunk = chunk;
     C.nchunk = nchunk;
     C.n = md.nbf;
-    C.nsh = md.nsh;
-    C.np = (C.n + 15) & ~15;
-    const int nq = C.np / 4;  // AO columns per thread quarter (multiple of 4)
-    C.L = tc_layout(C.np, C.nsh);
+    C.np = 4 * NQ;
+    C.L = tc_layout(C.np);
     C.t = threadIdx.x;
     C.lane = C.t & 31;
     C.warp = C.t >> 5;
     C.p = C.t & (TC_BP - 1);
     C.q4 = C.t >> 7;
-    C.c0 = C.q4 * nq;
+    C.c0 = C.q4 * NQ;
     C.sm = smem;
     C.part = (float *)(smem + C.L.part);
     C.xcp = (float *)(smem + C.L.xcp);
     C.grd = (float *)(smem + C.L.grd);
-    float *shx = (float *)(smem + C.L.shx);
-    C.shx = shx;
-    C.shf = (float *)(smem + C.L.shf);
-    int *col = (int *)(smem + C.L.col);
-    C.col = col;
+    float *atx = (float *)(smem + C.L.atx), *atf = (float *)(smem + C.L.atf);
+    int *perm = (int *)(smem + C.L.perm);
+    C.atx = atx;
+    C.atf = atf;
+    C.perm = perm;
     C.sg = (uint32_t)(C.np / 4) * 128u;  // bytes per 8-row group of the unswizzled tiles
     C.bar1 = &bar1;
     C.bar2 = &bar2;
     C.s_fail = &s_fail;
-    const int n = C.n, nsh = C.nsh, np = C.np, t = C.t;
+    const int n = C.n, nsh = md.nsh, np = C.np, t = C.t;
+    const int *plan = b.tc_plan + (long long)m * RKS_TC_PLAN;
 
-    // ---- per-CTA constants: D (hi, lo) as GEMM1's B, or plain FP32 D[mu][nu]
-    // for the CUDA-core contraction of the final step; shells; column codes
+    // ---- per-CTA constants: the column plan, the atom tables, and D in the
+    // kernel's column order (hi, lo) as GEMM1's B, or plain FP32 D for the
+    // CUDA-core contraction of the final step
+    for (int i = t; i < TC_NAT * TC_ATX; i += blockDim.x) atx[i] = 0.f;
+    for (int i = t; i < TC_NAT * 8; i += blockDim.x) atf[i] = 0.f;
+    for (int c = t; c < np; c += blockDim.x) perm[c] = plan[20 + c];
+    __syncthreads();
+    for (int s = t; s < nsh; s += blockDim.x) {
+        // shells are in packing order (s shells, then p shells, atom order
+        // inside): an s shell right after an s shell of the same atom is its 2s
+        const int g = md.sh0 + s, A = b.sh_atom[g];
+        const int slot = b.sh_l[g] ? 2 : ((s > 0 && b.sh_atom[g - 1] == A && b.sh_l[g - 1] == 0) ? 1 : 0);
+        // float4 offsets in the atom's entry: 1s a, c, -2ac at 0, 4, 8; 2s at
+        // 12, 16, 20; 2p c, -2ac at 24, 28 (its exponents are the 2s ones)
+        float *e = atx + A * TC_ATX;
+        const int oa = slot == 0 ? 0 : 12, oc = slot == 0 ? 4 : (slot == 1 ? 16 : 24), om = oc + 4;
+        for (int k = 0; k < 3; k++) {
+            const double a = b.sh_ex[g * 3 + k], c = b.sh_co[g * 3 + k];
+            if (slot < 2) e[oa + k] = (float)a;
+            e[oc + k] = (float)c;
+            e[om + k] = (float)(-2.0 * a * c);
+        }
+    }
     const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
     if constexpr (FINAL) {
         float *Dp = (float *)(smem + C.L.D_hi);
         for (int i = t; i < np * np; i += blockDim.x) {
-            const int row = i / np, cc = i % np;
-            Dp[i] = (row < n && cc < n) ? (float)D[row * n + cc] : 0.f;
+            const int pr = perm[i / np], pc = perm[i % np];
+            Dp[i] = (pr >= 0 && pc >= 0) ? (float)D[pr * n + pc] : 0.f;
         }
     } else {
         for (int i = t; i < np * np / 4; i += blockDim.x) {
             const int row = i / (np / 4), kc = i % (np / 4);
+            const int pr = perm[row];
             float v[4];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const int k = kc * 4 + j;
-                v[j] = (row < n && k < n) ? (float)D[row * n + k] : 0.f;
+                const int pc = perm[kc * 4 + j];
+                v[j] = (pr >= 0 && pc >= 0) ? (float)D[pr * n + pc] : 0.f;
             }
             float4 hi, lo;
             tc::split4(v, hi, lo);
@@ -806,36 +833,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
             *(float4 *)(smem + C.L.D_lo + tc::coff(row, kc * 4, C.sg)) = lo;
         }
     }
-    for (int s = t; s < nsh; s += blockDim.x) {
-        const int g = md.sh0 + s;
-        for (int k = 0; k < 3; k++) {
-            const double a = b.sh_ex[g * 3 + k], c = b.sh_co[g * 3 + k];
-            shx[s * TC_SHX + k] = (float)a;
-            shx[s * TC_SHX + 3 + k] = (float)c;
-            shx[s * TC_SHX + 6 + k] = (float)(-2.0 * a * c);
-        }
-        shx[s * TC_SHX + 9] = shx[s * TC_SHX + 10] = shx[s * TC_SHX + 11] = 0.f;
-    }
-    for (int mu = t; mu < np; mu += blockDim.x) col[mu] = -1;
-    __syncthreads();
-    for (int s = t; s < nsh; s += blockDim.x) {
-        const int g = md.sh0 + s;
-        const int l = b.sh_l[g], a0 = b.sh_ao0[g];
-        // an atom's 2p shell follows its 2s shell in AO order with the same exponents
-        bool share = false;
-        if (l == 1 && a0 > 0) {
-            for (int s2 = 0; s2 < nsh; s2++) {
-                const int h2 = md.sh0 + s2;
-                if (b.sh_l[h2] == 0 && b.sh_ao0[h2] == a0 - 1 && b.sh_atom[h2] == b.sh_atom[g] &&
-                    b.sh_ex[h2 * 3] == b.sh_ex[g * 3] && b.sh_ex[h2 * 3 + 1] == b.sh_ex[g * 3 + 1] &&
-                    b.sh_ex[h2 * 3 + 2] == b.sh_ex[g * 3 + 2])
-                    share = true;
-            }
-        }
-        if (l == 0) col[a0] = s << 2;
-        else
-            for (int c = 0; c < 3; c++) col[a0 + c] = (s << 2) | (c + 1) | (share && c == 0 ? 0x100 : 0);
-    }
+    constexpr int U = NQ / 5;
+    uint32_t uw[U > 0 ? U : 1];
+#pragma unroll
+    for (int k = 0; k < U; k++) uw[k] = (uint32_t)plan[C.q4 * 5 + k];
+    const uint32_t rw = (uint32_t)plan[C.q4 * 5 + 4];
     if (C.warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_slot)),
                      "r"(TC_TMEM_COLS)
@@ -857,21 +859,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     C.tS = tmem + TC_SCOL;
     C.lanes = (uint32_t)((C.warp & 3) * 32) << 16;  // this warp's TMEM lane quarter
     C.id = tc::idesc(128, np);
-    C.id2 = tc::idesc(128, 2 * np);
     C.su = tc::smem_u32(smem);
-    (void)nq;  // == NQ: the host launches each molecule with its own size class
-    tc_loop<TA, FINAL, NQ>(b, C);
+    tc_loop<TA, FINAL, NQ>(b, C, uw, rw);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (C.warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
 }
 
-
 template <typename TA, bool FINAL, int NQ>
-static void launch_tc_class(const DevBatch &b, int nchunk, int mode, int max_nsh, const int *list, int count,
-                            cudaStream_t s) {
-    const size_t sm = tc_layout(4 * NQ, max_nsh).total;
+static void launch_tc_class(const DevBatch &b, int nchunk, int mode, const int *list, int count, cudaStream_t s) {
+    const size_t sm = tc_layout(4 * NQ).total;
     cudaFuncSetAttribute(grid_xc_tc_kernel<TA, FINAL, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     grid_xc_tc_kernel<TA, FINAL, NQ><<<dim3(nchunk, count), TC_THREADS, sm, s>>>(b, nchunk, mode, list);
 }
@@ -879,11 +877,11 @@ static void launch_tc_class(const DevBatch &b, int nchunk, int mode, int max_nsh
 template <typename TA, bool FINAL>
 static void launch_tc_all(const DevBatch &b, int nchunk, int mode, const TcClasses &cl, cudaStream_t s) {
     const int *l = cl.list;
-    if (cl.count[0]) launch_tc_class<TA, FINAL, 4>(b, nchunk, mode, cl.max_nsh[0], l + cl.off[0], cl.count[0], s);
-    if (cl.count[1]) launch_tc_class<TA, FINAL, 8>(b, nchunk, mode, cl.max_nsh[1], l + cl.off[1], cl.count[1], s);
-    if (cl.count[2]) launch_tc_class<TA, FINAL, 12>(b, nchunk, mode, cl.max_nsh[2], l + cl.off[2], cl.count[2], s);
-    if (cl.count[3]) launch_tc_class<TA, FINAL, 16>(b, nchunk, mode, cl.max_nsh[3], l + cl.off[3], cl.count[3], s);
-    if (cl.count[4]) launch_tc_class<TA, FINAL, 20>(b, nchunk, mode, cl.max_nsh[4], l + cl.off[4], cl.count[4], s);
+    if (cl.count[0]) launch_tc_class<TA, FINAL, 4>(b, nchunk, mode, l + cl.off[0], cl.count[0], s);
+    if (cl.count[1]) launch_tc_class<TA, FINAL, 8>(b, nchunk, mode, l + cl.off[1], cl.count[1], s);
+    if (cl.count[2]) launch_tc_class<TA, FINAL, 12>(b, nchunk, mode, l + cl.off[2], cl.count[2], s);
+    if (cl.count[3]) launch_tc_class<TA, FINAL, 16>(b, nchunk, mode, l + cl.off[3], cl.count[3], s);
+    if (cl.count[4]) launch_tc_class<TA, FINAL, 20>(b, nchunk, mode, l + cl.off[4], cl.count[4], s);
 }
 
 void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, const TcClasses &cl, cudaStream_t s) {

@@ -30,21 +30,21 @@ void launch_fix_list(const DevBatch &b, cudaStream_t s);
 void launch_jk_fix(const DevBatch &b, int mode, cudaStream_t s, const int *mlist = nullptr, int nlist = 0,
                    int nchunk = 8);
 // AO + density + B3LYP + V_xc on the grid; acc_fp64 and mode as above.
-// skip_tc: leave out the molecules the tensor-core kernel takes (grid_tc_fits).
+// skip_tc: leave out the molecules the tensor-core kernel takes (MolDesc::tcq).
 void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int skip_tc, int max_nbf, int max_nsh,
                     cudaStream_t s);
-// Per-block shell significance masks of the tensor-core grid kernel (setup,
+// Per-block atom significance masks of the tensor-core grid kernel (setup,
 // after the grid is built; molecules the kernel does not take are skipped).
 void launch_grid_masks(const DevBatch &b, long long nblk_total, const int *blk_mol, cudaStream_t s);
 // Tensor-core (tcgen05, 3xTF32) version for the mixed path; takes the
-// molecules with grid_tc_fits() and skips the others.  acc_fp64 = 1 is the
-// final step: density contraction on the CUDA cores (round-to-nearest sums).
-// Molecules the tensor-core kernel takes, by size class (padded basis 16, 32,
-// 48, 64, 80): device list of molecule indices, class offsets and counts,
-// largest shell count per class.
+// molecules with a column plan (MolDesc::tcq) and skips the others.
+// acc_fp64 = 1 is the final step: density contraction on the CUDA cores
+// (round-to-nearest sums).  Molecules the kernel takes, by column class
+// (NQ = 4, 8, 12, 16, 20): device list of molecule indices, class offsets and
+// counts.
 struct TcClasses {
     const int *list;
-    int off[5], count[5], max_nsh[5];
+    int off[5], count[5];
 };
 void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, const TcClasses &cl, cudaStream_t s);
 // Per-molecule FP64 SCF stages.
