@@ -10,15 +10,19 @@
 //
 // One thread block owns one molecule's share of grid blocks (grid (nchunk,
 // nmol)); per sub-block of BP points it evaluates every AO into shared memory,
-// forms rho (G threads per point, shuffle-reduced), runs the functional, builds
-// X, and accumulates V' in a per-thread register tile (16 x 16 threads, TILE x
-// TILE entries each).  V' and E_xc leave the block once, at the end.
+// forms rho (G threads per point, shuffle-reduced), runs the functional in
+// three parts on three full warps (lane = point), builds X, and accumulates V'
+// in a per-thread register tile (16 x 16 threads, TILE x TILE entries each).
+// V' and E_xc leave the block once, at the end.  TILE and NV (the density
+// step's registers per thread) are sized for the launch's largest basis: on
+// the FP64 path every issued DFMA costs the same whether or not its result is
+// used (the pipe, not the issue, bounds the kernel).
 #include "common.cuh"
 #include "kernels.h"
 #include "xc.cuh"
 #include "boys.cuh"
 
-template <typename T, typename TA, int BP, int TILE>
+template <typename T, typename TA, int BP, int TILE, int NV>
 __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk, int mode, int skip_tc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = blockIdx.y, chunk = blockIdx.x;
@@ -32,7 +36,9 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
     T *Xs = phi + 4 * n * BP;              // [BP][XS]
     T *pt = Xs + BP * XS;                  // [4][BP] x y z w
     T *cf = pt + 4 * BP;                   // [4][BP] coefficients
-    T *shd = cf + 4 * BP;                  // [nsh][8]: x y z e0 e1 e2 (c's below)
+    T *rr = cf + 4 * BP;                   // [4][BP] rho, grad rho
+    T *xv = rr + 4 * BP;                   // [3][2][BP] v_rho, v_sigma per functional part
+    T *shd = xv + 6 * BP;                  // [nsh][8]: x y z e0 e1 e2 (c's below)
     T *shc = shd + nsh * 8;                // [nsh][4]: c0 c1 c2 -
     T *dlt = shc + nsh * 4;                // [2][nsh][3]: R_owner - C_shell for the sub-block's owners
     int *shi = (int *)(dlt + 6 * nsh);     // [nsh][2]: l, ao0
@@ -91,9 +97,12 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
             T g = 0, gp = 0;
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                const T e = shc[s * 4 + k] * xc::exp_(-shd[s * 8 + 3 + k] * r2);
-                g += e;
-                gp -= (T)2 * shd[s * 8 + 3 + k] * e;
+                const T x = shd[s * 8 + 3 + k] * r2;
+                if (x < (T)40) {  // e^-40 ~ 4e-18: below anything the sums can see
+                    const T e = shc[s * 4 + k] * xc::exp_(-x);
+                    g += e;
+                    gp -= (T)2 * shd[s * 8 + 3 + k] * e;
+                }
             }
             const int l = shi[s * 2], mu = shi[s * 2 + 1];
             if (l == 0) {
@@ -117,7 +126,6 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
         // NV columns nu of T = Phi D, summed in NV independent registers (the
         // FP64 pipe needs the independent chains to stay busy)
         {
-            constexpr int NV = (RKS_NBF_CAP + G - 1) / G;
             const int p = t / G, gg = t % G;
             const int nper = (n + G - 1) / G, nu0 = gg * nper;
             T tv[NV];
@@ -149,16 +157,36 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
                 rz += __shfl_xor_sync(0xffffffffu, rz, o);
             }
             if (gg == 0) {
-                rx *= (T)2; ry *= (T)2; rz *= (T)2;
+                rr[p] = rho;
+                rr[BP + p] = (T)2 * rx;
+                rr[2 * BP + p] = (T)2 * ry;
+                rr[3 * BP + p] = (T)2 * rz;
+            }
+        }
+        __syncthreads();
+        // ---- the functional: part (exchange, VWN5, LYP) = warp, point = lane
+        if (t < 96) {
+            const int part = t >> 5;
+            for (int p = t & 31; p < BP; p += 32) {
                 const T w = pt[3 * BP + p];
                 T e = 0, vr = 0, vs = 0;
-                if (w != (T)0) xc::b3lyp<T>(rho, rx * rx + ry * ry + rz * rz, e, vr, vs);
+                if (w != (T)0) {
+                    const T gx = rr[BP + p], gy = rr[2 * BP + p], gz = rr[3 * BP + p];
+                    xc::b3lyp_part<T>(part, rr[p], gx * gx + gy * gy + gz * gz, e, vr, vs);
+                }
                 exc += (double)w * (double)e;
-                cf[p] = (T)0.5 * w * vr;
-                cf[BP + p] = (T)2 * w * vs * rx;
-                cf[2 * BP + p] = (T)2 * w * vs * ry;
-                cf[3 * BP + p] = (T)2 * w * vs * rz;
+                xv[(part * 2) * BP + p] = vr;
+                xv[(part * 2 + 1) * BP + p] = vs;
             }
+        }
+        __syncthreads();
+        for (int p = t; p < BP; p += blockDim.x) {
+            const T w = pt[3 * BP + p];
+            const T vr = xv[p] + xv[2 * BP + p] + xv[4 * BP + p], vs = xv[BP + p] + xv[5 * BP + p];
+            cf[p] = (T)0.5 * w * vr;
+            cf[BP + p] = (T)2 * w * vs * rr[BP + p];
+            cf[2 * BP + p] = (T)2 * w * vs * rr[2 * BP + p];
+            cf[3 * BP + p] = (T)2 * w * vs * rr[3 * BP + p];
         }
         __syncthreads();
         // ---- X[p][nu]
@@ -215,20 +243,31 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
     if ((t & 31) == 0 && exc != 0.0) exc_add(&b.st[m].exc_fx, exc);
 }
 
-template <typename T, typename TA, int BP, int TILE>
-static void launch_gx(const DevBatch &b, int nchunk, int mode, int skip_tc, int max_nbf, int max_nsh, cudaStream_t s) {
+template <typename T, typename TA, int BP, int TILE, int NV>
+static void launch_gx1(const DevBatch &b, int nchunk, int mode, int skip_tc, int max_nbf, int max_nsh, cudaStream_t s) {
     const int n = max_nbf, XS = n | 1;
-    size_t sm = sizeof(T) * ((size_t)n * n + 4ull * n * BP + (size_t)BP * XS + 8ull * BP + 18ull * max_nsh) +
+    size_t sm = sizeof(T) * ((size_t)n * n + 4ull * n * BP + (size_t)BP * XS + 18ull * BP + 18ull * max_nsh) +
                 sizeof(int) * 2ull * max_nsh + 64;
-    cudaFuncSetAttribute(grid_xc_kernel<T, TA, BP, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    grid_xc_kernel<T, TA, BP, TILE><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode, skip_tc);
+    cudaFuncSetAttribute(grid_xc_kernel<T, TA, BP, TILE, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    grid_xc_kernel<T, TA, BP, TILE, NV><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode, skip_tc);
+}
+
+// V' tile and density registers sized for the largest basis of the launch
+// (16 TILE >= nbf; NV >= nbf / G with G = 256 / BP threads per point)
+template <typename T, typename TA, int BP>
+static void launch_gx(const DevBatch &b, int nchunk, int mode, int skip_tc, int max_nbf, int max_nsh, cudaStream_t s) {
+    constexpr int G = 256 / BP;
+    static_assert(RKS_NBF_CAP <= 96, "tile classes cover nbf <= 96");
+    if (max_nbf <= 64) launch_gx1<T, TA, BP, 4, (64 + G - 1) / G>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
+    else if (max_nbf <= 80) launch_gx1<T, TA, BP, 5, (80 + G - 1) / G>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
+    else launch_gx1<T, TA, BP, 6, (96 + G - 1) / G>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
 }
 
 void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int skip_tc, int max_nbf, int max_nsh,
                     cudaStream_t s) {
-    if (b.precision == 0) launch_gx<double, double, 32, 6>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
-    else if (acc_fp64) launch_gx<float, double, 64, 6>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
-    else launch_gx<float, float, 64, 6>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
+    if (b.precision == 0) launch_gx<double, double, 32>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
+    else if (acc_fp64) launch_gx<float, double, 64>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
+    else launch_gx<float, float, 64>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
 }
 
 // --------------------------------------------------------- unit entry

@@ -455,6 +455,13 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint3
     const int npa = b.n_rad * b.n_theta * b.n_phi;
     float nx = gxp[C.chunk * TC_BP + p], ny = gyp[C.chunk * TC_BP + p], nz = gzp[C.chunk * TC_BP + p];
     float nw = gwp[C.chunk * TC_BP + p];
+    // the MMA operand descriptors at K step 0 (the tiles do not move); a K
+    // step adds its byte offset / 16 to the start-address field, which cannot
+    // carry out of its 14 bits (every shared-memory address is below 2^18)
+    const uint64_t g1ah = tc::sdesc(C.su + C.L.phi_hi, 128, C.sg), g1al = tc::sdesc(C.su + C.L.phi_lo, 128, C.sg);
+    const uint64_t g1bh = tc::sdesc(C.su + C.L.D_hi, 128, C.sg), g1bl = tc::sdesc(C.su + C.L.D_lo, 128, C.sg);
+    const uint64_t g2ah = tc::sdesc_sw128(C.su + C.L.pt_hi), g2al = tc::sdesc_sw128(C.su + C.L.pt_lo);
+    const uint64_t g2bh = tc::sdesc_sw128(C.su + C.L.x_hi), g2bl = tc::sdesc_sw128(C.su + C.L.x_lo);
     int atf_owner = -1;  // owner atom the atf table was built for
     float *atf_w = const_cast<float *>(C.atf);
 
@@ -462,7 +469,7 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint3
     // round-to-nearest across blocks; the tensor cores' accumulation only
     // spans one block): 8 columns per batch of loads, one wait per batch
     auto drain = [&]() -> bool {
-        const bool ok = __syncthreads_and(tc::wait(C.bar2, ph2));
+        const bool ok = __syncthreads_and(C.warp != 0 || tc::wait(C.bar2, ph2));  // warp 0 polls, the rest block
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) return false;  // still pending: the exit path waits on the same phase
         ph2 ^= 1;
@@ -572,19 +579,15 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint3
             if (t == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int s = 0; s < C.np / 8; s++) {
-                    const uint32_t ka = 2u * s * 128u;
-                    const uint64_t ah = tc::sdesc(C.su + C.L.phi_hi + ka, 128, C.sg);
-                    const uint64_t al = tc::sdesc(C.su + C.L.phi_lo + ka, 128, C.sg);
-                    const uint64_t bh = tc::sdesc(C.su + C.L.D_hi + ka, 128, C.sg);
-                    const uint64_t bl = tc::sdesc(C.su + C.L.D_lo + ka, 128, C.sg);
-                    tc::mma(C.tT, ah, bh, C.id, s > 0);  // Phi_hi D_hi
-                    tc::mma(C.tT, ah, bl, C.id, 1);      // + Phi_hi D_lo
-                    tc::mma(C.tT, al, bh, C.id, 1);      // + Phi_lo D_hi
+                    const uint64_t ka = (uint64_t)s * 16u;  // 2 cores of 128 B, in 16-byte units
+                    tc::mma(C.tT, g1ah + ka, g1bh + ka, C.id, s > 0);  // Phi_hi D_hi
+                    tc::mma(C.tT, g1ah + ka, g1bl + ka, C.id, 1);      // + Phi_hi D_lo
+                    tc::mma(C.tT, g1al + ka, g1bh + ka, C.id, 1);      // + Phi_lo D_hi
                 }
                 tc::commit(C.bar1);
             }
             in1 = true;
-            const bool ok1 = __syncthreads_and(tc::wait(C.bar1, ph1));
+            const bool ok1 = __syncthreads_and(C.warp != 0 || tc::wait(C.bar1, ph1));
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (!ok1) {
                 failed = true;
@@ -697,12 +700,10 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint3
         if (t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int k = 0; k < TC_BP / 8; k++) {
-                const uint32_t ko = (uint32_t)(k >> 2) * 1024u + (uint32_t)(k & 3) * 32u;
-                const uint64_t ah = tc::sdesc_sw128(C.su + C.L.pt_hi + ko), al = tc::sdesc_sw128(C.su + C.L.pt_lo + ko);
-                const uint64_t bh = tc::sdesc_sw128(C.su + C.L.x_hi + ko), bl = tc::sdesc_sw128(C.su + C.L.x_lo + ko);
-                tc::mma(C.tV, ah, bh, C.id, k > 0);  // Phi_hi^T X_hi
-                tc::mma(C.tV, ah, bl, C.id, 1);      // + Phi_hi^T X_lo
-                tc::mma(C.tV, al, bh, C.id, 1);      // + Phi_lo^T X_hi
+                const uint64_t ko = (uint64_t)((k >> 2) * 64 + (k & 3) * 2);  // (k/4) KB + (k%4) 32 B, 16-byte units
+                tc::mma(C.tV, g2ah + ko, g2bh + ko, C.id, k > 0);  // Phi_hi^T X_hi
+                tc::mma(C.tV, g2ah + ko, g2bl + ko, C.id, 1);      // + Phi_hi^T X_lo
+                tc::mma(C.tV, g2al + ko, g2bh + ko, C.id, 1);      // + Phi_lo^T X_hi
             }
             tc::commit(C.bar2);
         }
