@@ -6,8 +6,12 @@
 //   rho_p = sum_n T_pn phi_pn,  grad rho_p = 2 sum_n T_pn grad phi_pn
 //   GEMM2  V' += Phi^T X        (M = 128 AO rows, N = np, K = 128 points)
 // Split products (Ootomo & Yokota 2022): a = a_hi + a_lo with a_hi the TF32
-// rounding of a; a b ~= a_hi b_hi + a_hi b_lo + a_lo b_hi: three MMAs per K
-// step into one FP32 accumulator.
+// rounding of a; a b ~= a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32.
+// The b_lo tile follows the b_hi tile row for row, so a_hi [b_hi | b_lo] is
+// one MMA of N = 2 np into two halves of the accumulator and a_lo b_hi a
+// second one into the first half: two MMAs per K step (an MMA's issue, not
+// its N, sets the pace at these sizes), and the halves are summed when the
+// accumulator is read.
 //
 // Column order.  The kernel works in its own order of the AO basis (the
 // molecule's column plan, built on the host, layout in common.cuh): thread
@@ -31,8 +35,9 @@
 //    32 different banks, without the padding an unswizzled tile would need.
 //    A K step of 8 points is 32 bytes inside an atom.
 //
-// One thread block (512 threads, one per SM) owns 1/nchunk of a molecule's
-// 128-point grid blocks and keeps the running sum of V' in tensor memory.
+// One thread block (512 threads, one per SM) owns a contiguous 1/nchunk of a
+// molecule's 128-point grid blocks and keeps the running sum of V' in tensor
+// memory.
 // Thread t serves point p = t % 128 and the column quarter q4 = t / 128; the
 // radial values g, g' of its columns stay in its registers between phases.
 // Per block:
@@ -61,8 +66,8 @@
 #define TC_BP 128
 #define TC_NPMAX RKS_TC_NPMAX   // padded basis size this kernel handles
 #define TC_TMEM_COLS 512
-#define TC_TCOL 0               // TMEM columns of T (GEMM1, np columns)
-#define TC_VCOL 160             // of V' (GEMM2, one block)
+#define TC_TCOL 0               // TMEM columns of T (GEMM1: two halves of np columns)
+#define TC_VCOL 160             // of V' (GEMM2, one block: two halves of np columns)
 #define TC_SCOL 320             // and of the running sum of V' over the CTA's blocks
 #define TC_SPIN_LIMIT 4000000  // polls before a wait gives up: >= ~40 ms, far above any MMA here
 #define TC_THREADS 512
@@ -340,7 +345,7 @@ struct TcCta {
     float *part, *xcp, *grd;
     uint64_t *bar1, *bar2;
     int *s_fail;
-    uint32_t su, sg, tT, tV, tS, lanes, id;
+    uint32_t su, sg, tT, tV, tS, lanes, id, id2;
     int m, chunk, nchunk, n, np, t, lane, warp, p, q4, c0;
 };
 
@@ -453,15 +458,19 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint3
     const float *gzp = (const float *)b.gz + md.pts0, *gwp = (const float *)b.gw + md.pts0;
     const unsigned long long *bmask = b.blk_mask + 2 * (md.pts0 / TC_BP) + (FINAL ? 1 : 0);
     const int npa = b.n_rad * b.n_theta * b.n_phi;
-    float nx = gxp[C.chunk * TC_BP + p], ny = gyp[C.chunk * TC_BP + p], nz = gzp[C.chunk * TC_BP + p];
-    float nw = gwp[C.chunk * TC_BP + p];
+    // the CTA's blocks are one contiguous run (the owner-atom table changes
+    // about once per atom's worth of blocks, not every few blocks)
+    const int blk0 = (int)((long long)md.nblk * C.chunk / C.nchunk);
+    const int blk1 = (int)((long long)md.nblk * (C.chunk + 1) / C.nchunk);
+    float nx = gxp[blk0 * TC_BP + p], ny = gyp[blk0 * TC_BP + p], nz = gzp[blk0 * TC_BP + p];
+    float nw = gwp[blk0 * TC_BP + p];
     // the MMA operand descriptors at K step 0 (the tiles do not move); a K
     // step adds its byte offset / 16 to the start-address field, which cannot
     // carry out of its 14 bits (every shared-memory address is below 2^18)
     const uint64_t g1ah = tc::sdesc(C.su + C.L.phi_hi, 128, C.sg), g1al = tc::sdesc(C.su + C.L.phi_lo, 128, C.sg);
-    const uint64_t g1bh = tc::sdesc(C.su + C.L.D_hi, 128, C.sg), g1bl = tc::sdesc(C.su + C.L.D_lo, 128, C.sg);
+    const uint64_t g1bh = tc::sdesc(C.su + C.L.D_hi, 128, C.sg);  // D_lo follows as rows np .. 2 np - 1
     const uint64_t g2ah = tc::sdesc_sw128(C.su + C.L.pt_hi), g2al = tc::sdesc_sw128(C.su + C.L.pt_lo);
-    const uint64_t g2bh = tc::sdesc_sw128(C.su + C.L.x_hi), g2bl = tc::sdesc_sw128(C.su + C.L.x_lo);
+    const uint64_t g2bh = tc::sdesc_sw128(C.su + C.L.x_hi);  // X_lo follows as rows np .. 2 np - 1
     int atf_owner = -1;  // owner atom the atf table was built for
     float *atf_w = const_cast<float *>(C.atf);
 
@@ -475,12 +484,16 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint3
         ph2 ^= 1;
         auto batch = [&](auto wtag, int c) {
             constexpr int W = decltype(wtag)::value;
-            uint32_t rv[W], rs[W];
-            float v[W], s[W];
+            uint32_t rv[W], rv2[W], rs[W];
+            float v[W], v2[W], s[W];
             tld_issue<W>(C.tV + C.lanes + C.c0 + c, rv);
+            tld_issue<W>(C.tV + C.lanes + C.np + C.c0 + c, rv2);
             if (!first) tld_issue<W>(C.tS + C.lanes + C.c0 + c, rs);
             tld_wait();
             tld_done<W>(rv, v);
+            tld_done<W>(rv2, v2);
+#pragma unroll
+            for (int i = 0; i < W; i++) v[i] += v2[i];
             if (!first) {
                 tld_done<W>(rs, s);
 #pragma unroll
@@ -497,12 +510,12 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint3
         return true;
     };
 
-    for (int blk = C.chunk; blk < md.nblk; blk += C.nchunk) {
+    for (int blk = blk0; blk < blk1; blk++) {
         const int p0 = blk * TC_BP;
         const int own0 = min(p0 / npa, md.natom - 1);
         const float px = nx, py = ny, pz = nz, pw = nw;
-        if (blk + C.nchunk < md.nblk) {  // this thread's point of the next block
-            const int i1 = p0 + C.nchunk * TC_BP + p;
+        if (blk + 1 < blk1) {  // this thread's point of the next block
+            const int i1 = p0 + TC_BP + p;
             nx = gxp[i1]; ny = gyp[i1]; nz = gzp[i1]; nw = gwp[i1];
         }
         const unsigned long long amask = bmask[2 * blk];
@@ -580,9 +593,8 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint3
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int s = 0; s < C.np / 8; s++) {
                     const uint64_t ka = (uint64_t)s * 16u;  // 2 cores of 128 B, in 16-byte units
-                    tc::mma(C.tT, g1ah + ka, g1bh + ka, C.id, s > 0);  // Phi_hi D_hi
-                    tc::mma(C.tT, g1ah + ka, g1bl + ka, C.id, 1);      // + Phi_hi D_lo
-                    tc::mma(C.tT, g1al + ka, g1bh + ka, C.id, 1);      // + Phi_lo D_hi
+                    tc::mma(C.tT, g1ah + ka, g1bh + ka, C.id2, s > 0);  // [Phi_hi D_hi | Phi_hi D_lo]
+                    tc::mma(C.tT, g1al + ka, g1bh + ka, C.id, 1);       // + Phi_lo D_hi into the first half
                 }
                 tc::commit(C.bar1);
             }
@@ -595,7 +607,22 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint3
             }
             ph1 ^= 1;
             in1 = false;
-            tld<NQ>(C.tT + C.lanes + C.c0, Tv);
+            // T = the two halves of the accumulator, 8 columns per batch of loads
+            auto tbatch = [&](auto wtag, int c) {
+                constexpr int W = decltype(wtag)::value;
+                uint32_t r1[W], r2[W];
+                float v2[W];
+                tld_issue<W>(C.tT + C.lanes + C.c0 + c, r1);
+                tld_issue<W>(C.tT + C.lanes + C.np + C.c0 + c, r2);
+                tld_wait();
+                tld_done<W>(r1, Tv + c);
+                tld_done<W>(r2, v2);
+#pragma unroll
+                for (int i = 0; i < W; i++) Tv[c + i] += v2[i];
+            };
+#pragma unroll
+            for (int c = 0; c + 8 <= NQ; c += 8) tbatch(std::integral_constant<int, 8>{}, c);
+            if constexpr (NQ % 8 != 0) tbatch(std::integral_constant<int, 4>{}, NQ - 4);
         } else {
             // T on the CUDA cores: this point's row of Phi (hi + lo is the FP32
             // value) against D's rows, the thread's column quarter
@@ -701,9 +728,8 @@ __device__ __forceinline__ void tc_loop(const DevBatch &b, TcCta &C, const uint3
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int k = 0; k < TC_BP / 8; k++) {
                 const uint64_t ko = (uint64_t)((k >> 2) * 64 + (k & 3) * 2);  // (k/4) KB + (k%4) 32 B, 16-byte units
-                tc::mma(C.tV, g2ah + ko, g2bh + ko, C.id, k > 0);  // Phi_hi^T X_hi
-                tc::mma(C.tV, g2ah + ko, g2bl + ko, C.id, 1);      // + Phi_hi^T X_lo
-                tc::mma(C.tV, g2al + ko, g2bh + ko, C.id, 1);      // + Phi_lo^T X_hi
+                tc::mma(C.tV, g2ah + ko, g2bh + ko, C.id2, k > 0);  // [Phi_hi^T X_hi | Phi_hi^T X_lo]
+                tc::mma(C.tV, g2al + ko, g2bh + ko, C.id, 1);       // + Phi_lo^T X_hi into the first half
             }
             tc::commit(C.bar2);
         }
@@ -757,7 +783,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     const int m = list[blockIdx.y], chunk = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
-    if (chunk >= md.nblk) return;
+    if ((long long)md.nblk * (chunk + 1) / nchunk == (long long)md.nblk * chunk / nchunk) return;  // no blocks
     TcCta C;
     C.md = &md;
     C.m = m;
@@ -860,6 +886,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) grid_xc_tc_kernel(DevBatch b, i
     C.tS = tmem + TC_SCOL;
     C.lanes = (uint32_t)((C.warp & 3) * 32) << 16;  // this warp's TMEM lane quarter
     C.id = tc::idesc(128, np);
+    C.id2 = tc::idesc(128, 2 * np);
     C.su = tc::smem_u32(smem);
     tc_loop<TA, FINAL, NQ>(b, C, uw, rw);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
