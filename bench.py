@@ -10,7 +10,7 @@ DIIS/eigh, final step.
 The mixed path runs with the recheck: molecules whose DIIS error is still
 above 1e-4 after the 20 iterations run again from the initial guess with
 every Fock build at the final step's precision, and the unconverged ones
-(DIIS error above 1e-3) are redone on the FP64 path.
+(DIIS error above 3e-4) are redone on the FP64 path.
 
 Printed JSON line (rank 0):
   value       molecules within the accuracy gate per second, inputs resident
@@ -380,7 +380,7 @@ def validate_main(args):
 # Mixed-precision options of the benchmark (and of every GPU leg below): the
 # fixed protocol, with molecules still moving after the 20 iterations run
 # again at the final step's precision (rks_options.recheck_err).
-RECHECK_ERR, RECHECK_FP64_ERR = 1e-4, 1e-3
+RECHECK_ERR, RECHECK_FP64_ERR = 1e-4, 3e-4
 GATE_DE, GATE_DGAP = 1e-5, 1e-4
 
 
@@ -609,7 +609,9 @@ def main():
     dom = max(stages, key=lambda k: stages[k]["ms"])
     roof = roofline(dom, stages[dom], B, mols, pk, probes)
     others = {k: roofline(k, stages[k], B, mols, pk, probes)
-              for k in ("jk", "grid_xc_tc", "grid_xc_tc_final", "jk_final", "grid_xc_final")
+              # the parent batch's kernels (the FP64 redo's stages share names with
+              # the CUDA-core grid stages and cover only its few molecules)
+              for k in ("jk", "grid_xc_tc", "grid_xc_tc_final", "jk_final")
               if k in stages and k != dom}
 
     cpu = None

@@ -135,7 +135,8 @@ typedef struct rks_options {
                                converged molecules, the rest are recomputed in float64); its
                                result is the FP64 path's.  The redo runs as a batch of its own
                                on its own stream, beside the precise reruns and the final step.
-                               0 disables.  Default 1e-3 */
+                               0 disables.  Default 3e-4 (above it, a precise rerun of the
+                               9-11-heavy-atom workload missed the FP64 gap by 1.2e-4 Ha) */
 } rks_options;
 
 #define RKS_ITER_JK_FINAL 1

@@ -165,7 +165,7 @@ extern "C" int rks_options_default(rks_options *o) {
     o->admit_wait_us = 20000;
     o->iter_precision = 0;
     o->recheck_err = 1e-4;
-    o->recheck_fp64_err = 1e-3;
+    o->recheck_fp64_err = 3e-4;
     return RKS_OK;
 }
 

@@ -123,7 +123,8 @@ struct JkPlan {
 };
 template <typename TS, typename TA, typename TACC> static JkPlan jk_plan(int n, int npair) {
     const size_t mats = (((size_t)n * n * sizeof(TA) + 15) & ~(size_t)15) + 2 * (size_t)n * n * sizeof(TACC);
-    const size_t table = (size_t)npair * sizeof(double) + (((size_t)npair * sizeof(uint32_t) + 15) & ~(size_t)15);
+    const size_t table = (((size_t)npair * sizeof(float) + 15) & ~(size_t)15) +
+                         (((size_t)npair * sizeof(uint32_t) + 15) & ~(size_t)15);
     const int ch_max = 32 * JK_STAGE_BLOCK;  // a full chunk of the largest staged blocks
     JkPlan p;
     for (p.warps = sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS_MAX; p.warps >= 8; p.warps /= 2)
@@ -167,10 +168,11 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
     TACC *Js = (TACC *)(smem_raw + o);
     TACC *Ks = Js + nn;
     o += 2 * (size_t)nn * sizeof(TACC);
-    double *kq = (double *)(smem_raw + o);
+    float *kqf = (float *)(smem_raw + o);  // Schwarz factors rounded to FP32 (screening, see below)
+    const double *kq = b.kq + md.pair0;    // and exact, for the few kets near the threshold
     uint32_t *pinfo = nullptr;
     if (pairs_in_smem) {
-        o += (size_t)max_pair * sizeof(double);
+        o += ((size_t)max_pair * sizeof(float) + 15) & ~(size_t)15;  // keeps the stage below 16-byte aligned
         pinfo = (uint32_t *)(smem_raw + o);
         o += ((size_t)max_pair * sizeof(uint32_t) + 15) & ~(size_t)15;
     }
@@ -189,11 +191,11 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
     };
     if (pairs_in_smem) {
         for (int i = threadIdx.x; i < npair; i += blockDim.x) {
-            kq[i] = b.kq[md.pair0 + i];
+            kqf[i] = (float)kq[i];
             pinfo[i] = pair_of(i);
         }
     } else {
-        kq = b.kq + md.pair0;  // tables stay in global memory
+        kqf = nullptr;  // tables stay in global memory
     }
     __syncthreads();
     const TS *store = (const TS *)b.store + md.eri0;
@@ -207,6 +209,7 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
         const int r = npair - 1 - q;
         const uint32_t bi = pairs_in_smem ? pinfo[r] : pair_of(r);
         const double qpq = kq[r];
+        const float qpqf = (float)qpq;
         const int a0 = bi & 127, b0 = (bi >> 7) & 127, lP = (bi >> 14) & 1, lQ = (bi >> 15) & 1;
         const TA bra_scale = (bi >> 16) & 1 ? (TA)0.5 : (TA)1;
         const int npq = (lP ? 3 : 1) * (lQ ? 3 : 1);
@@ -219,7 +222,14 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
             int nel = 0;
             if (s <= r) {
                 ki = pairs_in_smem ? pinfo[s] : pair_of(s);
-                if (qpq * kq[s] >= TAU_SCHWARZ) {
+                // the store kept the quartet iff Q_pq Q_rs >= tau in FP64; the
+                // FP32 product is within 2e-7 of it, so it decides every ket
+                // outside +-1e-5 of tau, and the FP64 test the rest
+                const float pf = qpqf * (kqf ? kqf[s] : (float)kq[s]);
+                const bool pass = pf > (float)(TAU_SCHWARZ * (1.0 + 1e-5))   ? true
+                                  : pf < (float)(TAU_SCHWARZ * (1.0 - 1e-5)) ? false
+                                                                             : qpq * kq[s] >= TAU_SCHWARZ;
+                if (pass) {
                     keep = true;
                     nel = npq * ((ki >> 14) & 1 ? 3 : 1) * ((ki >> 15) & 1 ? 3 : 1);
                 }

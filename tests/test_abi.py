@@ -81,7 +81,7 @@ def test_options_default(L):
     assert o.precision == g.RKS_FP64 and o.xc == 1 and o.diis_space == 8
     assert o.guess == g.RKS_GUESS_SAD and o.fix_theta == 0.1 and o.grid_tc == 1
     assert o.max_cohorts == 4 and o.admit_wait_us == 20000
-    assert o.iter_precision == 0 and o.recheck_err == 1e-4 and o.recheck_fp64_err == 1e-3
+    assert o.iter_precision == 0 and o.recheck_err == 1e-4 and o.recheck_fp64_err == 3e-4
     assert L.rks_options_default(None) == g.RKS_EINVAL
 
 
