@@ -17,18 +17,22 @@
 // step's registers per thread) are sized for the launch's largest basis: on
 // the FP64 path every issued DFMA costs the same whether or not its result is
 // used (the pipe, not the issue, bounds the kernel).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "xc.cuh"
 #include "boys.cuh"
 
 template <typename T, typename TA, int BP, int TILE, int NV>
-__global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk, int mode, int skip_tc) {
+__global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk, int mode, int skip_tc, int nbf_lo,
+                                                          int nbf_hi) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = blockIdx.y, chunk = blockIdx.x;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
     if (skip_tc && b.mol[m].tcq) return;  // done by the tensor-core kernel
+    if (md.nbf <= nbf_lo || md.nbf > nbf_hi) return;  // another size class's launch
     const int n = md.nbf, nsh = md.nsh;
     const int XS = n | 1;  // odd row stride of X (bank-conflict free both ways)
     T *Ds = (T *)smem_raw;                 // [n][n]
@@ -244,23 +248,27 @@ __global__ void __launch_bounds__(256, 1) grid_xc_kernel(DevBatch b, int nchunk,
 }
 
 template <typename T, typename TA, int BP, int TILE, int NV>
-static void launch_gx1(const DevBatch &b, int nchunk, int mode, int skip_tc, int max_nbf, int max_nsh, cudaStream_t s) {
-    const int n = max_nbf, XS = n | 1;
+static void launch_gx1(const DevBatch &b, int nchunk, int mode, int skip_tc, int nbf_lo, int nbf_hi, int max_nsh,
+                       cudaStream_t s) {
+    const int n = nbf_hi, XS = n | 1;
     size_t sm = sizeof(T) * ((size_t)n * n + 4ull * n * BP + (size_t)BP * XS + 18ull * BP + 18ull * max_nsh) +
                 sizeof(int) * 2ull * max_nsh + 64;
     cudaFuncSetAttribute(grid_xc_kernel<T, TA, BP, TILE, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    grid_xc_kernel<T, TA, BP, TILE, NV><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode, skip_tc);
+    grid_xc_kernel<T, TA, BP, TILE, NV><<<dim3(nchunk, b.nmol), 256, sm, s>>>(b, nchunk, mode, skip_tc, nbf_lo, nbf_hi);
 }
 
-// V' tile and density registers sized for the largest basis of the launch
-// (16 TILE >= nbf; NV >= nbf / G with G = 256 / BP threads per point)
+// One launch per basis-size class (nbf <= 64, <= 80, <= 96) up to the batch's
+// largest: the V' tile and the density registers are sized for the class
+// (16 TILE >= nbf; NV >= nbf / G with G = 256 / BP threads per point), and
+// each launch skips the molecules of the other classes
 template <typename T, typename TA, int BP>
 static void launch_gx(const DevBatch &b, int nchunk, int mode, int skip_tc, int max_nbf, int max_nsh, cudaStream_t s) {
     constexpr int G = 256 / BP;
     static_assert(RKS_NBF_CAP <= 96, "tile classes cover nbf <= 96");
-    if (max_nbf <= 64) launch_gx1<T, TA, BP, 4, (64 + G - 1) / G>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
-    else if (max_nbf <= 80) launch_gx1<T, TA, BP, 5, (80 + G - 1) / G>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
-    else launch_gx1<T, TA, BP, 6, (96 + G - 1) / G>(b, nchunk, mode, skip_tc, max_nbf, max_nsh, s);
+    launch_gx1<T, TA, BP, 4, (64 + G - 1) / G>(b, nchunk, mode, skip_tc, 0, std::min(max_nbf, 64), max_nsh, s);
+    if (max_nbf > 64)
+        launch_gx1<T, TA, BP, 5, (80 + G - 1) / G>(b, nchunk, mode, skip_tc, 64, std::min(max_nbf, 80), max_nsh, s);
+    if (max_nbf > 80) launch_gx1<T, TA, BP, 6, (96 + G - 1) / G>(b, nchunk, mode, skip_tc, 80, max_nbf, max_nsh, s);
 }
 
 void launch_grid_xc(const DevBatch &b, int nchunk, int acc_fp64, int mode, int skip_tc, int max_nbf, int max_nsh,
