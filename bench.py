@@ -49,10 +49,12 @@ sys.path.insert(0, ROOT)
 
 import molgen  # noqa: E402
 
-# dram__bytes_read.sum + dram__bytes_write.sum of grid_xc_tc_kernel<float, 0>
-# per grid point from one ncu capture of the current kernel (None until the
-# kernel as it stands has been captured); scaled by the points of a launch
-GRID_TC_DRAM_BYTES_PER_POINT = None
+# dram__bytes_read.sum + dram__bytes_write.sum of grid_xc_tc_kernel<float, 0, NQ>
+# per grid point from one ncu capture of the current kernel (38 molecules:
+# 16.73 B at NQ = 16, 16.90 B at NQ = 20; the points' coordinates and weights
+# are 16 B); scaled by the points of a launch.  Set to None when the kernel
+# changes until it has been captured again.
+GRID_TC_DRAM_BYTES_PER_POINT = 16.8
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
@@ -494,6 +496,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="one step with per-stage times")
+    ap.add_argument("--profile-precision", choices=("mixed", "fp64"), default="mixed",
+                    help="--profile-only: the mixed path (default) or the plain FP64 path")
+    ap.add_argument("--profile-iters", type=int, default=20, help="--profile-only: SCF iterations")
     ap.add_argument("--serve", action="store_true", help="Poisson serving sweep instead of the batch step")
     ap.add_argument("--serve-n", type=int, default=1500)
     ap.add_argument("--validate", action="store_true",
@@ -534,11 +539,20 @@ def main():
         B.run()
 
     if args.profile_only:
+        if args.profile_precision == "fp64" or args.profile_iters != 20:
+            B.close()
+            ctx.close()
+            prec = g.RKS_FP64 if args.profile_precision == "fp64" else g.RKS_MIXED
+            ctx = g.Context(precision=prec, fixed_iters=args.profile_iters, recheck_err=RECHECK_ERR,
+                            recheck_fp64_err=RECHECK_FP64_ERR, device=local)
+            B = g.Batch(ctx, mols)
         ctx.profile(True)
-        step()
+        B.setup()
+        B.run()
         B.sync()
         prof = ctx.profile_read()
-        print(json.dumps({"stages": prof, "nmol": nmol}, indent=1))
+        print(json.dumps({"stages": prof, "nmol": nmol, "precision": args.profile_precision,
+                          "iterations": args.profile_iters}, indent=1))
         return
 
     # W untimed warm-up steps; the last one records per-stage CUDA events
