@@ -319,6 +319,63 @@ def _oracle_fixed20(mol):
     return r["E"], r["gap"], r["D"]
 
 
+def converge_main(args):
+    """The batch workload under the converge protocol: each molecule iterates
+    until |E_k - E_(k-1)| and the DIIS error fall below the thresholds (at
+    most max_iters), drops out of the iterations when it does, then takes the
+    final step.  Mixed on every molecule, timed with CUDA events on the
+    batch's stream (setup included); the FP64 path, converged tighter, on the
+    first --converge-ref-n molecules as the reference of the gate."""
+    import torch
+    import paper_2311_01135_gb300 as g
+    g.build()
+    mols = workload(args.nmol)
+    copt = dict(fixed_iters=0, max_iters=100)
+    with g.Context(precision=g.RKS_MIXED, e_tol=1e-6, err_tol=1e-5, **copt) as ctx:
+        stream = torch.cuda.ExternalStream(ctx.stream())
+        with g.Batch(ctx, mols[:8]) as Bw:  # module load, first launches
+            Bw.run()
+            Bw.sync()
+        with g.Batch(ctx, mols) as B:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.setup()
+            B.run()
+            e1.record(stream)
+            B.sync()
+            ms = e0.elapsed_time(e1)
+            rmx = [B.result(m) for m in range(len(mols))]
+    nref = min(args.converge_ref_n, len(mols))
+    with g.Context(precision=g.RKS_FP64, e_tol=1e-8, err_tol=1e-6, **copt) as c64, \
+            g.Batch(c64, mols[:nref]) as B64:
+        t0 = time.perf_counter()
+        B64.run()
+        B64.sync()
+        t64 = time.perf_counter() - t0
+        r64 = [B64.result(m) for m in range(nref)]
+    it = np.array([r["iters"] for r in rmx])
+    conv = np.array([r["status"] == "ok" for r in rmx])
+    ok = [(a, b) for a, b in zip(rmx[:nref], r64) if a["status"] == "ok" and b["status"] == "ok"]
+    dE = np.array([abs(a["E"] - b["E"]) for a, b in ok])
+    dg = np.array([abs(a["gap"] - b["gap"]) for a, b in ok])
+    line = {"metric": "molecules/s under the converge protocol (mixed, |dE_k| < 1e-6 Ha, DIIS error < 1e-5)",
+            "value": len(mols) / (ms / 1e3), "unit": "molecules/s", "n_gpus": 1, "nmol": len(mols),
+            "ms": ms, "converged": int(conv.sum()), "not_converged": int((~conv).sum()),
+            "iterations": {"min": int(it.min()), "p50": float(np.median(it)), "p90": float(np.percentile(it, 90)),
+                           "max": int(it.max()), "mean": float(it.mean())},
+            "gate_vs_fp64_converged": {"n_checked": len(ok), "n_dE_over_1e-5": int((dE > GATE_DE).sum()),
+                                       "n_dgap_over_1e-4": int((dg > GATE_DGAP).sum()),
+                                       "max_abs_dE": float(dE.max()) if len(dE) else None,
+                                       "max_abs_dgap": float(dg.max()) if len(dg) else None,
+                                       "p99_abs_dE": float(np.percentile(dE, 99)) if len(dE) else None,
+                                       "fp64": "converged to |dE_k| < 1e-8 Ha, DIIS error < 1e-6",
+                                       "fp64_not_converged": sum(1 for b in r64 if b["status"] != "ok")},
+            "fp64_reference_mol_per_s": nref / t64,
+            "data": "synthetic", "config": workload_config(len(mols), 1)}
+    print(json.dumps(line), flush=True)
+
+
 def validate_main(args):
     """Accuracy of the whole workload: the mixed path against the FP64 GPU path
     on every molecule, and both against the FP64 oracle on a subset stratified
@@ -501,6 +558,9 @@ def main():
     ap.add_argument("--profile-iters", type=int, default=20, help="--profile-only: SCF iterations")
     ap.add_argument("--serve", action="store_true", help="Poisson serving sweep instead of the batch step")
     ap.add_argument("--serve-n", type=int, default=1500)
+    ap.add_argument("--converge", action="store_true",
+                    help="the batch workload under the converge protocol (retire on convergence)")
+    ap.add_argument("--converge-ref-n", type=int, default=512)
     ap.add_argument("--validate", action="store_true",
                     help="mixed vs FP64 GPU on every molecule, and vs the oracle on a stratified subset")
     ap.add_argument("--oracle-n", type=int, default=96)
@@ -512,6 +572,8 @@ def main():
         return serve_main(args)
     if args.validate:
         return validate_main(args)
+    if args.converge:
+        return converge_main(args)
 
     import torch
     import paper_2311_01135_gb300 as g
