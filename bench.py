@@ -372,7 +372,10 @@ def converge_main(args):
                                        "fp64": "converged to |dE_k| < 1e-8 Ha, DIIS error < 1e-6",
                                        "fp64_not_converged": sum(1 for b in r64 if b["status"] != "ok")},
             "fp64_reference_mol_per_s": nref / t64,
-            "data": "synthetic", "config": workload_config(len(mols), 1)}
+            "data": "synthetic",
+            "config": dict(workload_config(len(mols), 1),
+                           workload=f"{len(mols)} molecules/GPU, 9-11 heavy atoms (C/N/O/F+H), B3LYP(VWN5)/STO-3G, "
+                                    "mixed precision, converge protocol (at most 100 iterations) + final step")}
     print(json.dumps(line), flush=True)
 
 
