@@ -164,6 +164,25 @@ class DIIS:
         return self.F[-1]
 
 
+def sad_density(Z, S):
+    """Superposed neutral atoms (the "sad" reading in the module docstring)
+    from the atomic numbers and the overlap matrix alone."""
+    n = S.shape[0]
+    D = np.zeros((n, n))
+    i = 0
+    for z in Z:
+        if int(z) == 1:
+            D[i, i] = 1.0 / S[i, i]
+            i += 1
+            continue
+        ss = S[i:i + 2, i:i + 2]
+        D[i:i + 2, i:i + 2] = 2.0 * np.linalg.inv(ss)
+        for k in range(2, 5):
+            D[i + k, i + k] = (int(z) - 4) / 3.0
+        i += 5
+    return D
+
+
 class System:
     """Everything of iteration 0 for one molecule (Section 3.1)."""
 
@@ -214,19 +233,7 @@ class System:
         return solve_fock(self.H, self.X, self.nocc)[2]
 
     def sad_guess(self):
-        D = np.zeros((self.nbf, self.nbf))
-        i = 0
-        for z in self.Z:
-            if int(z) == 1:
-                D[i, i] = 1.0 / self.S[i, i]
-                i += 1
-                continue
-            ss = self.S[i:i + 2, i:i + 2]
-            D[i:i + 2, i:i + 2] = 2.0 * np.linalg.inv(ss)
-            for k in range(2, 5):
-                D[i + k, i + k] = (int(z) - 4) / 3.0
-            i += 5
-        return D
+        return sad_density(self.Z, self.S)
 
     def guess(self, kind):
         if kind == "core":
