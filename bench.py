@@ -379,6 +379,101 @@ def converge_main(args):
     print(json.dumps(line), flush=True)
 
 
+def large_workload(nmol, seed=4):
+    """The larger-molecule workload: 20-30 heavy atoms (seed 4), basis ~120-200."""
+    return molgen.batch(seed, nmol, 20, 30)
+
+
+def large_main(args):
+    """The 20-30-heavy-atom workload: every stage on the global-memory kernels
+    (J/K, two-pass grid quadrature, SCF steps with global Jacobi scratch).
+    Mixed precision, 20 iterations + recheck + final step on --large-n
+    molecules (CUDA events around setup + run on the batch's stream); stage
+    times of a profiled run on the first --large-prof-n; the FP64 path on the
+    first --large-fp64-n (the gate's reference, itself pinned to the oracle by
+    tests/test_gpu_large.py); direct SCF (every quartet recomputed inside J/K,
+    no packed store) on the first --large-direct-n."""
+    import torch
+    import paper_2311_01135_gb300 as g
+    g.build()
+    mols = large_workload(args.large_n)
+    nbf = np.array([g.rks_nbf(Z) for Z, _ in mols])
+    opt = dict(fixed_iters=20, recheck_err=RECHECK_ERR, recheck_fp64_err=RECHECK_FP64_ERR)
+
+    def timed(ctx, sub):
+        stream = torch.cuda.ExternalStream(ctx.stream())
+        with g.Batch(ctx, sub) as B:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.setup()
+            B.run()
+            e1.record(stream)
+            B.sync()
+            ms = e0.elapsed_time(e1)
+            return ms, [B.result(k) for k in range(len(sub))]
+
+    with g.Context(precision=g.RKS_MIXED, **opt) as ctx:
+        timed(ctx, mols[:1])  # module load, first launches
+        clocks = Clocks()
+        clocks.start()
+        ms, rmx = timed(ctx, mols)
+        ck = clocks.stop()
+        probes = measured_peaks(g, ctx)
+        sub = mols[:args.large_prof_n]
+        ctx.profile(True)
+        with g.Batch(ctx, sub) as Bp:
+            Bp.setup()
+            Bp.run()
+            Bp.sync()
+            sc = [Bp.dump(m, g.RKS_DUMP_SCALARS) for m in range(len(sub))]
+        prof = ctx.profile_read()
+        ctx.profile(False)
+    n64 = min(args.large_fp64_n, len(mols))
+    with g.Context(precision=g.RKS_FP64, fixed_iters=20) as c64:
+        timed(c64, mols[:1])
+        ms64, r64 = timed(c64, mols[:n64])
+    nd = min(args.large_direct_n, len(mols))
+    with g.Context(precision=g.RKS_MIXED, direct_scf=g.RKS_DIRECT_ALWAYS, **opt) as cd:
+        msd, rd = timed(cd, mols[:nd])
+    gate = gate_report(rmx[:n64], r64)
+    ddir = [abs(a["E"] - b["E"]) for a, b in zip(rd, rmx[:nd])]
+    # rooflines of the two iteration kernels, from the profiled sample
+    pk = peaks()
+    roof = {}
+    pts = [s_[6] for s_ in sc]
+    if "grid_large" in prof:
+        st = prof["grid_large"]
+        flops = sum(4.0 * p_ * k * k for p_, k in zip(pts, nbf[:len(sub)]))  # rho and V' passes, dense
+        ach = flops / (st["ms"] / max(st["launches"], 1) / 1e3) / 1e12
+        peak = probes.get("fp32_fma")
+        roof["grid_large"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                              "frac": ach / peak if peak else None,
+                              "units": "4 * points * nbf^2 per molecule per launch (T = Phi D and Phi^T X)",
+                              "peak_source": "FP32 FMA measured by rks_probe_peak in this run"}
+    if "jk_large" in prof:
+        st = prof["jk_large"]
+        nbytes = sum(4.0 * s_[5] for s_ in sc)
+        ach = nbytes / (st["ms"] / max(st["launches"], 1) / 1e3) / 1e9
+        roof["jk_large"] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                            "frac": ach / pk["hbm_gbs"], "units": "4 B x packed store elements per launch",
+                            "peak_source": pk["_source"]}
+    line = {"metric": "molecules/s (20-30 heavy atoms) mixed vs FP64 on 1 GB300", "value": len(mols) / (ms / 1e3),
+            "unit": "molecules/s", "n_gpus": 1, "ms": ms, "higher_is_better": True, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{len(mols)} molecules, 20-30 heavy atoms (C/N/O/F+H), B3LYP(VWN5)/STO-3G, "
+                                   "mixed precision, 20 SCF iterations + recheck + final step", "seed": 4,
+                       "nbf": {"min": int(nbf.min()), "mean": float(nbf.mean()), "max": int(nbf.max())}},
+            "status_not_ok": sum(1 for r in rmx if r["status"] != "ok"),
+            "clocks": ck, "gate_vs_fp64_sample": gate,
+            "fp64_gpu": {"value": n64 / (ms64 / 1e3), "unit": "molecules/s", "nmol": n64},
+            "direct_scf": {"value": nd / (msd / 1e3), "unit": "molecules/s", "nmol": nd,
+                           "max_abs_dE_vs_stored": float(max(ddir)) if ddir else None},
+            "roofline_large": roof, "peaks_probed_tflops": probes,
+            "stages_ms_sample": {k: round(v["ms"], 3) for k, v in prof.items()}, "sample_n": len(sub)}
+    print(json.dumps(line), flush=True)
+
+
 def validate_main(args):
     """Accuracy of the whole workload: the mixed path against the FP64 GPU path
     on every molecule, and both against the FP64 oracle on a subset stratified
@@ -567,6 +662,12 @@ def main():
     ap.add_argument("--validate", action="store_true",
                     help="mixed vs FP64 GPU on every molecule, and vs the oracle on a stratified subset")
     ap.add_argument("--oracle-n", type=int, default=96)
+    ap.add_argument("--large", action="store_true",
+                    help="the 20-30-heavy-atom workload (global-memory kernels, direct SCF sample)")
+    ap.add_argument("--large-n", type=int, default=256)
+    ap.add_argument("--large-fp64-n", type=int, default=4)
+    ap.add_argument("--large-direct-n", type=int, default=8)
+    ap.add_argument("--large-prof-n", type=int, default=16)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 1)
     if args.impl == "reference":
@@ -577,6 +678,8 @@ def main():
         return validate_main(args)
     if args.converge:
         return converge_main(args)
+    if args.large:
+        return large_main(args)
 
     import torch
     import paper_2311_01135_gb300 as g

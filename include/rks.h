@@ -65,7 +65,8 @@ extern "C" {
 #define RKS_FP64 0  /* every step in FP64 */
 #define RKS_MIXED 1 /* FP32 ERIs / J/K / grid + FP64 linear algebra and energy, FP64 final correction */
 
-#define RKS_MAX_NBF 96 /* largest basis a molecule may have */
+#define RKS_MAX_NBF 224 /* largest basis a molecule may have (20-30 heavy atoms reach ~200); above
+                           96 functions a molecule takes the global-memory J/K, grid and SCF kernels */
 
 /* ---------------------------------------------------------- initial guess */
 #define RKS_GUESS_SAD 0  /* superposed neutral atoms: 1s/2s space full, 2p^(Z-4) spherically averaged */
@@ -121,7 +122,13 @@ typedef struct rks_options {
                                RKS_ITER_GRID_FINAL = grid pass as in the final step (density
                                contraction on the CUDA cores); default 0 (both at iteration
                                precision) */
-    int32_t pad1;
+    int32_t direct_scf;     /* where J/K get the two-electron integrals (paper Section 5,
+                               "Recomputation"): RKS_DIRECT_NEVER (default) computes the
+                               Schwarz-screened packed store once and streams it every Fock
+                               build; RKS_DIRECT_ALWAYS keeps no store and recomputes every kept
+                               quartet inside each J/K pass (the mixed final step recomputes
+                               them in FP64); RKS_DIRECT_AUTO does so only for a batch whose
+                               packed stores would take more than 70% of the free device memory */
     double recheck_err;     /* RKS_MIXED, fixed protocol: a molecule whose DIIS error max|e|
                                after the fixed iterations exceeds recheck_err is run again from
                                the initial guess, the same number of iterations, with both Fock
@@ -141,6 +148,10 @@ typedef struct rks_options {
 
 #define RKS_ITER_JK_FINAL 1
 #define RKS_ITER_GRID_FINAL 2
+
+#define RKS_DIRECT_NEVER 0
+#define RKS_DIRECT_ALWAYS 1
+#define RKS_DIRECT_AUTO 2
 
 /* One molecule's outputs: the labels the paper's dataset records per
  * conformer (Section 4: energy, HOMO, LUMO, HL gap) and the SCF bookkeeping

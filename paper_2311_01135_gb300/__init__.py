@@ -23,7 +23,8 @@ RKS_GUESS_SAD, RKS_GUESS_CORE = 0, 1
 RKS_ITER_JK_FINAL, RKS_ITER_GRID_FINAL = 1, 2
 RKS_PROBE_FP32_FMA, RKS_PROBE_FP64_FMA, RKS_PROBE_TF32_MMA = 0, 1, 2
 RKS_XC_NOALLOC_MAX = 65536
-RKS_MAX_NBF = 96
+RKS_MAX_NBF = 224
+RKS_DIRECT_NEVER, RKS_DIRECT_ALWAYS, RKS_DIRECT_AUTO = 0, 1, 2
 RKS_STATUS = {0: "ok", 1: "not_converged", 2: "nonfinite", 3: "s_ill", 4: "eigh"}
 (RKS_DUMP_PAIRS, RKS_DUMP_PAIR_Q, RKS_DUMP_ROW_OFF, RKS_DUMP_STORE, RKS_DUMP_S, RKS_DUMP_T, RKS_DUMP_V,
  RKS_DUMP_GRID, RKS_DUMP_J, RKS_DUMP_K, RKS_DUMP_VXC, RKS_DUMP_D, RKS_DUMP_F, RKS_DUMP_EPS, RKS_DUMP_X,
@@ -41,7 +42,7 @@ class rks_options(ctypes.Structure):
                 ("grid_tc", ctypes.c_int32), ("guess", ctypes.c_int32),
                 ("max_cohorts", ctypes.c_int32), ("admit_wait_us", ctypes.c_int32),
                 ("grid_chunks", ctypes.c_int32), ("jk_chunks", ctypes.c_int32),
-                ("iter_precision", ctypes.c_int32), ("pad1", ctypes.c_int32), ("recheck_err", ctypes.c_double),
+                ("iter_precision", ctypes.c_int32), ("direct_scf", ctypes.c_int32), ("recheck_err", ctypes.c_double),
                 ("recheck_fp64_err", ctypes.c_double)]
 
 
@@ -207,7 +208,7 @@ class Context:
     def wait(self, ticket, timeout_s=600.0):
         return _chk(lib().rks_wait(self.h, ticket, timeout_s), "rks_wait")
 
-    def result(self, ticket, nbf_cap=128):
+    def result(self, ticket, nbf_cap=RKS_MAX_NBF):
         r = rks_result_t()
         eps = np.zeros(nbf_cap)
         D = np.zeros(nbf_cap * nbf_cap)

@@ -9,7 +9,9 @@
 #include <type_traits>
 #include <cuda_runtime.h>
 
-#define RKS_NBF_CAP 96      // largest nbf the kernels are compiled for
+#define RKS_NBF_CAP 224     // largest nbf the kernels are compiled for
+#define RKS_NBF_SMALL 96    // largest nbf of the shared-memory J/K, grid and SCF kernels; larger
+                            // molecules take the global-memory kernels of large.cu
 #define RKS_DIIS_MAX 8
 #define RKS_MAXP 3          // primitives per STO-3G shell
 #define RKS_PTS_BLOCK 128   // grid points are stored in blocks of this many
@@ -32,7 +34,7 @@ struct MolDesc {
     long long mat0;     // FP64 matrix arena (doubles); see MatSlot
     long long acc0;     // accumulator arena offset (elements), 3 * nbf^2
     int tcq;            // tensor-core grid kernel: columns per quarter NQ (0: CUDA-core kernel)
-    int pad_;
+    int big;            // nbf > RKS_NBF_SMALL: the global-memory kernels of large.cu
 };
 
 // FP64 matrices of one molecule, each nbf*nbf, at mat0 + slot * nbf*nbf.
@@ -164,6 +166,9 @@ struct DevBatch {
     struct Fx *accx;
     double *accd;
     int *jk_next;           // [nmol] J/K row queue heads (zeroed before each J/K launch)
+    void *gcf;              // molecules above RKS_NBF_SMALL: per grid point the four coefficients of
+                            // X (w v_rho / 2, 2 w v_sigma grad rho), [pts0 + p][4] (T), else null
+    int direct;             // 1: no packed store; J/K recompute the quartets every pass (direct SCF)
     // Boys tables
     const double *boys64;
     const float *boys32;

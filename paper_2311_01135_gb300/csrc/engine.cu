@@ -294,6 +294,11 @@ struct rks_batch {
     int nmol = 0;
     int precision = 0;
     int max_nbf = 0, max_nsh = 0, max_atoms = 0, max_pair = 0;
+    // molecules up to RKS_NBF_SMALL (shared-memory kernels) and above it
+    // (global-memory kernels of large.cu): largest basis, shell and pair counts
+    int max_nbf_small = 0, max_nsh_small = 0, max_pair_small = 0;
+    int max_nbf_big = 0, max_nsh_big = 0, n_big = 0;
+    bool direct = false;               // no packed store: J/K recompute the quartets every pass
     long long ncand = 0, nblk_total = 0;
     std::vector<HostMol> hm;
     std::vector<MolDesc> md;
@@ -497,11 +502,14 @@ static size_t mol_bytes(const rks_options &o, int na, const int32_t *Z) {
     const long long nsh = ns + np, npair = nsh * (nsh + 1) / 2;
     const long long npts = (long long)na * o.n_rad * o.n_theta * o.n_phi;
     const long long nblk = (npts + RKS_PTS_BLOCK - 1) / RKS_PTS_BLOCK;
+    const bool direct = o.direct_scf == RKS_DIRECT_ALWAYS;
     size_t b = sizeof(MolDesc) + sizeof(MolState) + 8 + (size_t)na * 28 + (size_t)nsh * 84;
     b += (size_t)npair * (8 + 4 + 8 + 8 + 8 + 4 + 8 + 45 * esz);
-    if (o.precision == RKS_MIXED && o.fix_theta > 0) b += (size_t)npair * 45 * 8 + 6 * (RKS_FIX_CAP * 16 + 4);
-    b += (size_t)((store_cap(ns, np) + 3) & ~3LL) * esz;
+    if (o.precision == RKS_MIXED && (o.fix_theta > 0 || direct)) b += (size_t)npair * 45 * 8;
+    if (o.precision == RKS_MIXED && o.fix_theta > 0 && !direct) b += 6 * (RKS_FIX_CAP * 16 + 4);
+    if (!direct) b += (size_t)((store_cap(ns, np) + 3) & ~3LL) * esz;
     b += (size_t)nblk * RKS_PTS_BLOCK * 4 * esz + (size_t)nblk * 4;
+    if (nbf > RKS_NBF_SMALL) b += (size_t)nblk * RKS_PTS_BLOCK * 4 * esz;  // X coefficients between the grid passes
     if (o.precision == RKS_MIXED) b += (size_t)nblk * 16;  // grid block masks
     b += (size_t)nbf * nbf * (M_COUNT * 8 + 3 * 8);
     return b;
@@ -617,11 +625,21 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
             d.tcq = tc_plan_mol(na, Zm, nbf, pl);
             hplan.insert(hplan.end(), pl, pl + RKS_TC_PLAN);
         }
+        d.big = nbf > RKS_NBF_SMALL;
         b->hm[m] = {na, nbf, nel / 2, nsh, npair_all, cap, npts};
         b->max_nbf = std::max(b->max_nbf, nbf);
         b->max_nsh = std::max(b->max_nsh, nsh);
         b->max_pair = std::max(b->max_pair, npair_all);
         b->max_atoms = std::max(b->max_atoms, na);
+        if (d.big) {
+            b->n_big++;
+            b->max_nbf_big = std::max(b->max_nbf_big, nbf);
+            b->max_nsh_big = std::max(b->max_nsh_big, nsh);
+        } else {
+            b->max_nbf_small = std::max(b->max_nbf_small, nbf);
+            b->max_nsh_small = std::max(b->max_nsh_small, nsh);
+            b->max_pair_small = std::max(b->max_pair_small, npair_all);
+        }
         atom_off += na;
         sh_off += nsh;
         pair_off += npair_all;
@@ -650,7 +668,18 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     d.boys64 = ctx->boys64;
     d.boys32 = ctx->boys32;
     const size_t esz = o.precision ? sizeof(float) : sizeof(double);
+    // direct SCF: always, or (auto) when the packed stores would take more
+    // than 70% of the device memory free now
+    b->direct = o.direct_scf == RKS_DIRECT_ALWAYS;
+    if (o.direct_scf == RKS_DIRECT_AUTO) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) b->direct = (double)eri_off * esz > 0.7 * (double)fr;
+    }
+    d.direct = b->direct ? 1 : 0;
+    const bool want64 = o.precision == RKS_MIXED && (o.fix_theta > 0 || b->direct);  // FP64 pair data
+    const bool want_fix = o.precision == RKS_MIXED && o.fix_theta > 0 && !b->direct;   // FP64 recompute lists
     int rc = 0;
+    void *gcf = nullptr;
     MolDesc *dmol; MolState *dst; int *dZ, *dsa, *dsl, *dsao, *dcm, *dnp, *drnq; double *dax, *dsx, *dse, *dsc, *dcq, *dkq;
     int2 *dcand, *dkp; long long *droff; void *store; void *gx, *gy, *gz, *gw; double *mat, *accd;
     void *pairprim, *pairprim64 = nullptr;
@@ -662,11 +691,12 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
         (rc = dalloc(b, &dsc, 3 * sh_off)) || (rc = dalloc(b, &dcand, pair_off)) || (rc = dalloc(b, &dcm, pair_off)) ||
         (rc = dalloc(b, &dcq, pair_off)) || (rc = dalloc(b, &dkp, pair_off)) || (rc = dalloc(b, &dkq, pair_off)) ||
         (rc = dalloc(b, &dnp, nmol)) || (rc = dalloc(b, &drnq, pair_off)) || (rc = dalloc(b, &droff, pair_off + nmol)) ||
-        (rc = dalloc(b, (unsigned char **)&store, eri_off * esz)) ||
+        (rc = dalloc(b, (unsigned char **)&store, (b->direct ? 4 : eri_off) * esz)) ||
         (rc = dalloc(b, (unsigned char **)&pairprim, pair_off * 9 * 5 * esz)) ||
-        (o.precision == RKS_MIXED && o.fix_theta > 0 &&
-         ((rc = dalloc(b, (unsigned char **)&pairprim64, pair_off * 9 * 5 * sizeof(double))) ||
-          (rc = dalloc(b, &fixlist, (size_t)nmol * 6 * RKS_FIX_CAP)) || (rc = dalloc(b, &fixcount, (size_t)nmol * 6)))) ||
+        (want64 && (rc = dalloc(b, (unsigned char **)&pairprim64, pair_off * 9 * 5 * sizeof(double)))) ||
+        (want_fix && ((rc = dalloc(b, &fixlist, (size_t)nmol * 6 * RKS_FIX_CAP)) ||
+                      (rc = dalloc(b, &fixcount, (size_t)nmol * 6)))) ||
+        (b->n_big > 0 && (rc = dalloc(b, (unsigned char **)&gcf, pts_off * 4 * esz))) ||
         (rc = dalloc(b, (unsigned char **)&gx, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gy, pts_off * esz)) ||
         (rc = dalloc(b, (unsigned char **)&gz, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gw, pts_off * esz)) ||
         (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) ||
@@ -689,6 +719,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     d.fixcount = fixcount;
     d.fix_theta = o.fix_theta;
     d.gx = gx; d.gy = gy; d.gz = gz; d.gw = gw; d.mat = mat; d.accd = accd; d.accx = (Fx *)accd;  // one buffer, two views
+    d.gcf = gcf;
     cudaStream_t s = b->stream;
 #define UP(dst_, src_)                                                                                      \
     if (!(src_).empty()) {                                                                                  \
@@ -759,12 +790,12 @@ extern "C" int rks_batch_setup(rks_batch *b) {
     { StageScope sc(c, s, "row_count", 0); launch_row_count(d, (int)b->ncand, s); }
     { StageScope sc(c, s, "row_scan", 0); launch_row_scan(d, s); }
     { StageScope sc(c, s, "pair_prim", 0); launch_pair_prim(d, (int)b->ncand, fp32, s); }
-    { StageScope sc(c, s, "eri", 0); launch_eri_store(d, (int)b->ncand, fp32, s); }
+    if (!b->direct) { StageScope sc(c, s, "eri", 0); launch_eri_store(d, (int)b->ncand, fp32, s); }
     if (d.fixlist) { StageScope sc(c, s, "fix_list", 0); launch_fix_list(d, s); }
     { StageScope sc(c, s, "grid_build", 0); launch_grid_build(d, b->nblk_total, b->blk_mol, c->rad, c->ang, b->max_atoms, s); }
     { StageScope sc(c, s, "grid_masks", 0); launch_grid_masks(d, b->nblk_total, b->blk_mol, s); }
     { StageScope sc(c, s, "scf_init", 0); launch_scf_init(d, s); }
-    { StageScope sc(c, s, "scf_guess", 0); launch_scf_guess(d, b->max_nbf, 0, s); }
+    { StageScope sc(c, s, "scf_guess", 0); launch_scf_guess(d, b->max_nbf_small, 0, s); }
     int rc = check_launch("setup kernels");
     if (rc) return rc;
     b->it_enq = 0;
@@ -800,10 +831,20 @@ static int fock_pass(rks_batch *b, int prec, int mode) {
     const int jk_fin = b->precision == 0 || (prec & RKS_ITER_JK_FINAL);
     const int gr_fin = b->precision == 0 || (prec & RKS_ITER_GRID_FINAL);
     const char *jk_name = mode ? "jk_final" : (jk_fin ? "jk_precise" : "jk");
-    {
+    if (!b->direct && b->max_nbf_small > 0) {
         StageScope sc(c, s, jk_name, 0);
-        if (launch_jk(d, nchunk_jk, jk_fin, mode, b->max_nbf, b->max_pair, s))
+        if (launch_jk(d, nchunk_jk, jk_fin, mode, b->max_nbf_small, b->max_pair_small, s))
             return fail(RKS_EINVAL, "basis too large for the J/K kernel's shared memory");
+    }
+    if (b->direct || b->n_big > 0) {
+        // molecules above RKS_NBF_SMALL, or every molecule in direct SCF
+        const char *nm = b->direct ? (mode ? "jk_direct_final" : "jk_direct") : (mode ? "jk_large_final" : "jk_large");
+        StageScope sc(c, s, nm, 0);
+        const int nm_mol = b->direct ? b->nmol : b->n_big;
+        const int nch = c->opt.jk_chunks > 0 ? c->opt.jk_chunks
+                                             : std::min(256, std::max(8, (4 * c->nsm + nm_mol - 1) / nm_mol));
+        if (launch_jk_large(d, nch, jk_fin, mode, b->direct ? 1 : 0, s))
+            return fail(RKS_EINVAL, "direct SCF final step without FP64 pair data");
     }
     if (jk_fin && b->precision == RKS_MIXED && d.fixlist) {
         StageScope sc(c, s, mode ? "jk_fp64_fix" : "jk_fp64_fix_it", 0);
@@ -826,7 +867,7 @@ static int fock_pass(rks_batch *b, int prec, int mode) {
             bool any_tc = false;
             for (auto &m : b->md) {
                 if (m.tcq) any_tc = true;
-                else need_cc = true;
+                else if (!m.big) need_cc = true;
             }
             if (any_tc) {
                 const int nchunk_tc = c->opt.grid_chunks > 0 ? c->opt.grid_chunks : 16;
@@ -834,11 +875,23 @@ static int fock_pass(rks_batch *b, int prec, int mode) {
                 launch_grid_xc_tc(d, nchunk_tc, gr_fin, mode, b->tcc, s);
             }
         }
-        if (need_cc) {
+        if (need_cc && b->max_nbf_small > 0) {
             const int nchunk_gx = c->opt.grid_chunks > 0 ? c->opt.grid_chunks
                                   : (b->precision == RKS_FP64 ? std::min(256, std::max(16, spread)) : 16);
             StageScope sc(c, s, mode ? "grid_xc_final" : (gr_fin ? "grid_xc_precise" : "grid_xc"), 0);
-            launch_grid_xc(d, nchunk_gx, gr_fin, mode, tc ? 1 : 0, b->max_nbf, b->max_nsh, s);
+            launch_grid_xc(d, nchunk_gx, gr_fin, mode, tc ? 1 : 0, b->max_nbf_small, b->max_nsh_small, s);
+        }
+        if (b->n_big > 0) {
+            // molecules above RKS_NBF_SMALL: two passes, global-memory D and V'.
+            // The mixed path keeps 64 blocks per molecule, so that a molecule
+            // sums its points in the same groups in any batch; FP64 spreads.
+            const int nchunk_lg = c->opt.grid_chunks > 0 ? c->opt.grid_chunks
+                                  : b->precision == RKS_MIXED
+                                      ? 64
+                                      : std::min(512, std::max(16, (2 * c->nsm + b->n_big - 1) / b->n_big));
+            StageScope sc(c, s, mode ? "grid_large_final" : (gr_fin ? "grid_large_precise" : "grid_large"), 0);
+            if (launch_grid_xc_large(d, nchunk_lg, gr_fin, mode, b->max_nbf_big, b->max_nsh_big, s))
+                return fail(RKS_EINVAL, "basis too large for the grid kernels' shared memory");
         }
     }
     return check_launch("fock pass");
@@ -850,7 +903,7 @@ static int enqueue_one_iter(rks_batch *b, int prec) {
     int rc = fock_pass(b, prec, 0);
     if (rc) return rc;
     StageScope sc(b->ctx, b->stream, "scf_step", 0);
-    launch_scf_step(b->d, b->precision == 0, b->max_nbf, b->stream);
+    launch_scf_step(b->d, b->precision == 0, b->max_nbf_small, b->stream);
     return check_launch("scf step");
 }
 
@@ -913,7 +966,7 @@ static int enqueue_recheck_start(rks_batch *b) {
     }
     {
         StageScope sc(b->ctx, s, "scf_guess", 0);
-        launch_scf_guess(b->d, b->max_nbf, 1, s);
+        launch_scf_guess(b->d, b->max_nbf_small, 1, s);
     }
     CUDA_OK(cudaMemcpyAsync(pinw(b), b->recheck_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     return check_launch("recheck start");
@@ -967,7 +1020,7 @@ static int enqueue_final(rks_batch *b) {
     int rc = fock_pass(b, kPrecise, 1);
     if (rc) return rc;
     StageScope sc(b->ctx, b->stream, "scf_final", 0);
-    launch_scf_final(b->d, 1, b->max_nbf, b->stream);
+    launch_scf_final(b->d, 1, b->max_nbf_small, b->stream);
     b->st_valid = false;
     return check_launch("final");
 }
@@ -1131,6 +1184,7 @@ extern "C" int64_t rks_batch_dump(rks_batch *b, int32_t m, int32_t what, void *o
         return bytes;
     }
     case RKS_DUMP_STORE: {
+        if (b->direct) return fail(RKS_EINVAL, "direct SCF keeps no packed store");
         long long n = st.n_elem;
         int64_t bytes = n * 8;
         if (cap < bytes) return RKS_EINVAL;
@@ -1578,7 +1632,8 @@ extern "C" int rks_create(const rks_options *options, rks_ctx **out) {
         (o.precision != RKS_FP64 && o.precision != RKS_MIXED) || o.max_iters <= 0 || o.max_slots <= 0 ||
         !(o.fix_theta >= 0) || (o.guess != RKS_GUESS_SAD && o.guess != RKS_GUESS_CORE) || o.max_cohorts <= 0 ||
         o.iter_precision < 0 || o.iter_precision > 3 || !(o.recheck_err >= 0) || !(o.recheck_fp64_err >= 0) ||
-        o.admit_wait_us < 0 || o.grid_chunks < 0 || o.grid_chunks > 256 || o.jk_chunks < 0 || o.jk_chunks > 256)
+        o.admit_wait_us < 0 || o.grid_chunks < 0 || o.grid_chunks > 256 || o.jk_chunks < 0 || o.jk_chunks > 256 ||
+        o.direct_scf < RKS_DIRECT_NEVER || o.direct_scf > RKS_DIRECT_AUTO)
         return fail(RKS_EINVAL, "bad options");
     int ndev = 0;
     CUDA_OK(cudaGetDeviceCount(&ndev));

@@ -264,7 +264,7 @@ static void launch_gx1(const DevBatch &b, int nchunk, int mode, int skip_tc, int
 template <typename T, typename TA, int BP>
 static void launch_gx(const DevBatch &b, int nchunk, int mode, int skip_tc, int max_nbf, int max_nsh, cudaStream_t s) {
     constexpr int G = 256 / BP;
-    static_assert(RKS_NBF_CAP <= 96, "tile classes cover nbf <= 96");
+    static_assert(RKS_NBF_SMALL <= 96, "tile classes cover nbf <= 96 (larger molecules: large.cu)");
     launch_gx1<T, TA, BP, 4, (64 + G - 1) / G>(b, nchunk, mode, skip_tc, 0, std::min(max_nbf, 64), max_nsh, s);
     if (max_nbf > 64)
         launch_gx1<T, TA, BP, 5, (80 + G - 1) / G>(b, nchunk, mode, skip_tc, 64, std::min(max_nbf, 80), max_nsh, s);

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__((sizeof(TA) == 8 ? JK_WARPS_MAX / 2 : JK_WARPS
     const int m = blockIdx.y;
     const MolDesc md = b.mol[m];
     if (mode == 0 && !b.st[m].active) return;
+    if (md.big) return;  // above RKS_NBF_SMALL: jk_large_kernel
     const int n = md.nbf, nn = n * n;
     const int npair = b.npair[m];
     TA *Ds = (TA *)smem_raw;
@@ -378,7 +379,9 @@ __global__ void __launch_bounds__(256) fix_list_kernel(DevBatch b) {
     if (threadIdx.x < 6) cnt[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int npair = b.npair[m];
+    // molecules above RKS_NBF_SMALL recompute their listed quartets inside
+    // jk_large_kernel: their lists stay empty
+    const int npair = md.big ? 0 : b.npair[m];
     double qmax = 0.0;
     for (int i = lane; i < npair; i += 32) qmax = fmax(qmax, b.kq[md.pair0 + i]);
     for (int o = 16; o > 0; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));

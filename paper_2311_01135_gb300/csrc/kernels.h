@@ -47,7 +47,18 @@ struct TcClasses {
     int off[5], count[5];
 };
 void launch_grid_xc_tc(const DevBatch &b, int nchunk, int acc_fp64, int mode, const TcClasses &cl, cudaStream_t s);
-// Per-molecule FP64 SCF stages.
+// Molecules above RKS_NBF_SMALL (large.cu): J/K with D and the accumulators
+// in global memory.  jk_fin: the mixed path's final-step precision; direct:
+// every molecule, each quartet recomputed (no store).  Returns -1 when the
+// FP64 pair data a direct final step needs is missing.
+int launch_jk_large(const DevBatch &b, int nchunk, int jk_fin, int mode, int direct, cudaStream_t s);
+// The two-pass grid quadrature of those molecules (b.gcf holds the per-point
+// coefficients between the passes); max_nbf / max_nsh over them.  Returns -1
+// when their shared memory would not fit.
+int launch_grid_xc_large(const DevBatch &b, int nchunk, int acc_fp64, int mode, int max_nbf, int max_nsh,
+                         cudaStream_t s);
+// Per-molecule FP64 SCF stages.  max_nbf: the largest basis whose matrices
+// the kernels keep in shared memory; larger molecules use global scratch.
 void launch_scf_init(const DevBatch &b, cudaStream_t s);
 // only_rechecked: guess only for the molecules marked by launch_mark_recheck
 void launch_scf_guess(const DevBatch &b, int max_nbf, int only_rechecked, cudaStream_t s);

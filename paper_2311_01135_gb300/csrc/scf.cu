@@ -31,7 +31,11 @@ struct ScfSmem {
 
 // A and V are sized for the batch's largest basis nmax (not the compiled
 // cap), so that two or three molecules' blocks share an SM: the step is
-// latency-bound FP64 work and gains from the extra resident warps.
+// latency-bound FP64 work and gains from the extra resident warps.  A
+// molecule above nmax (a basis above RKS_NBF_SMALL: 2 n^2 doubles exceed
+// shared memory) keeps A and V in its global scratch matrices M_TMP2 and
+// M_TMP3 instead (scf_big_scratch); every caller leaves those two free while
+// it diagonalises.
 __device__ inline ScfSmem scf_smem(unsigned char *raw, int nmax) {
     ScfSmem s;
     double *d = (double *)raw;
@@ -42,6 +46,13 @@ __device__ inline ScfSmem scf_smem(unsigned char *raw, int nmax) {
     s.cs = s.red + 64;
     s.perm = (int *)(s.cs + 2 * RKS_NBF_CAP + 8);
     return s;
+}
+__device__ inline void scf_big_scratch(ScfSmem &sm, const DevBatch &b, const MolDesc &md, int nmax) {
+    if (md.nbf > nmax) {
+        const long long nn = nbf2(md.nbf);
+        sm.A = b.mat + md.mat0 + (long long)M_TMP2 * nn;
+        sm.V = b.mat + md.mat0 + (long long)M_TMP3 * nn;
+    }
 }
 static size_t scf_smem_bytes(int nmax) {
     return sizeof(double) * (2 * (size_t)nmax * nmax + RKS_NBF_CAP + 64 + 2 * RKS_NBF_CAP + 8) +
@@ -116,6 +127,7 @@ __global__ void scf_guess_kernel(DevBatch b, int nmax, int only_rechecked) {
     const int m = blockIdx.x;
     if (only_rechecked && !b.st[m].rechecked) return;
     const MolDesc md = b.mol[m];
+    scf_big_scratch(sm, b, md, nmax);
     const int n = md.nbf, nn = n * n;
     double *S = b.mat + md.mat0 + (long long)M_S * nn;
     double *X = b.mat + md.mat0 + (long long)M_X * nn;
@@ -289,6 +301,7 @@ __global__ void scf_step_kernel(DevBatch b, const TA *accbase, int nmax) {
     const MolDesc &md = b.mol[m];
     MolState &st = b.st[m];
     if (!st.active) return;
+    scf_big_scratch(sm, b, md, nmax);
     const int n = md.nbf, nn = n * n;
     double *S = b.mat + md.mat0 + (long long)M_S * nn;
     double *X = b.mat + md.mat0 + (long long)M_X * nn;
@@ -475,6 +488,7 @@ __global__ void scf_final_kernel(DevBatch b, const TA *accbase, int nmax) {
     const int m = blockIdx.x;
     const MolDesc &md = b.mol[m];
     MolState &st = b.st[m];
+    scf_big_scratch(sm, b, md, nmax);
     const int n = md.nbf, nn = n * n;
     double *X = b.mat + md.mat0 + (long long)M_X * nn;
     double *D = b.mat + md.mat0 + (long long)M_D * nn;

@@ -1,0 +1,233 @@
+"""Replica dispatcher: one batched RKS engine per GPU, on any number of hosts.
+
+Molecules are independent (the SCF of Section 3.1 has no exchange step
+between molecules), so several GPUs, on one box or on many, run as
+independent replicas with no collective.  A dispatcher process holds the
+molecule list; each worker process owns one GPU (one rks context) and pulls
+work from the dispatcher over TCP:
+
+* order: molecules go out largest estimated cost first (cost ~ atoms x nbf^2,
+  the grid quadrature's scaling), so the last chunks are the cheapest and the
+  replicas finish close together (longest-processing-time-first);
+* flow: a worker keeps two chunks of `chunk` molecules in flight on its GPU
+  (the next one queued while the current one runs) and asks for another as
+  each finishes, so faster GPUs simply pull more;
+* failure: a worker whose connection drops, or that sends nothing for
+  `timeout_s` while it holds work, is dropped and its molecules go back to
+  the front of the queue for the others (a result is kept once, the first
+  time it arrives).
+
+Transport is multiprocessing.connection (TCP, HMAC challenge with a shared
+auth key); messages are pickled tuples:
+  worker -> dispatcher  ("want", k)                   ask for up to k molecules
+                        ("done", [(i, result), ...])  results of molecules i
+  dispatcher -> worker  ("work", [(i, Z, xyz), ...])
+                        ("stop",)
+
+    # dispatcher host
+    d = Dispatcher(("0.0.0.0", 7788), authkey=b"...", n_workers=8)
+    results = d.run(mols)            # list of result dicts, input order
+    # each GPU (any host)
+    python -m paper_2311_01135_gb300.dispatch --connect HOST:7788 --device 0
+
+This module is host code only: every molecule a worker runs goes through the
+library's serving calls (rks_submit_batch / rks_wait / rks_result).
+"""
+from __future__ import annotations
+
+import argparse
+import collections
+import os
+import threading
+import time
+from multiprocessing.connection import Client, Listener, wait
+
+import numpy as np
+
+
+def cost_estimate(Z):
+    """Relative cost of one molecule: atoms x nbf^2 (grid points scale with
+    atoms, the density and V_xc contractions with nbf^2 per point)."""
+    Z = np.asarray(Z)
+    nbf = int(np.sum(np.where(Z > 1, 5, 1)))
+    return len(Z) * nbf * nbf
+
+
+class Dispatcher:
+    """Serves molecules to `n_workers` replicas; see the module docstring."""
+
+    def __init__(self, address, authkey, n_workers, chunk=64, timeout_s=600.0):
+        self.listener = Listener(address, authkey=authkey)
+        self.address = self.listener.address
+        self.n_workers = n_workers
+        self.chunk = chunk
+        self.timeout_s = timeout_s
+        self._new = collections.deque()
+        self._lock = threading.Lock()
+        self._accepting = True
+        self._acceptor = threading.Thread(target=self._accept, daemon=True)
+        self._acceptor.start()
+        self.stats = collections.Counter()
+
+    def _accept(self):
+        while self._accepting:
+            try:
+                c = self.listener.accept()
+            except Exception:  # noqa: BLE001 - listener closed, or a failed handshake
+                if not self._accepting:
+                    return
+                continue
+            with self._lock:
+                self._new.append(c)
+
+    def run(self, mols):
+        """Every molecule of mols [(Z, xyz), ...] through the replicas; returns
+        the results in input order."""
+        self._cost = [cost_estimate(Z) for Z, _ in mols]
+        order = sorted(range(len(mols)), key=lambda i: -self._cost[i])
+        queue = collections.deque(order)
+        results = [None] * len(mols)
+        left = len(mols)
+        held = {}      # conn -> set of molecule ids it holds
+        seen = {}      # conn -> time of its last message
+        while left > 0:
+            with self._lock:
+                while self._new:
+                    c = self._new.popleft()
+                    held[c] = set()
+                    seen[c] = time.monotonic()
+            if not held:
+                time.sleep(0.01)
+                continue
+            for c in wait(list(held), timeout=0.2):
+                try:
+                    msg = c.recv()
+                except (EOFError, OSError):
+                    self._drop(c, held, seen, queue, results)
+                    continue
+                seen[c] = time.monotonic()
+                if msg[0] == "done":
+                    for i, r in msg[1]:
+                        held[c].discard(i)
+                        if results[i] is None:
+                            results[i] = r
+                            left -= 1
+                            self.stats["done"] += 1
+                elif msg[0] == "want":
+                    k = min(int(msg[1]), self.chunk)
+                    out = []
+                    while queue and len(out) < k:
+                        i = queue.popleft()
+                        if results[i] is None:
+                            out.append(i)
+                    held[c].update(out)
+                    try:
+                        c.send(("work", [(i, np.asarray(mols[i][0], np.int32), np.asarray(mols[i][1], float))
+                                         for i in out]))
+                    except (EOFError, OSError):
+                        self._drop(c, held, seen, queue, results)
+            now = time.monotonic()
+            for c in [c for c in held if held[c] and now - seen[c] > self.timeout_s]:
+                self._drop(c, held, seen, queue, results)
+        for c in list(held):
+            try:
+                c.send(("stop",))
+            except (EOFError, OSError):
+                pass
+        return results
+
+    def _drop(self, c, held, seen, queue, results):
+        """A worker is gone: its unfinished molecules go back to the front."""
+        back = sorted((i for i in held.pop(c, ()) if results[i] is None), key=lambda i: -self._cost[i])
+        queue.extendleft(reversed(back))
+        seen.pop(c, None)
+        self.stats["dropped_workers"] += 1
+        self.stats["requeued"] += len(back)
+        try:
+            c.close()
+        except OSError:
+            pass
+
+    def close(self):
+        self._accepting = False
+        try:
+            self.listener.close()
+        except OSError:
+            pass
+
+
+class EngineRunner:
+    """A worker's engine: one rks context on one GPU, molecules through the
+    serving calls (rks_submit_batch / rks_wait / rks_result).  submit()
+    queues a chunk and returns at once; collect() waits for its results."""
+
+    def __init__(self, device=0, **options):
+        import paper_2311_01135_gb300 as g
+        self.ctx = g.Context(device=device, **options)
+
+    def submit(self, jobs):
+        return [i for i, _, _ in jobs], self.ctx.submit_many([(Z, xyz) for _, Z, xyz in jobs])
+
+    def collect(self, handle):
+        ids, tickets = handle
+        out = []
+        for i, t in zip(ids, tickets):
+            self.ctx.wait(t, 3600)
+            out.append((i, self.ctx.result(t)))
+        return out
+
+    def close(self):
+        self.ctx.close()
+
+
+def worker_loop(address, authkey, engine, chunk=64, depth=2):
+    """Pull molecules from the dispatcher at `address` until it says stop,
+    with up to `depth` chunks in flight on the engine (engine.submit(jobs)
+    -> handle, engine.collect(handle) -> [(i, result), ...])."""
+    conn = Client(address, authkey=authkey)
+    pending = collections.deque()
+    try:
+        while True:
+            if len(pending) < depth:
+                conn.send(("want", chunk))
+                msg = conn.recv()
+                if msg[0] == "stop":
+                    return
+                if msg[1]:
+                    pending.append(engine.submit(msg[1]))
+                    continue
+                if not pending:
+                    # nothing queued now (others hold the rest): ask again shortly
+                    time.sleep(0.05)
+                    continue
+            conn.send(("done", engine.collect(pending.popleft())))
+    except (EOFError, OSError):
+        return
+    finally:
+        conn.close()
+
+
+def main():
+    ap = argparse.ArgumentParser(description="RKS replica worker: pulls molecules from a dispatcher")
+    ap.add_argument("--connect", required=True, help="dispatcher HOST:PORT")
+    ap.add_argument("--device", type=int, default=int(os.environ.get("LOCAL_RANK", "0")))
+    ap.add_argument("--authkey-env", default="RKS_DISPATCH_KEY")
+    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--fixed-iters", type=int, default=20)
+    ap.add_argument("--chunk", type=int, default=64)
+    a = ap.parse_args()
+    host, port = a.connect.rsplit(":", 1)
+    key = os.environ.get(a.authkey_env, "").encode()
+    if not key:
+        raise SystemExit(f"set {a.authkey_env} to the dispatcher's auth key")
+    import paper_2311_01135_gb300 as g
+    eng = EngineRunner(device=a.device, precision=g.RKS_MIXED if a.precision == "mixed" else g.RKS_FP64,
+                       fixed_iters=a.fixed_iters)
+    try:
+        worker_loop((host, int(port)), key, eng, chunk=a.chunk)
+    finally:
+        eng.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -82,7 +82,24 @@ def test_options_default(L):
     assert o.guess == g.RKS_GUESS_SAD and o.fix_theta == 0.1 and o.grid_tc == 1
     assert o.max_cohorts == 4 and o.admit_wait_us == 20000
     assert o.iter_precision == 0 and o.recheck_err == 1e-4 and o.recheck_fp64_err == 3e-4
+    assert o.direct_scf == g.RKS_DIRECT_NEVER
     assert L.rks_options_default(None) == g.RKS_EINVAL
+
+
+def test_header_constants_match_binding():
+    src = open(HDR).read()
+    for name in ("RKS_MAX_NBF", "RKS_DIRECT_NEVER", "RKS_DIRECT_ALWAYS", "RKS_DIRECT_AUTO",
+                 "RKS_ITER_JK_FINAL", "RKS_ITER_GRID_FINAL"):
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)", src)
+        assert m and int(m.group(1)) == getattr(g, name), name
+
+
+def test_larger_workload_fits_the_basis_cap(L):
+    """The 20-30-heavy-atom workload (seed 4) stays within RKS_MAX_NBF, and
+    spans the global-memory kernels' range (above 96 functions)."""
+    import molgen
+    nbf = [g.rks_nbf(Z) for Z, _ in molgen.batch(4, 256, 20, 30)]
+    assert min(nbf) > 96 and max(nbf) <= g.RKS_MAX_NBF
 
 
 def test_nbf_and_validation(L):
@@ -116,6 +133,9 @@ def test_bad_options_rejected_before_any_device_call(L):
     assert L.rks_create(ctypes.byref(o), ctypes.byref(h)) == g.RKS_EINVAL
     L.rks_options_default(ctypes.byref(o))
     o.max_cohorts = 0
+    assert L.rks_create(ctypes.byref(o), ctypes.byref(h)) == g.RKS_EINVAL
+    L.rks_options_default(ctypes.byref(o))
+    o.direct_scf = 3
     assert L.rks_create(ctypes.byref(o), ctypes.byref(h)) == g.RKS_EINVAL
 
 

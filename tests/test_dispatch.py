@@ -1,0 +1,111 @@
+"""The replica dispatcher (paper_2311_01135_gb300/dispatch.py) on the CPU:
+worker processes on this host stand in for GPUs on other boxes, with a
+stand-in engine that answers each molecule with a value computed from its
+atoms (the real engine is the library's serving API, covered by the GPU
+tests).  Checked: every molecule is answered once, in input order, by the
+replica that ran it; molecules go out largest estimated cost first; a worker
+that dies with work in hand, or stops answering, loses that work to the
+others and the run still completes."""
+import multiprocessing as mp
+import os
+import time
+
+import numpy as np
+import pytest
+
+import molgen
+from paper_2311_01135_gb300 import dispatch
+
+KEY = b"test-dispatch-key"
+
+
+class FakeEngine:
+    """Answers molecule i with a value of its atoms; `die_after` chunks
+    submitted it exits the process, `hang_after` it stops answering."""
+
+    def __init__(self, die_after=None, hang_after=None):
+        self.n = 0
+        self.die_after = die_after
+        self.hang_after = hang_after
+
+    def submit(self, jobs):
+        self.n += 1
+        if self.die_after is not None and self.n > self.die_after:
+            os._exit(3)
+        return [(i, {"E": -float(np.sum(Z)) - 1e-3 * float(np.sum(xyz)), "pid": os.getpid()}) for i, Z, xyz in jobs]
+
+    def collect(self, handle):
+        if self.hang_after is not None and self.n > self.hang_after:
+            time.sleep(120)
+        time.sleep(0.01)
+        return handle
+
+
+def _worker(address, die_after=None, hang_after=None, chunk=4):
+    dispatch.worker_loop(address, KEY, FakeEngine(die_after, hang_after), chunk=chunk)
+
+
+def _expected(mol):
+    Z, xyz = mol
+    return -float(np.sum(Z)) - 1e-3 * float(np.sum(xyz))
+
+
+@pytest.fixture()
+def mols():
+    return molgen.batch(5, 40, 1, 6)
+
+
+def _run(mols, workers, timeout_s=60.0):
+    d = dispatch.Dispatcher(("127.0.0.1", 0), KEY, n_workers=len(workers), chunk=4, timeout_s=timeout_s)
+    ctx = mp.get_context("spawn")
+    ps = [ctx.Process(target=_worker, args=(d.address,) + w) for w in workers]
+    for p in ps:
+        p.start()
+    try:
+        res = d.run(mols)
+    finally:
+        d.close()
+        for p in ps:
+            p.join(timeout=20)
+            if p.is_alive():
+                p.kill()
+                p.join()
+    return d, res, ps
+
+
+def test_two_workers_answer_every_molecule_once(mols):
+    d, res, ps = _run(mols, [(), ()])
+    assert all(r is not None for r in res)
+    for m, r in zip(mols, res):
+        assert r["E"] == _expected(m)
+    assert d.stats["done"] == len(mols) and d.stats["dropped_workers"] == 0
+    assert len({r["pid"] for r in res}) == 2  # both replicas took work
+    assert all(p.exitcode == 0 for p in ps)
+
+
+def test_largest_first_order():
+    costs = [dispatch.cost_estimate(Z) for Z, _ in molgen.batch(5, 40, 1, 6)]
+    order = sorted(range(40), key=lambda i: -costs[i])
+    assert all(costs[a] >= costs[b] for a, b in zip(order, order[1:]))
+    # water: 3 atoms x 7^2; benzene-sized C6H6: 12 atoms x 36^2
+    assert dispatch.cost_estimate([8, 1, 1]) == 3 * 49
+    assert dispatch.cost_estimate([6] * 6 + [1] * 6) == 12 * 36 * 36
+
+
+def test_worker_that_dies_loses_its_work_to_the_other(mols):
+    d, res, ps = _run(mols, [(1, None), ()])
+    assert all(r is not None for r in res)
+    for m, r in zip(mols, res):
+        assert r["E"] == _expected(m)
+    assert d.stats["dropped_workers"] == 1 and d.stats["requeued"] >= 1
+    assert sorted(p.exitcode for p in ps) == [0, 3]
+
+
+def test_silent_worker_is_dropped_after_the_timeout(mols):
+    t0 = time.monotonic()
+    d, res, ps = _run(mols, [(None, 1), ()], timeout_s=2.0)
+    assert all(r is not None for r in res)
+    for m, r in zip(mols, res):
+        assert r["E"] == _expected(m)
+    assert d.stats["dropped_workers"] == 1
+    assert time.monotonic() - t0 < 60
