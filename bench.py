@@ -421,22 +421,28 @@ def large_main(args):
         ck = clocks.stop()
         probes = measured_peaks(g, ctx)
         sub = mols[:args.large_prof_n]
-        ctx.profile(True)
-        with g.Batch(ctx, sub) as Bp:
-            Bp.setup()
-            Bp.run()
-            Bp.sync()
-            sc = [Bp.dump(m, g.RKS_DUMP_SCALARS) for m in range(len(sub))]
-        prof = ctx.profile_read()
-        ctx.profile(False)
+        sc, prof = [], {}
+        if sub:
+            ctx.profile(True)
+            with g.Batch(ctx, sub) as Bp:
+                Bp.setup()
+                Bp.run()
+                Bp.sync()
+                sc = [Bp.dump(m, g.RKS_DUMP_SCALARS) for m in range(len(sub))]
+            prof = ctx.profile_read()
+            ctx.profile(False)
     n64 = min(args.large_fp64_n, len(mols))
-    with g.Context(precision=g.RKS_FP64, fixed_iters=20) as c64:
-        timed(c64, mols[:1])
-        ms64, r64 = timed(c64, mols[:n64])
+    ms64, r64 = None, []
+    if n64 > 0:
+        with g.Context(precision=g.RKS_FP64, fixed_iters=20) as c64:
+            timed(c64, mols[:1])
+            ms64, r64 = timed(c64, mols[:n64])
     nd = min(args.large_direct_n, len(mols))
-    with g.Context(precision=g.RKS_MIXED, direct_scf=g.RKS_DIRECT_ALWAYS, **opt) as cd:
-        msd, rd = timed(cd, mols[:nd])
-    gate = gate_report(rmx[:n64], r64)
+    msd, rd = None, []
+    if nd > 0:
+        with g.Context(precision=g.RKS_MIXED, direct_scf=g.RKS_DIRECT_ALWAYS, **opt) as cd:
+            msd, rd = timed(cd, mols[:nd])
+    gate = gate_report(rmx[:n64], r64) if n64 > 0 else None
     ddir = [abs(a["E"] - b["E"]) for a, b in zip(rd, rmx[:nd])]
     # rooflines of the two iteration kernels, from the profiled sample
     pk = peaks()
@@ -466,9 +472,9 @@ def large_main(args):
                        "nbf": {"min": int(nbf.min()), "mean": float(nbf.mean()), "max": int(nbf.max())}},
             "status_not_ok": sum(1 for r in rmx if r["status"] != "ok"),
             "clocks": ck, "gate_vs_fp64_sample": gate,
-            "fp64_gpu": {"value": n64 / (ms64 / 1e3), "unit": "molecules/s", "nmol": n64},
+            "fp64_gpu": {"value": n64 / (ms64 / 1e3), "unit": "molecules/s", "nmol": n64} if ms64 else None,
             "direct_scf": {"value": nd / (msd / 1e3), "unit": "molecules/s", "nmol": nd,
-                           "max_abs_dE_vs_stored": float(max(ddir)) if ddir else None},
+                           "max_abs_dE_vs_stored": float(max(ddir)) if ddir else None} if msd else None,
             "roofline_large": roof, "peaks_probed_tflops": probes,
             "stages_ms_sample": {k: round(v["ms"], 3) for k, v in prof.items()}, "sample_n": len(sub)}
     print(json.dumps(line), flush=True)

@@ -123,9 +123,8 @@ def test_large_alone_equals_in_mix(gold):
     one batch; fixed-point sums make the results bit-identical."""
     Zw, xw = molgen.h2o()
     mols = [(gold["Z"], gold["xyz"]), (Zw, xw)]
-    opt = dict(precision=g.RKS_MIXED, fixed_iters=20)
-    alone = [_run(Z, x, **opt) for Z, x in mols]
-    with g.Context(**opt) as c, g.Batch(c, mols) as B:
+    alone = [_run(Z, x, precision=g.RKS_MIXED) for Z, x in mols]
+    with g.Context(precision=g.RKS_MIXED, fixed_iters=20) as c, g.Batch(c, mols) as B:
         B.run()
         B.sync()
         mix = [B.result(k) for k in range(2)]
