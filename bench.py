@@ -387,10 +387,13 @@ def large_workload(nmol, seed=4):
 def large_main(args):
     """The 20-30-heavy-atom workload: every stage on the global-memory kernels
     (J/K, two-pass grid quadrature, SCF steps with global Jacobi scratch).
-    Mixed precision, 20 iterations + recheck + final step on --large-n
-    molecules (CUDA events around setup + run on the batch's stream); stage
+    Mixed precision on --large-n molecules (CUDA events around setup + run on
+    the batch's stream), under the converge protocol (default: each molecule
+    iterates until |dE_k| < 1e-6 Ha and its DIIS error < 1e-5, then takes the
+    final step) or the fixed one (20 iterations + recheck + final step); stage
     times of a profiled run on the first --large-prof-n; the FP64 path on the
-    first --large-fp64-n (the gate's reference, itself pinned to the oracle by
+    first --large-fp64-n (the gate's reference, converged to 1e-8 Ha / 1e-6
+    under the converge protocol; pinned to the oracle by
     tests/test_gpu_large.py); direct SCF (every quartet recomputed inside J/K,
     no packed store) on the first --large-direct-n."""
     import torch
@@ -398,7 +401,12 @@ def large_main(args):
     g.build()
     mols = large_workload(args.large_n)
     nbf = np.array([g.rks_nbf(Z) for Z, _ in mols])
-    opt = dict(fixed_iters=20, recheck_err=RECHECK_ERR, recheck_fp64_err=RECHECK_FP64_ERR)
+    if args.large_protocol == "converge":
+        opt = dict(fixed_iters=0, max_iters=100, e_tol=1e-6, err_tol=1e-5)
+        opt64 = dict(fixed_iters=0, max_iters=100, e_tol=1e-8, err_tol=1e-6)
+    else:
+        opt = dict(fixed_iters=20, recheck_err=RECHECK_ERR, recheck_fp64_err=RECHECK_FP64_ERR)
+        opt64 = dict(fixed_iters=20)
 
     def timed(ctx, sub):
         stream = torch.cuda.ExternalStream(ctx.stream())
@@ -434,8 +442,7 @@ def large_main(args):
     n64 = min(args.large_fp64_n, len(mols))
     ms64, r64 = None, []
     if n64 > 0:
-        with g.Context(precision=g.RKS_FP64, fixed_iters=20) as c64:
-            timed(c64, mols[:1])
+        with g.Context(precision=g.RKS_FP64, **opt64) as c64:
             ms64, r64 = timed(c64, mols[:n64])
     nd = min(args.large_direct_n, len(mols))
     msd, rd = None, []
@@ -443,6 +450,7 @@ def large_main(args):
         with g.Context(precision=g.RKS_MIXED, direct_scf=g.RKS_DIRECT_ALWAYS, **opt) as cd:
             msd, rd = timed(cd, mols[:nd])
     gate = gate_report(rmx[:n64], r64) if n64 > 0 else None
+    it = np.array([r["iters"] for r in rmx])
     ddir = [abs(a["E"] - b["E"]) for a, b in zip(rd, rmx[:nd])]
     # rooflines of the two iteration kernels, from the profiled sample
     pk = peaks()
@@ -468,9 +476,15 @@ def large_main(args):
             "unit": "molecules/s", "n_gpus": 1, "ms": ms, "higher_is_better": True, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": f"{len(mols)} molecules, 20-30 heavy atoms (C/N/O/F+H), B3LYP(VWN5)/STO-3G, "
-                                   "mixed precision, 20 SCF iterations + recheck + final step", "seed": 4,
+                                   "mixed precision, " + ("converge protocol (|dE_k| < 1e-6 Ha, DIIS error < 1e-5, "
+                                                          "at most 100 iterations) + final step"
+                                                          if args.large_protocol == "converge" else
+                                                          "20 SCF iterations + recheck + final step"),
+                       "seed": 4, "protocol": args.large_protocol,
                        "nbf": {"min": int(nbf.min()), "mean": float(nbf.mean()), "max": int(nbf.max())}},
             "status_not_ok": sum(1 for r in rmx if r["status"] != "ok"),
+            "iterations": {"min": int(it.min()), "p50": float(np.median(it)), "max": int(it.max()),
+                           "mean": float(it.mean())},
             "clocks": ck, "gate_vs_fp64_sample": gate,
             "fp64_gpu": {"value": n64 / (ms64 / 1e3), "unit": "molecules/s", "nmol": n64} if ms64 else None,
             "direct_scf": {"value": nd / (msd / 1e3), "unit": "molecules/s", "nmol": nd,
@@ -674,6 +688,7 @@ def main():
     ap.add_argument("--large-fp64-n", type=int, default=4)
     ap.add_argument("--large-direct-n", type=int, default=8)
     ap.add_argument("--large-prof-n", type=int, default=16)
+    ap.add_argument("--large-protocol", choices=("converge", "fixed"), default="converge")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 1)
     if args.impl == "reference":

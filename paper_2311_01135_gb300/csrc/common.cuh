@@ -169,6 +169,8 @@ struct DevBatch {
     void *gcf;              // molecules above RKS_NBF_SMALL: per grid point the four coefficients of
                             // X (w v_rho / 2, 2 w v_sigma grad rho), [pts0 + p][4] (T), else null
     int direct;             // 1: no packed store; J/K recompute the quartets every pass (direct SCF)
+    void *gdt;              // mixed path, molecules above RKS_NBF_SMALL: D in FP32 for the grid
+                            // pass, n^2 floats at acc0 (converted once per pass), else null
     // Boys tables
     const double *boys64;
     const float *boys32;

@@ -510,6 +510,7 @@ static size_t mol_bytes(const rks_options &o, int na, const int32_t *Z) {
     if (!direct) b += (size_t)((store_cap(ns, np) + 3) & ~3LL) * esz;
     b += (size_t)nblk * RKS_PTS_BLOCK * 4 * esz + (size_t)nblk * 4;
     if (nbf > RKS_NBF_SMALL) b += (size_t)nblk * RKS_PTS_BLOCK * 4 * esz;  // X coefficients between the grid passes
+    if (nbf > RKS_NBF_SMALL && o.precision == RKS_MIXED) b += (size_t)nbf * nbf * 3 * 4;  // FP32 copy of D
     if (o.precision == RKS_MIXED) b += (size_t)nblk * 16;  // grid block masks
     b += (size_t)nbf * nbf * (M_COUNT * 8 + 3 * 8);
     return b;
@@ -679,7 +680,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     const bool want64 = o.precision == RKS_MIXED && (o.fix_theta > 0 || b->direct);  // FP64 pair data
     const bool want_fix = o.precision == RKS_MIXED && o.fix_theta > 0 && !b->direct;   // FP64 recompute lists
     int rc = 0;
-    void *gcf = nullptr;
+    void *gcf = nullptr, *gdt = nullptr;
     MolDesc *dmol; MolState *dst; int *dZ, *dsa, *dsl, *dsao, *dcm, *dnp, *drnq; double *dax, *dsx, *dse, *dsc, *dcq, *dkq;
     int2 *dcand, *dkp; long long *droff; void *store; void *gx, *gy, *gz, *gw; double *mat, *accd;
     void *pairprim, *pairprim64 = nullptr;
@@ -697,6 +698,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
         (want_fix && ((rc = dalloc(b, &fixlist, (size_t)nmol * 6 * RKS_FIX_CAP)) ||
                       (rc = dalloc(b, &fixcount, (size_t)nmol * 6)))) ||
         (b->n_big > 0 && (rc = dalloc(b, (unsigned char **)&gcf, pts_off * 4 * esz))) ||
+        (b->n_big > 0 && o.precision == RKS_MIXED && (rc = dalloc(b, (float **)&gdt, acc_off))) ||
         (rc = dalloc(b, (unsigned char **)&gx, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gy, pts_off * esz)) ||
         (rc = dalloc(b, (unsigned char **)&gz, pts_off * esz)) || (rc = dalloc(b, (unsigned char **)&gw, pts_off * esz)) ||
         (rc = dalloc(b, &mat, mat_off)) || (rc = dalloc(b, &accd, acc_off)) ||
@@ -720,6 +722,7 @@ static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, i
     d.fix_theta = o.fix_theta;
     d.gx = gx; d.gy = gy; d.gz = gz; d.gw = gw; d.mat = mat; d.accd = accd; d.accx = (Fx *)accd;  // one buffer, two views
     d.gcf = gcf;
+    d.gdt = gdt;
     cudaStream_t s = b->stream;
 #define UP(dst_, src_)                                                                                      \
     if (!(src_).empty()) {                                                                                  \

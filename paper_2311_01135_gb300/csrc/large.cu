@@ -308,13 +308,29 @@ __device__ __forceinline__ void lg_radial(const LgShells<T> &sh, int s, T dx, T 
     }
 }
 
+// D in FP32 for the mixed path's grid pass, once per pass (b.gdt at acc0):
+// the density pass then streams FP32 tiles, with no FP64-to-FP32 conversion
+// (a slow FP64-pipe instruction on this GPU) in its inner loop.
+__global__ void d_to_f32_kernel(DevBatch b, int mode) {
+    const int m = blockIdx.y;
+    const MolDesc md = b.mol[m];
+    if (mode == 0 && !b.st[m].active) return;
+    if (md.nbf <= RKS_NBF_SMALL) return;
+    const long long nn = nbf2(md.nbf);
+    const double *D = b.mat + md.mat0 + (long long)M_D * nn;
+    float *dst = (float *)b.gdt + md.acc0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (float)D[i];
+}
+
 // Pass 1.  grid (nchunk, nmol), 256 threads; per sub-block of BP points:
 // phi and grad phi of every AO into shared memory, T = Phi D with G = 256/BP
 // threads per point (thread g takes the columns nu = g, g + G, ...; D comes
-// through shared memory DT rows at a time), rho and grad rho, the functional
-// (three parts on three warps, as in the shared-memory kernel), and the
-// coefficients (w v_rho / 2, 2 w v_sigma grad rho) of X for pass 2.
-#define LG_DT 8
+// through shared memory DT rows at a time, in T: the FP64 matrix itself, or
+// its FP32 copy on the mixed path), rho and grad rho, the functional (three
+// parts on three warps, as in the shared-memory kernel), and the coefficients
+// (w v_rho / 2, 2 w v_sigma grad rho) of X for pass 2.
+#define LG_DT 32
 template <typename T, int BP, int NV>
 __global__ void __launch_bounds__(256, 1) grid_rho_large_kernel(DevBatch b, int nchunk, int mode, T *cfg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -331,7 +347,9 @@ __global__ void __launch_bounds__(256, 1) grid_rho_large_kernel(DevBatch b, int 
     T *xv = rr + 4 * BP;              // [6][BP]
     LgShells<T> sh = lg_shells<T>(xv + 6 * BP, nsh);
     lg_load_shells<T>(b, md, sh);
-    const double *D = b.mat + md.mat0 + (long long)M_D * n * n;
+    const T *D;
+    if constexpr (sizeof(T) == 8) D = (const T *)(b.mat + md.mat0 + (long long)M_D * n * n);
+    else D = (const T *)b.gdt + md.acc0;
     const T *gx = (const T *)b.gx + md.pts0, *gy = (const T *)b.gy + md.pts0;
     const T *gz = (const T *)b.gz + md.pts0, *gw = (const T *)b.gw + md.pts0;
     T *cf = cfg + 4 * md.pts0;
@@ -382,7 +400,7 @@ __global__ void __launch_bounds__(256, 1) grid_rho_large_kernel(DevBatch b, int 
         for (int mt = 0; mt < n; mt += LG_DT) {
             const int rows = min(LG_DT, n - mt);
             __syncthreads();  // the previous tile is consumed (first pass: phi is written)
-            for (int i = t; i < rows * n; i += blockDim.x) Dt[i] = (T)D[(long long)mt * n + i];
+            for (int i = t; i < rows * n; i += blockDim.x) Dt[i] = D[(long long)mt * n + i];
             __syncthreads();
             for (int k = 0; k < rows; k++) {
                 const T f = phi[(mt + k) * BP + p];
@@ -580,6 +598,10 @@ static int launch_lg(const DevBatch &b, int nchunk, int mode, int max_nbf, int m
     const size_t sm2 = sizeof(T) * ((size_t)BPV * ((16 * TC) | 1) + 16ull * TR * BPV + 8ull * BPV) +
                        lg_shell_bytes<T>(max_nsh) + 64;
     if (sm1 > 232448 || sm2 > 232448) return -1;
+    if constexpr (sizeof(T) == 4) {
+        if (!b.gdt) return -1;
+        d_to_f32_kernel<<<dim3(32, b.nmol), 256, 0, s>>>(b, mode);
+    }
     cudaFuncSetAttribute(grid_rho_large_kernel<T, BPR, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     grid_rho_large_kernel<T, BPR, NV><<<dim3(nchunk, b.nmol), 256, sm1, s>>>(b, nchunk, mode, (T *)cfg);
     cudaFuncSetAttribute(grid_vxc_large_kernel<T, TA, BPV, TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
