@@ -185,6 +185,17 @@ int rks_options_default(rks_options *o);
  * negative RKS_EINVAL for an unsupported element or natom <= 0. */
 int rks_nbf(int32_t natom, const int32_t *Z);
 
+/* Device bytes one molecule adds to a batch under `options` (NULL: the
+ * defaults), no context or device needed: its packed two-electron store (the
+ * unscreened capacity of Section 3.2's 8-fold-symmetric I^2e; none under
+ * RKS_DIRECT_ALWAYS), grid, FP64 matrices, accumulators and state.  The
+ * paper's memory limit per molecule (Section 5: N <= 70 within 940 MB of
+ * on-chip memory) becomes here the admission figure the serving worker holds
+ * against hbm_budget_bytes.  Z: natom atomic numbers (read only).  Returns the
+ * byte count, or RKS_EINVAL for natom <= 0, a null Z, an unsupported element
+ * or a basis above RKS_MAX_NBF. */
+int64_t rks_mol_bytes(const rks_options *options, int32_t natom, const int32_t *Z);
+
 /* The tensor-core grid kernel's column plan of a molecule (no context
  * needed; mixed path, Section 3.1 V_xc on the grid).  The kernel's threads own
  * AO columns in four quarters of NQ = 4, 8, 12, 16 or 20 (padded basis 4 NQ);

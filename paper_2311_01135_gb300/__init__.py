@@ -65,6 +65,7 @@ _P = ctypes.c_void_p
 _SIGS = {
     "rks_options_default": (ctypes.c_int, [ctypes.POINTER(rks_options)]),
     "rks_nbf": (ctypes.c_int, [ctypes.c_int32, _P]),
+    "rks_mol_bytes": (ctypes.c_int64, [ctypes.POINTER(rks_options), ctypes.c_int32, _P]),
     "rks_tc_plan": (ctypes.c_int, [ctypes.c_int32, _P, _P]),
     "rks_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "rks_last_error": (ctypes.c_char_p, [_P]),
@@ -144,6 +145,13 @@ def options(**kw):
 def rks_nbf(Z):
     Z = np.ascontiguousarray(Z, np.int32)
     return _chk(lib().rks_nbf(len(Z), _ptr(Z)), "rks_nbf")
+
+
+def rks_mol_bytes(Z, **opts):
+    """Device bytes the molecule adds to a batch under these options."""
+    Z = np.ascontiguousarray(Z, np.int32)
+    o = options(**opts)
+    return _chk(lib().rks_mol_bytes(ctypes.byref(o), len(Z), _ptr(Z)), "rks_mol_bytes")
 
 
 RKS_TC_PLAN_INTS = 100

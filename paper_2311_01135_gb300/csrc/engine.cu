@@ -516,6 +516,17 @@ static size_t mol_bytes(const rks_options &o, int na, const int32_t *Z) {
     return b;
 }
 
+extern "C" int64_t rks_mol_bytes(const rks_options *options, int32_t natom, const int32_t *Z) {
+    if (natom <= 0 || !Z) return fail(RKS_EINVAL, "natom <= 0 or null Z");
+    std::call_once(g_basis_once, init_basis);
+    rks_options o;
+    if (options) o = *options; else rks_options_default(&o);
+    const int nbf = rks_nbf(natom, Z);
+    if (nbf < 0) return nbf;
+    if (nbf > RKS_NBF_CAP) return fail(RKS_EINVAL, "nbf " + std::to_string(nbf) + " above the compiled maximum");
+    return (int64_t)mol_bytes(o, natom, Z);
+}
+
 // precision: RKS_FP64 / RKS_MIXED, or -1 for the context's; bohr: coordinates
 // are already in bohr (the FP64 redo of a batch's molecules).
 static int batch_create_on(rks_ctx *ctx, cudaStream_t stream, bool own_stream, int32_t nmol, const int32_t *natom,

@@ -56,18 +56,20 @@ def cost_estimate(Z):
 class Dispatcher:
     """Serves molecules to `n_workers` replicas; see the module docstring."""
 
-    def __init__(self, address, authkey, n_workers, chunk=64, timeout_s=600.0):
+    def __init__(self, address, authkey, n_workers, chunk=64, timeout_s=600.0, connect_timeout_s=60.0):
         self.listener = Listener(address, authkey=authkey)
         self.address = self.listener.address
         self.n_workers = n_workers
         self.chunk = chunk
         self.timeout_s = timeout_s
+        self.connect_timeout_s = connect_timeout_s
         self._new = collections.deque()
         self._lock = threading.Lock()
         self._accepting = True
         self._acceptor = threading.Thread(target=self._accept, daemon=True)
         self._acceptor.start()
         self.stats = collections.Counter()
+        self.sent = []  # molecule ids in the order they went out
 
     def _accept(self):
         while self._accepting:
@@ -85,6 +87,15 @@ class Dispatcher:
         the results in input order."""
         self._cost = [cost_estimate(Z) for Z, _ in mols]
         order = sorted(range(len(mols)), key=lambda i: -self._cost[i])
+        # start once the expected replicas have connected (or the wait runs
+        # out), so that the largest molecules spread over all of them; later
+        # workers join whenever they connect
+        t0 = time.monotonic()
+        while time.monotonic() - t0 < self.connect_timeout_s:
+            with self._lock:
+                if len(self._new) >= self.n_workers:
+                    break
+            time.sleep(0.01)
         queue = collections.deque(order)
         results = [None] * len(mols)
         left = len(mols)
@@ -121,6 +132,7 @@ class Dispatcher:
                         if results[i] is None:
                             out.append(i)
                     held[c].update(out)
+                    self.sent.extend(out)
                     try:
                         c.send(("work", [(i, np.asarray(mols[i][0], np.int32), np.asarray(mols[i][1], float))
                                          for i in out]))

@@ -110,6 +110,27 @@ def test_nbf_and_validation(L):
     assert L.rks_nbf(0, Z.ctypes.data) == g.RKS_EINVAL
 
 
+def test_mol_bytes_footprint(L):
+    """The admission figure: grows with the molecule, FP64 above mixed,
+    direct SCF drops the packed store (the bulk for 20-30 heavy atoms),
+    invalid molecules are rejected."""
+    import molgen
+    w = g.rks_mol_bytes([8, 1, 1])
+    small = g.rks_mol_bytes(molgen.batch(2, 1, 9, 9)[0][0], precision=g.RKS_MIXED)
+    Zb = molgen.batch(4, 1, 20, 20)[0][0]
+    big = g.rks_mol_bytes(Zb, precision=g.RKS_MIXED)
+    big_direct = g.rks_mol_bytes(Zb, precision=g.RKS_MIXED, direct_scf=g.RKS_DIRECT_ALWAYS)
+    assert 0 < w < small < big
+    assert g.rks_mol_bytes(Zb, precision=g.RKS_FP64) > big
+    n = g.rks_nbf(Zb)
+    npair = n * (n + 1) // 2
+    # the store's unscreened capacity is about npair^2 / 2 elements of 4 bytes
+    assert big - big_direct > 0.4 * 4 * npair * npair / 2
+    Z = np.array([2], np.int32)
+    assert L.rks_mol_bytes(None, 1, Z.ctypes.data) == g.RKS_EINVAL
+    assert L.rks_mol_bytes(None, 0, Z.ctypes.data) == g.RKS_EINVAL
+
+
 def test_error_names(L):
     for code in range(0, -9, -1):
         assert L.rks_strerror(code)

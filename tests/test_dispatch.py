@@ -80,13 +80,14 @@ def test_two_workers_answer_every_molecule_once(mols):
         assert r["E"] == _expected(m)
     assert d.stats["done"] == len(mols) and d.stats["dropped_workers"] == 0
     assert len({r["pid"] for r in res}) == 2  # both replicas took work
+    # every molecule went out once, largest estimated cost first
+    assert sorted(d.sent) == list(range(len(mols)))
+    costs = [dispatch.cost_estimate(mols[i][0]) for i in d.sent]
+    assert all(a >= b for a, b in zip(costs, costs[1:]))
     assert all(p.exitcode == 0 for p in ps)
 
 
-def test_largest_first_order():
-    costs = [dispatch.cost_estimate(Z) for Z, _ in molgen.batch(5, 40, 1, 6)]
-    order = sorted(range(40), key=lambda i: -costs[i])
-    assert all(costs[a] >= costs[b] for a, b in zip(order, order[1:]))
+def test_cost_estimate():
     # water: 3 atoms x 7^2; benzene-sized C6H6: 12 atoms x 36^2
     assert dispatch.cost_estimate([8, 1, 1]) == 3 * 49
     assert dispatch.cost_estimate([6] * 6 + [1] * 6) == 12 * 36 * 36
