@@ -186,10 +186,10 @@ def sad_density(Z, S):
 class System:
     """Everything of iteration 0 for one molecule (Section 3.1)."""
 
-    def __init__(self, Z, xyz, xc=True, grid_opts=None, tau=ints.TAU, grid_cache=True):
+    def __init__(self, Z, xyz, xc=True, grid_opts=None, tau=ints.TAU, grid_cache=True, basis="sto-3g"):
         self.Z = np.asarray(Z, np.int32)
         self.xyz = np.asarray(xyz, float).reshape(-1, 3)
-        self.sh = Shells(self.Z, self.xyz)
+        self.sh = Shells(self.Z, self.xyz, basis=basis)
         self.nbf = self.sh.nbf
         nel = int(self.Z.sum())
         if nel % 2:
@@ -233,6 +233,8 @@ class System:
         return solve_fock(self.H, self.X, self.nocc)[2]
 
     def sad_guess(self):
+        if self.sh.basis != "sto-3g":
+            raise ValueError("the superposed-atom guess is defined for STO-3G; use guess='core'")
         return sad_density(self.Z, self.S)
 
     def guess(self, kind):
