@@ -18,7 +18,9 @@ one-primitive outer valence s and p pair, for C, N, O, F (Hehre, Ditchfield
 and Pople, J. Chem. Phys. 56, 2257 (1972)); three primitives plus one for H
 (Ditchfield, Hehre and Pople, J. Chem. Phys. 54, 724 (1971); the same H
 functions as 4-31G).  AO order per heavy atom: 1s, 2s, 2p, 3s, 3p; per H:
-1s, 2s.
+1s, 2s.  Pinned: the contracted shells' unit norm and H2 against a printed
+energy (tests/test_oracle_631g.py); parity unpinned: the single outer
+exponents of C, N, O and F.
 
 Shell model (the packing convention of the two-electron store):
 * AO order: atoms in input order; per heavy atom 1s, 2s, 2px, 2py, 2pz; per H 1s.
