@@ -15,7 +15,11 @@ work from the dispatcher over TCP:
 * failure: a worker whose connection drops, or that sends nothing for
   `timeout_s` while it holds work, is dropped and its molecules go back to
   the front of the queue for the others (a result is kept once, the first
-  time it arrives).
+  time it arrives);
+* resume: with a checkpoint file, every result is appended to it as it
+  arrives (pickled, keyed by a hash of the molecule's atoms and
+  coordinates), and a later run over the same molecules dispatches only
+  those without a record (a record cut short by a crash is ignored).
 
 Transport is multiprocessing.connection (TCP, HMAC challenge with a shared
 auth key); messages are pickled tuples:
@@ -37,7 +41,9 @@ from __future__ import annotations
 
 import argparse
 import collections
+import hashlib
 import os
+import pickle
 import threading
 import time
 from multiprocessing.connection import Client, Listener, wait
@@ -51,6 +57,32 @@ def cost_estimate(Z):
     Z = np.asarray(Z)
     nbf = int(np.sum(np.where(Z > 1, 5, 1)))
     return len(Z) * nbf * nbf
+
+
+def mol_key(Z, xyz):
+    """Checkpoint key of a molecule: SHA-1 of its atomic numbers (int32) and
+    coordinates (float64)."""
+    h = hashlib.sha1()
+    h.update(np.ascontiguousarray(Z, np.int32).tobytes())
+    h.update(np.ascontiguousarray(xyz, np.float64).tobytes())
+    return h.hexdigest()
+
+
+def load_checkpoint(path, with_length=False):
+    """{key: result} from an append-only checkpoint file (a trusted file:
+    records are pickles); reading stops at the first incomplete record.
+    with_length: also return the byte length of the complete records."""
+    out, good = {}, 0
+    if os.path.exists(path):
+        with open(path, "rb") as f:
+            while True:
+                try:
+                    k, r = pickle.load(f)
+                except Exception:  # noqa: BLE001 - end of file, or a record cut short
+                    break
+                out[k] = r
+                good = f.tell()
+    return (out, good) if with_length else out
 
 
 class Dispatcher:
@@ -82,23 +114,36 @@ class Dispatcher:
             with self._lock:
                 self._new.append(c)
 
-    def run(self, mols):
+    def run(self, mols, checkpoint=None):
         """Every molecule of mols [(Z, xyz), ...] through the replicas; returns
-        the results in input order."""
+        the results in input order.  checkpoint: path of the resume file
+        (results already recorded there are not dispatched again)."""
         self._cost = [cost_estimate(Z) for Z, _ in mols]
         order = sorted(range(len(mols)), key=lambda i: -self._cost[i])
+        results = [None] * len(mols)
+        keys, ck = None, None
+        if checkpoint:
+            keys = [mol_key(Z, x) for Z, x in mols]
+            done, good = load_checkpoint(checkpoint, with_length=True)
+            for i, k in enumerate(keys):
+                if k in done:
+                    results[i] = done[k]
+                    self.stats["resumed"] += 1
+            # append after the last complete record (drop a record cut short)
+            ck = open(checkpoint, "r+b" if os.path.exists(checkpoint) else "wb")
+            ck.truncate(good)
+            ck.seek(good)
+        left = sum(r is None for r in results)
+        queue = collections.deque(i for i in order if results[i] is None)
         # start once the expected replicas have connected (or the wait runs
         # out), so that the largest molecules spread over all of them; later
         # workers join whenever they connect
         t0 = time.monotonic()
-        while time.monotonic() - t0 < self.connect_timeout_s:
+        while left > 0 and time.monotonic() - t0 < self.connect_timeout_s:
             with self._lock:
                 if len(self._new) >= self.n_workers:
                     break
             time.sleep(0.01)
-        queue = collections.deque(order)
-        results = [None] * len(mols)
-        left = len(mols)
         held = {}      # conn -> set of molecule ids it holds
         seen = {}      # conn -> time of its last message
         while left > 0:
@@ -124,6 +169,9 @@ class Dispatcher:
                             results[i] = r
                             left -= 1
                             self.stats["done"] += 1
+                            if ck:
+                                pickle.dump((keys[i], r), ck)
+                                ck.flush()
                 elif msg[0] == "want":
                     k = min(int(msg[1]), self.chunk)
                     out = []
@@ -141,7 +189,12 @@ class Dispatcher:
             now = time.monotonic()
             for c in [c for c in held if held[c] and now - seen[c] > self.timeout_s]:
                 self._drop(c, held, seen, queue, results)
-        for c in list(held):
+        if ck:
+            ck.close()
+        with self._lock:
+            idle = list(self._new)
+            self._new.clear()
+        for c in list(held) + idle:
             try:
                 c.send(("stop",))
             except (EOFError, OSError):

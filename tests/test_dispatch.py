@@ -55,14 +55,14 @@ def mols():
     return molgen.batch(5, 40, 1, 6)
 
 
-def _run(mols, workers, timeout_s=60.0):
+def _run(mols, workers, timeout_s=60.0, checkpoint=None):
     d = dispatch.Dispatcher(("127.0.0.1", 0), KEY, n_workers=len(workers), chunk=4, timeout_s=timeout_s)
     ctx = mp.get_context("spawn")
     ps = [ctx.Process(target=_worker, args=(d.address,) + w) for w in workers]
     for p in ps:
         p.start()
     try:
-        res = d.run(mols)
+        res = d.run(mols, checkpoint=checkpoint)
     finally:
         d.close()
         for p in ps:
@@ -110,3 +110,39 @@ def test_silent_worker_is_dropped_after_the_timeout(mols):
         assert r["E"] == _expected(m)
     assert d.stats["dropped_workers"] == 1
     assert time.monotonic() - t0 < 60
+
+
+def test_checkpoint_resumes_without_redoing_work(mols, tmp_path):
+    ck = str(tmp_path / "results.ckpt")
+    d1, res1, _ = _run(mols, [(), ()], checkpoint=ck)
+    assert d1.stats["done"] == len(mols)
+    # a second run over the same molecules finds every result recorded
+    d2, res2, _ = _run(mols, [], checkpoint=ck)
+    assert d2.sent == [] and d2.stats["resumed"] == len(mols)
+    assert [r["E"] for r in res2] == [r["E"] for r in res1]
+
+
+def test_checkpoint_cut_short_redoes_only_the_missing(mols, tmp_path):
+    ck = str(tmp_path / "results.ckpt")
+    _run(mols, [(), ()], checkpoint=ck)
+    # keep the first 10 records and half of the 11th, as a crash would
+    import pickle
+    with open(ck, "rb") as f:
+        ends = []
+        while True:
+            try:
+                pickle.load(f)
+            except EOFError:
+                break
+            ends.append(f.tell())
+    with open(ck, "rb") as f:
+        blob = f.read()
+    with open(ck, "wb") as f:
+        f.write(blob[:ends[9] + (ends[10] - ends[9]) // 2])
+    kept = dispatch.load_checkpoint(ck)
+    assert len(kept) == 10
+    d, res, ps = _run(mols, [()], checkpoint=ck)
+    assert d.stats["resumed"] == 10 and len(d.sent) == len(mols) - 10
+    for m, r in zip(mols, res):
+        assert r["E"] == _expected(m)
+    assert len(dispatch.load_checkpoint(ck)) == len(mols)
