@@ -6,7 +6,7 @@ import, call, link or execute anything under this directory.  The product
 (the CUDA library and its Python binding) shares no code with it.
 
 Modules:
-  basis  - STO-3G table and shell model (packing order)
+  basis  - STO-3G and 6-31G tables and shell model (packing order)
   ints   - FP64 McMurchie-Davidson integrals (ints.c), Schwarz screening, the
            canonical packed two-electron store
   grid   - Treutler-Ahlrichs M4 radial x Gauss-Legendre/uniform angular
@@ -18,5 +18,6 @@ Modules:
 Parity status per function is listed in the module headers; every function
 here has at least one pin in tests/test_oracle_*.py except the whole-method
 absolute B3LYP energy, whose parity is unpinned beyond the invariants (the
-paper prints no energies).
+paper prints no energies), and the single outer exponents of the 6-31G heavy
+atoms (parity unpinned).
 """
