@@ -28,11 +28,13 @@ auth key); messages are pickled tuples:
   dispatcher -> worker  ("work", [(i, Z, xyz), ...])
                         ("stop",)
 
-    # dispatcher host
-    d = Dispatcher(("0.0.0.0", 7788), authkey=b"...", n_workers=8)
-    results = d.run(mols)            # list of result dicts, input order
+    # dispatcher host (RKS_DISPATCH_KEY holds the shared key everywhere)
+    python -m paper_2311_01135_gb300.dispatch serve --listen 0.0.0.0:7788 --workers 8 \
+        --input mols.npz --output results.npz --checkpoint results.ckpt
     # each GPU (any host)
-    python -m paper_2311_01135_gb300.dispatch --connect HOST:7788 --device 0
+    python -m paper_2311_01135_gb300.dispatch worker --connect HOST:7788 --device 0
+
+or from Python: Dispatcher(("0.0.0.0", 7788), authkey, n_workers=8).run(mols).
 
 This module is host code only: every molecule a worker runs goes through the
 library's serving calls (rks_submit_batch / rks_wait / rks_result).
@@ -272,19 +274,73 @@ def worker_loop(address, authkey, engine, chunk=64, depth=2):
         conn.close()
 
 
-def main():
-    ap = argparse.ArgumentParser(description="RKS replica worker: pulls molecules from a dispatcher")
-    ap.add_argument("--connect", required=True, help="dispatcher HOST:PORT")
-    ap.add_argument("--device", type=int, default=int(os.environ.get("LOCAL_RANK", "0")))
-    ap.add_argument("--authkey-env", default="RKS_DISPATCH_KEY")
-    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
-    ap.add_argument("--fixed-iters", type=int, default=20)
-    ap.add_argument("--chunk", type=int, default=64)
-    a = ap.parse_args()
-    host, port = a.connect.rsplit(":", 1)
-    key = os.environ.get(a.authkey_env, "").encode()
+def read_molecules(path):
+    """Molecules from an .npz in the batch calls' layout: natom (int32 [n]),
+    Z (int32, all atoms in order), xyz (float64 [atoms, 3], bohr)."""
+    f = np.load(path)
+    na = np.asarray(f["natom"], np.int64)
+    Z = np.asarray(f["Z"], np.int32)
+    xyz = np.asarray(f["xyz"], np.float64).reshape(-1, 3)
+    off = np.concatenate([[0], np.cumsum(na)])
+    return [(Z[off[k]:off[k + 1]], xyz[off[k]:off[k + 1]]) for k in range(len(na))]
+
+
+def write_results(path, results):
+    """Results to an .npz: per molecule the scalars of rks_result_t (E, homo,
+    lumo, gap, iters, nbf, status as a string), and eps and D concatenated
+    with their offsets (eps_off, D_off)."""
+    n = len(results)
+    nbf = np.array([r["nbf"] for r in results], np.int64)
+    eps_off = np.concatenate([[0], np.cumsum(nbf)])
+    D_off = np.concatenate([[0], np.cumsum(nbf * nbf)])
+    np.savez(path, E=np.array([r["E"] for r in results]), homo=np.array([r["homo"] for r in results]),
+             lumo=np.array([r["lumo"] for r in results]), gap=np.array([r["gap"] for r in results]),
+             iters=np.array([r["iters"] for r in results], np.int64), nbf=nbf,
+             status=np.array([str(r["status"]) for r in results]),
+             eps=np.concatenate([np.ravel(r["eps"]) for r in results]) if n else np.zeros(0),
+             D=np.concatenate([np.ravel(r["D"]) for r in results]) if n else np.zeros(0),
+             eps_off=eps_off, D_off=D_off)
+
+
+def _key(env):
+    key = os.environ.get(env, "").encode()
     if not key:
-        raise SystemExit(f"set {a.authkey_env} to the dispatcher's auth key")
+        raise SystemExit(f"set {env} to the shared auth key")
+    return key
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description="RKS replicas across hosts: a dispatcher and one worker per GPU")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    w = sub.add_parser("worker", help="one GPU: pull molecules from a dispatcher")
+    w.add_argument("--connect", required=True, help="dispatcher HOST:PORT")
+    w.add_argument("--device", type=int, default=int(os.environ.get("LOCAL_RANK", "0")))
+    w.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    w.add_argument("--fixed-iters", type=int, default=20)
+    w.add_argument("--chunk", type=int, default=64)
+    d = sub.add_parser("serve", help="hand the molecules of --input to the workers, write --output")
+    d.add_argument("--listen", required=True, help="HOST:PORT to accept workers on")
+    d.add_argument("--workers", type=int, required=True, help="replicas to wait for before starting")
+    d.add_argument("--input", required=True, help=".npz with natom, Z, xyz (bohr)")
+    d.add_argument("--output", required=True, help=".npz of the results, input order")
+    d.add_argument("--checkpoint", default=None, help="resume file (results recorded there are not redone)")
+    d.add_argument("--chunk", type=int, default=64)
+    d.add_argument("--timeout-s", type=float, default=600.0)
+    for p in (w, d):
+        p.add_argument("--authkey-env", default="RKS_DISPATCH_KEY")
+    a = ap.parse_args(argv)
+    key = _key(a.authkey_env)
+    if a.cmd == "serve":
+        host, port = a.listen.rsplit(":", 1)
+        mols = read_molecules(a.input)
+        disp = Dispatcher((host, int(port)), key, n_workers=a.workers, chunk=a.chunk, timeout_s=a.timeout_s)
+        try:
+            res = disp.run(mols, checkpoint=a.checkpoint)
+        finally:
+            disp.close()
+        write_results(a.output, res)
+        return
+    host, port = a.connect.rsplit(":", 1)
     import paper_2311_01135_gb300 as g
     eng = EngineRunner(device=a.device, precision=g.RKS_MIXED if a.precision == "mixed" else g.RKS_FP64,
                        fixed_iters=a.fixed_iters)

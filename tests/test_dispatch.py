@@ -146,3 +146,75 @@ def test_checkpoint_cut_short_redoes_only_the_missing(mols, tmp_path):
     for m, r in zip(mols, res):
         assert r["E"] == _expected(m)
     assert len(dispatch.load_checkpoint(ck)) == len(mols)
+
+
+class FullFakeEngine:
+    """Stand-in answering with every field the command line writes."""
+
+    def submit(self, jobs):
+        out = []
+        for i, Z, xyz in jobs:
+            n = int(np.sum(np.where(np.asarray(Z) > 1, 5, 1)))
+            e = _expected((Z, xyz))
+            out.append((i, {"E": e, "homo": -0.3, "lumo": 0.1, "gap": 0.4, "iters": 20, "nbf": n,
+                            "status": "ok", "eps": np.arange(n, dtype=float) + e,
+                            "D": np.full((n, n), float(i))}))
+        return out
+
+    def collect(self, handle):
+        return handle
+
+
+def _full_worker(address):
+    dispatch.worker_loop(address, KEY, FullFakeEngine(), chunk=4)
+
+
+def test_command_line_serve_round_trip(mols, tmp_path):
+    import socket
+    import subprocess
+    import sys
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    na = np.array([len(Z) for Z, _ in mols], np.int32)
+    np.savez(tmp_path / "in.npz", natom=na, Z=np.concatenate([Z for Z, _ in mols]).astype(np.int32),
+             xyz=np.concatenate([x for _, x in mols]))
+    env = dict(os.environ, RKS_DISPATCH_KEY=KEY.decode())
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    srv = subprocess.Popen([sys.executable, "-m", "paper_2311_01135_gb300.dispatch", "serve",
+                            "--listen", f"127.0.0.1:{port}", "--workers", "2", "--input", str(tmp_path / "in.npz"),
+                            "--output", str(tmp_path / "out.npz"), "--chunk", "4"], env=env, cwd=root)
+    ctx = mp.get_context("spawn")
+    ps = []
+    try:
+        time.sleep(1.0)
+        deadline = time.monotonic() + 60
+        while True:  # the listener may take a moment to come up (a bare TCP
+            # connect fails the auth handshake and is not counted as a worker)
+            try:
+                socket.create_connection(("127.0.0.1", port), timeout=1).close()
+                break
+            except OSError:
+                assert time.monotonic() < deadline
+                time.sleep(0.2)
+        ps = [ctx.Process(target=_full_worker, args=(("127.0.0.1", port),)) for _ in range(2)]
+        for p in ps:
+            p.start()
+        assert srv.wait(timeout=120) == 0
+    finally:
+        if srv.poll() is None:
+            srv.kill()
+        for p in ps:
+            p.join(timeout=20)
+            if p.is_alive():
+                p.kill()
+    out = np.load(tmp_path / "out.npz")
+    assert len(out["E"]) == len(mols)
+    for k, m in enumerate(mols):
+        assert out["E"][k] == _expected(m)
+        n = int(out["nbf"][k])
+        e = out["eps"][out["eps_off"][k]:out["eps_off"][k + 1]]
+        D = out["D"][out["D_off"][k]:out["D_off"][k + 1]].reshape(n, n)
+        assert np.array_equal(e, np.arange(n) + _expected(m)) and np.all(D == k)
+    assert set(out["status"]) == {"ok"}
