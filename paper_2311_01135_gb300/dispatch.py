@@ -22,7 +22,7 @@ work from the dispatcher over TCP:
   those without a record (a record cut short by a crash is ignored).
 
 Transport is multiprocessing.connection (TCP, HMAC challenge with a shared
-auth key); messages are pickled tuples:
+auth key), meant for a trusted cluster network; messages are pickled tuples:
   worker -> dispatcher  ("want", k)                   ask for up to k molecules
                         ("done", [(i, result), ...])  results of molecules i
   dispatcher -> worker  ("work", [(i, Z, xyz), ...])

@@ -90,3 +90,11 @@ def test_small_and_edge_molecules():
     assert g.rks_tc_plan(np.array([6] * 9 + [1] * 3))[0] == 16  # 9 heavy atoms need three units a quarter
     with pytest.raises(Exception):
         g.rks_tc_plan(np.array([2, 2]))
+
+
+def test_larger_molecules_take_no_plan():
+    """Molecules of the 20-30-heavy-atom workload (above 80 functions) get no
+    tensor-core plan: the global-memory kernels take them."""
+    for Z, _ in molgen.batch(4, 32, 20, 30):
+        assert g.rks_nbf(Z) > 96
+        assert check_plan(Z) == 0
